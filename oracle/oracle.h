@@ -1,0 +1,105 @@
+/*
+ * oracle.h -- plain, sequential, FP64 CPU restatement of Chebyshev-basis s-step PCG
+ * (PCG-S) with Forward Gauss-Seidel (FGS) Gram solves, and of classical PCG.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path: only the test
+ * suite, the smoke check and the CPU-baseline leg of the benchmark load it.  It shares no
+ * code, header, helper or constant with the CUDA library, and the CUDA library never
+ * calls it.
+ *
+ * Every routine is written as the paper states it ("Scalable s-step Preconditioned
+ * Conjugate Gradient with Chebyshev Basis and Gauss-Seidel Gram Solve"):
+ *   - Section 2, Algorithm 1 (PCG-S) and Algorithm 2 (MPK for the Chebyshev basis),
+ *   - Section 2, Chebyshev scalars alpha, sigma, gamma and the power method for lambda_max,
+ *   - Section 3.1, Eq. (fgs-iteration): FGS on the Gram system (plain splitting of W),
+ *   - Section 1 (PCG), textbook Hestenes-Stiefel preconditioned CG.
+ * The paper reuses the letter alpha for the Chebyshev scale and for the step vector; this
+ * code names the Chebyshev scalars c_alpha, c_sigma, c_gamma.
+ *
+ * Conventions: vectors are plain double arrays of length n; blocks are column-major
+ * n x k arrays with leading dimension n; the operator is CSR with int64 row pointers and
+ * int32 column indices.  No routine allocates more than O(n s) doubles.  Status codes are
+ * the integers listed below.
+ */
+#ifndef SSTEP_ORACLE_H
+#define SSTEP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  OR_OK = 0,
+  OR_NOT_CONVERGED = 1,
+  OR_ERR_INVALID = 2,
+  OR_ERR_BREAKDOWN = 3,   /* W_ii <= 0 or non-finite Gram entry */
+  OR_ERR_NONFINITE = 4    /* non-finite residual norm */
+};
+
+enum { OR_PREC_NONE = 0, OR_PREC_JACOBI = 1 };
+enum { OR_ALGO_LITERAL = 0, OR_ALGO_ONESYNC = 1 };
+enum { OR_GRAM_FGS = 0, OR_GRAM_CHOLESKY = 1 };
+
+typedef struct {
+  int64_t n;
+  const int64_t* rowptr;  /* n+1 */
+  const int32_t* colind;  /* nnz */
+  const double* vals;     /* nnz */
+} or_csr;
+
+typedef struct {
+  int status;
+  int iters;              /* outer iterations (PCG-S) or iterations (PCG) = executed x/r updates */
+  double relres;          /* ||r_rec|| / ||b|| at exit (recursively updated residual) */
+  double relres_true;     /* ||b - A x|| / ||b|| at exit */
+  double c_alpha, c_sigma, c_gamma;
+} or_info;
+
+/* y = A x. */
+void or_spmv(const or_csr* A, const double* x, double* y);
+/* dinv_i = 1 / a_ii  (Jacobi, M = diag(A)). Returns OR_ERR_INVALID if a diagonal is missing or <= 0. */
+int or_jacobi_dinv(const or_csr* A, double* dinv);
+/* y = M^{-1} x for M = I (dinv ignored) or M = diag(A). */
+void or_prec_apply(int prec, int64_t n, const double* dinv, const double* x, double* y);
+/* Gershgorin lower bound of the spectrum of M^{-1}A, clamped at 0. */
+double or_gershgorin_lower(const or_csr* A, int prec);
+/* Power method on M^{-1}A (Section 2): lambda^(l) = ||M^{-1}A v_{l-1}||, ||v_{l-1}|| = 1.
+ * Stops when |lambda^(l) - lambda^(l-1)| < tol |lambda^(l)| or after max_iters iterations
+ * (tol <= 0: exactly max_iters).  v0 need not be normalised.  Returns lambda, *iters_out. */
+double or_power_lambda_max(const or_csr* A, int prec, const double* dinv, const double* v0,
+                           int max_iters, double tol, int* iters_out);
+/* Chebyshev scalars of Section 2: c_alpha = 2/(lmax-lmin), c_sigma = (lmax+lmin)/(lmax-lmin), c_gamma = 1. */
+void or_cheb_scalars(double lmin, double lmax, double* c_alpha, double* c_sigma, double* c_gamma);
+/* Algorithm 2: Z (n x s) and P (n x (s+1)) for residual r. zp workspace is internal. */
+int or_mpk(const or_csr* A, int prec, const double* dinv, const double* r, int s,
+           double c_alpha, double c_sigma, double c_gamma, double* Z, double* P);
+/* Eq. (fgs-iteration) written on W itself (plain Gauss-Seidel splitting W = D + L_W + L_W^T):
+ * nu forward sweeps from alpha^(0) = 0 on W alpha = m.  W is s x s column-major. */
+int or_fgs(int s, const double* W, const double* m, int nu, double* alpha);
+/* Dense Cholesky solve of W alpha = m (W SPD, s x s column-major). */
+int or_chol_solve(int s, const double* W, const double* m, double* alpha);
+/* Gram products: G = X^T Y with X n x a, Y n x b (column-major), G a x b column-major. */
+void or_gram(int64_t n, int a, const double* X, int b, const double* Y, double* G);
+
+/* Algorithm 1 (PCG-S).  x holds x^(0) on entry and the solution on exit.
+ * algo: OR_ALGO_LITERAL follows Algorithm 1 line by line (two reductions per outer iteration);
+ *       OR_ALGO_ONESYNC forms W_{k+1} from the Gram blocks of [Q_k, Z_{k+1}] and beta_k
+ *       (algebraically identical; one reduction per outer iteration).
+ * gram: OR_GRAM_FGS (nu sweeps) or OR_GRAM_CHOLESKY (exact reduced solves).
+ * lambda_max > 0 is used as given; otherwise it is estimated by the power method.
+ * hist (optional, length max_outer+1): ||r^(k)|| / ||b||.  eta_a, eta_b (optional, length
+ * max_outer): reduced-solve relative residuals of Section 3.3. */
+int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
+            int s, int nu, double rtol, int max_outer, int algo, int gram,
+            double lambda_min, double lambda_max, const double* power_v0, int power_iters,
+            double power_tol, or_info* info, double* hist, double* eta_a, double* eta_b);
+
+/* Classical preconditioned CG (Hestenes-Stiefel).  hist optional, length max_iters+1. */
+int or_pcg(const or_csr* A, int prec, const double* b, double* x, double rtol, int max_iters,
+           or_info* info, double* hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

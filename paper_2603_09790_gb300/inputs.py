@@ -1,0 +1,135 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module draws random numbers and lays out test operators; it holds none of the
+solver's arithmetic (no Krylov step, no Chebyshev recurrence, no Gram product).
+
+* ``splitmix64`` / ``uniform_pm1``: SplitMix64 (Steele, Lea and Flood, "Fast splittable
+  pseudorandom number generators", OOPSLA 2014).  The k-th output of a stream with seed
+  ``s`` mixes ``s + (k+1) * 0x9E3779B97F4A7C15``; a double in [-1, 1) is
+  ``2 * (out >> 11) * 2**-53 - 1``.  x_true uses seed 0 and the power-method start vector
+  seed 1, both in lexicographic grid order.
+* ``poisson_csr``: the finite-difference Poisson matrices the paper's experiments use
+  (27-point as in HPCG, Section 6) and their 5- and 7-point relatives, on the interior
+  unknowns of an nx x ny x nz grid with Dirichlet neighbours dropped; row index
+  ``i + nx*(j + ny*k)``; diagonal 4 / 6 / 26, off-diagonals -1; columns sorted.
+* ``poisson_apply``: the same operator applied matrix-free, used only to form the
+  right-hand side b = A x_true of a synthetic problem.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+STENCIL_DIAG = {5: 4.0, 7: 6.0, 27: 26.0}
+
+
+def splitmix64(seed: int, n: int, start: int = 0) -> np.ndarray:
+    """Outputs ``start .. start+n-1`` of the SplitMix64 stream with the given seed (uint64)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed: int, n: int, start: int = 0) -> np.ndarray:
+    """Doubles in [-1, 1) from SplitMix64: 2*u - 1 with u = (next >> 11) * 2**-53."""
+    u = (splitmix64(seed, n, start) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return 2.0 * u - 1.0
+
+
+def stencil_offsets(points: int):
+    """Neighbour offsets (dx, dy, dz) of a stencil, sorted by linear column offset."""
+    if points == 5:
+        offs = [(0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0)]
+    elif points == 7:
+        offs = [(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    elif points == 27:
+        offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    else:
+        raise ValueError("points must be 5, 7 or 27")
+    return offs
+
+
+def _dims3(dims):
+    dims = tuple(int(d) for d in dims)
+    if len(dims) == 2:
+        dims = dims + (1,)
+    if len(dims) != 3 or min(dims) < 1:
+        raise ValueError("dims must be (nx, ny) or (nx, ny, nz) with positive entries")
+    return dims
+
+
+def poisson_csr(dims, points: int):
+    """CSR arrays (rowptr int64, colind int32, vals float64) of the Dirichlet Poisson matrix."""
+    nx, ny, nz = _dims3(dims)
+    if points == 5 and nz != 1:
+        raise ValueError("the 5-point stencil is two-dimensional")
+    n = nx * ny * nz
+    diag = STENCIL_DIAG[points]
+    idx = np.arange(n, dtype=np.int64)
+    ix = idx % nx
+    iy = (idx // nx) % ny
+    iz = idx // (nx * ny)
+    offs = stencil_offsets(points)
+    masks = []
+    for dx, dy, dz in offs:
+        m = np.ones(n, dtype=bool)
+        if dx:
+            m &= (ix + dx >= 0) & (ix + dx < nx)
+        if dy:
+            m &= (iy + dy >= 0) & (iy + dy < ny)
+        if dz:
+            m &= (iz + dz >= 0) & (iz + dz < nz)
+        masks.append(m)
+    counts = np.zeros(n, dtype=np.int64)
+    for m in masks:
+        counts += m
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    if nnz >= 2 ** 31 or n >= 2 ** 31:
+        raise ValueError("operator too large for int32 column indices")
+    colind = np.empty(nnz, dtype=np.int32)
+    vals = np.empty(nnz, dtype=np.float64)
+    fill = rowptr[:-1].copy()
+    for (dx, dy, dz), m in zip(offs, masks):
+        rows = idx[m]
+        pos = fill[m]
+        colind[pos] = (rows + dx + nx * (dy + ny * dz)).astype(np.int32)
+        vals[pos] = diag if (dx, dy, dz) == (0, 0, 0) else -1.0
+        fill[m] += 1
+    return rowptr, colind, vals
+
+
+def poisson_apply(dims, points: int, x: np.ndarray) -> np.ndarray:
+    """A x for the Dirichlet Poisson matrix, matrix-free (used to form b = A x_true)."""
+    nx, ny, nz = _dims3(dims)
+    u = np.asarray(x, dtype=np.float64).reshape(nz, ny, nx)
+    pad = np.zeros((nz + 2, ny + 2, nx + 2))
+    pad[1:-1, 1:-1, 1:-1] = u
+    y = STENCIL_DIAG[points] * u
+    for dx, dy, dz in stencil_offsets(points):
+        if (dx, dy, dz) == (0, 0, 0):
+            continue
+        y = y - pad[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+    return y.reshape(-1)
+
+
+def poisson_problem(dims, points: int, seed: int = 0):
+    """x_true ~ U[-1,1) (SplitMix64, given seed, lexicographic) and b = A x_true."""
+    nx, ny, nz = _dims3(dims)
+    n = nx * ny * nz
+    x_true = uniform_pm1(seed, n)
+    b = poisson_apply((nx, ny, nz), points, x_true)
+    return x_true, b
+
+
+def power_start(n: int, seed: int = 1) -> np.ndarray:
+    """Start vector of the power method: U[-1,1) with seed 1."""
+    return uniform_pm1(seed, n)
