@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Time to rtol 1e-8 of Chebyshev-basis s-step PCG with FGS Gram solves, against classical PCG
+from the same CUDA library, on the 3D 7-point Poisson problem (256^3 interior unknowns,
+stencil form, Jacobi), one GB300 per rank.  Prints one JSON line (rank 0).
+
+A step is one whole solve: r0 = b - A x0, the outer iterations of PCG-S to ||r|| <= 1e-8 ||b||
+(MPK, Gram reduction + reduced solves, fused block update, stop test) and the true residual.
+Inputs (b, x0) are resident in device memory when the timed region starts; every vector is
+134 MB, larger than L2, and the working set is several GB.
+
+--impl reference times the FP64 CPU oracle on the host cores on bounded samples of the same
+workload, extrapolated to a whole solve with the oracle's own iteration count.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual, s-step vs classical PCG, 256^3 Poisson; HBM GB/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+COUNTS_FILE = os.path.join(ROOT, "tests", "golden", "oracle_counts_256.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# FP64 pipe of GB300: 2 FMA per clock per SM x 152 SMs x 2.07 GHz x 2 flops = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=256, help="grid edge (n^3 unknowns)")
+    p.add_argument("--s", type=int, default=2)
+    p.add_argument("--sweeps", type=int, default=3)
+    p.add_argument("--form", choices=["stencil", "csr"], default="stencil")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--extra", default="", help="extra s-step configs to time, e.g. '4:3,4:30'")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_median": float(np.median(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- algorithmic work per kernel
+
+def kernel_work(s, n, points=7):
+    """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes)."""
+    V = 8.0 * n
+    sp_flops = {5: 5, 7: 7, 27: 27}[points]  # Poisson: (points-1) adds + 1 multiply per row
+    rec = 4  # z_{q+1} = c1 d (Az) - c2 z_q - z_{q-1}: 2 multiplies + 2 adds
+    ne = 2 * s * s + 3 * s  # Gram entries of the one-reduction form
+    mpk_bytes = (4 * (s - 1) + 2) * V if s > 1 else 3 * V
+    return {
+        "mpk_step": {"bytes": mpk_bytes / s, "flops": (sp_flops + rec) * n, "launches_per_outer": s},
+        "gram": {"bytes": (4 * s + 1) * V, "flops": 2.0 * ne * n, "launches_per_outer": 1},
+        "update": {"bytes": (6 * s + 4) * V, "flops": 2.0 * (2 * s * s + 2 * s + 1) * n,
+                   "launches_per_outer": 1},
+        "pcg_spmv_dot": {"bytes": 2 * V, "flops": (sp_flops + 2) * n},
+        "pcg_update": {"bytes": 6 * V, "flops": 10.0 * n},
+        "pcg_pdir": {"bytes": 3 * V, "flops": 3.0 * n},
+    }
+
+
+def source_hash(*files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, workload, src_hash):
+    try:
+        data = json.load(open(TRAFFIC_FILE))
+        rec = data.get(kernel + "@" + workload)
+        if rec and rec.get("source_hash") == src_hash:
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(PEAKS_FILE))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_sample(n_edge, s, nu, gpu_lambda=None, outer_sample=2):
+    """Time the oracle on bounded samples of the workload and extrapolate to a whole solve.
+
+    Returns (seconds_per_solve, description, details).  The extrapolation multiplies the
+    per-outer-iteration time by the oracle's own iteration count for this workload when it is
+    recorded (tests/golden/oracle_counts_256.json), else by the count given by the caller.
+    """
+    import oracle as O
+    from paper_2603_09790_gb300 import inputs as I
+
+    dims = (n_edge,) * 3
+    A = O.CSR(*I.poisson_csr(dims, 7))
+    xt, b = I.poisson_problem(dims, 7)
+    v0 = I.power_start(A.n)
+    t = time.perf_counter()
+    lam2, _ = O.power(A, "jacobi", v0, 2, 0.0)
+    t_power = (time.perf_counter() - t) / 2 * 20  # 20 power iterations
+    lam = gpu_lambda if gpu_lambda else lam2
+    t = time.perf_counter()
+    O.pcgs(A, b, s=s, nu=nu, rtol=0.0, max_outer=outer_sample, algo="onesync", lambda_max=lam)
+    t_outer_s = (time.perf_counter() - t) / outer_sample
+    t = time.perf_counter()
+    O.pcg(A, b, rtol=0.0, max_iters=4 * outer_sample)
+    t_pcg_it = (time.perf_counter() - t) / (4 * outer_sample)
+    return t_power, t_outer_s, t_pcg_it
+
+
+def oracle_counts():
+    try:
+        return json.load(open(COUNTS_FILE))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    counts = oracle_counts()
+    key = f"s{args.s}nu{args.sweeps}"
+    if args.n != 256 or key not in counts:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no recorded oracle iteration count for n={args.n}, {key}"}))
+        return 0
+    N_outer = counts[key]["iters"]
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_power, t_outer, _ = oracle_sample(args.n, args.s, args.sweeps, outer_sample=1)
+        if k >= args.warmup:
+            times.append(t_power + t_outer * N_outer)
+    v = float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"poisson7_{args.n}^3_csr_jacobi_s{args.s}_nu{args.sweeps}_rtol1e-8",
+                   "algo": "PCG-S one-reduction form, FP64 oracle (plain C, sequential)"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: 1 outer iteration + 2 power iterations of the oracle "
+                                   f"at {args.n}^3, extrapolated to 20 power iterations and the oracle's "
+                                   f"recorded {N_outer} outer iterations"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_09790_gb300 import inputs as I
+    from paper_2603_09790_gb300 import sstep
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N = args.n
+    dims = (N, N, N)
+    n = N ** 3
+    xt, b = I.poisson_problem(dims, 7)
+    v0 = I.power_start(n)
+    bd = torch.from_numpy(b).to(dev)
+    v0d = torch.from_numpy(v0).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    if args.form == "stencil":
+        A = sstep.Stencil(N, N, N, 7)
+    else:
+        rp, ci, vv = I.poisson_csr(dims, 7)
+        A = sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                      torch.from_numpy(vv).to(dev))
+    common = dict(rtol=1e-8, power_iters=20, power_tol=0.0, power_v0=v0d, lambda_min=-1.0,
+                  stream=stream)
+
+    def timed_solves(S, xd, K, W):
+        for _ in range(W):
+            xd.zero_()
+            S.solve(bd, xd)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = []
+        infos = []
+        for _ in range(K):
+            with torch.cuda.stream(stream):
+                xd.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            infos.append(S.solve(bd, xd))
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b_) for a, b_ in evs]
+        return ms, infos
+
+    # ---- s-step (headline)
+    S = sstep.Solver(A, s=args.s, sweeps=args.sweeps, algo="onesync", **common)
+    xd = torch.zeros(n, dtype=torch.float64, device=dev)
+    gpu_id = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(("GPU-" + str(gpu_id)) if gpu_id else local)
+    for _ in range(args.warmup):
+        xd.zero_()
+        S.solve(bd, xd)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ms, infos = timed_solves(S, xd, args.steps, 0)
+    clocks = sampler.stop()
+    ms_step = float(np.mean(ms))
+    ms_max = ms_step
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    info = infos[-1]
+    basis = S.get_basis_info()
+
+    # ---- end to end through the public API with host (pinned) buffers
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve(bh, xh)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    x_host = xh.numpy()
+    err_true = float(np.linalg.norm(x_host - xt) / np.linalg.norm(xt))
+
+    # ---- per-phase device times (CUDA events between the phases of eager outer iterations)
+    S.profile(bd, iters=2)
+    ph = S.profile(bd, iters=5)
+    S.free()
+
+    # ---- classical PCG from the same library
+    P = sstep.Solver(A, algo="pcg", **common)
+    xp = torch.zeros(n, dtype=torch.float64, device=dev)
+    pms, pinfos = timed_solves(P, xp, args.steps, args.warmup)
+    P.profile(bd, iters=2)
+    pph = P.profile(bd, iters=5)
+    P.free()
+
+    # ---- optional extra s-step configurations
+    extra = {}
+    for item in filter(None, args.extra.split(",")):
+        s_, nu_ = (int(v) for v in item.split(":"))
+        E = sstep.Solver(A, s=s_, sweeps=nu_, algo="onesync", **common)
+        ems, einfos = timed_solves(E, xd, 1, 1)
+        extra[f"s{s_}_nu{nu_}"] = {"s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
+                                   "relres_true": einfos[0].relres_true}
+        E.free()
+
+    # ---- roofline of each kernel from the phase times
+    work = kernel_work(args.s, n)
+    hbm, hbm_src = hbm_peak()
+    per = {}
+    for name, t_ms, launches in (("mpk_step", ph[0] / args.s, args.s), ("gram", ph[1], 1),
+                                 ("update", ph[2], 1), ("pcg_spmv_dot", pph[0], 1),
+                                 ("pcg_update", pph[1], 1), ("pcg_pdir", pph[2], 1)):
+        w = work[name]
+        per[name] = {"ms_per_launch": t_ms, "GB_s": w["bytes"] / (t_ms * 1e-3) / 1e9,
+                     "TFLOP_s": w["flops"] / (t_ms * 1e-3) / 1e12,
+                     "hbm_frac": w["bytes"] / (t_ms * 1e-3) / 1e9 / hbm,
+                     "fp64_frac": w["flops"] / (t_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    share = {"mpk": ph[0], "gram": ph[1], "update": ph[2]}
+    dom = max(share, key=share.get)
+    dom_kernel = {"mpk": "mpk_step", "gram": "gram", "update": "update"}[dom]
+    d = per[dom_kernel]
+    workload = f"poisson7_{N}^3_{args.form}_jacobi_s{args.s}_nu{args.sweeps}"
+    src = source_hash("paper_2603_09790_gb300/csrc/k_blas.cu", "paper_2603_09790_gb300/csrc/k_operator.cu",
+                      "paper_2603_09790_gb300/csrc/common.cuh")
+    traffic = load_traffic(dom_kernel, workload, src)
+    roofline = {"bound": "alu", "kernel": dom_kernel, "achieved": d["TFLOP_s"],
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": d["TFLOP_s"] / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "traffic": traffic, "algorithmic_bytes": work[dom_kernel]["bytes"],
+                "hbm_GB_s": d["GB_s"], "hbm_peak_GB_s": hbm, "hbm_peak_source": hbm_src,
+                "hbm_frac": d["hbm_frac"],
+                "timing": "CUDA events on the solver's stream between the phases of 5 outer "
+                          "iterations launched right after the timed solves"}
+
+    line = {
+        "metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "n": n, "grid": list(dims), "stencil": 7, "form": args.form,
+                   "precond": "jacobi", "s": args.s, "sweeps": args.sweeps, "rtol": 1e-8,
+                   "power_iters": 20, "lambda_min": basis["lambda_min"],
+                   "lambda_max": basis["lambda_max"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (each vector 134 MB; working set > 4 GB)"},
+        "outer_iters": info.outer_iters, "inner_equiv": info.inner_equiv,
+        "relres": info.relres, "relres_true": info.relres_true, "x_rel_error_vs_true": err_true,
+        "pcg": {"s": float(np.mean(pms)) / 1e3, "iters": pinfos[-1].outer_iters,
+                "relres_true": pinfos[-1].relres_true},
+        "sstep_over_pcg_time": ms_step / float(np.mean(pms)),
+        "extra_configs": extra,
+        "e2e": {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": int(info.launches),
+        "phase_ms_per_outer": {"mpk": ph[0], "gram": ph[1], "update": ph[2]},
+        "per_kernel": per, "roofline": roofline, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_power, t_outer, t_pcg = oracle_sample(N, args.s, args.sweeps, basis["lambda_max"])
+        counts = oracle_counts().get(f"s{args.s}nu{args.sweeps}")
+        n_outer = counts["iters"] if counts and N == 256 else info.outer_iters
+        v = t_power + t_outer * n_outer
+        line["cpu_baseline"] = {
+            "value": v, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"2 power + 2 outer iterations + 8 PCG iterations of the FP64 C oracle at {N}^3 "
+                      f"(single thread), extrapolated to 20 power and {n_outer} outer iterations",
+            "pcg_value": t_pcg * (oracle_counts().get("pcg", {}).get("iters") or pinfos[-1].outer_iters)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * sstep.h -- C ABI of libsstep.so: Chebyshev-basis s-step preconditioned conjugate gradient
+ * (PCG-S) with Forward Gauss-Seidel (FGS) Gram solves, and classical PCG, on one NVIDIA GB300
+ * (sm_103a).  Method: D'Ambra, Bernaschi, Carrozzo, Thomas, "Scalable s-step Preconditioned
+ * Conjugate Gradient with Chebyshev Basis and Gauss-Seidel Gram Solve" (arXiv 2603.09790).
+ *
+ * General conventions
+ *  - All floating point is IEEE binary64 unless a name says otherwise.
+ *  - Vectors are dense arrays of n doubles.  Blocks of k vectors are column-major with leading
+ *    dimension ld >= n (column j starts at base + j*ld).
+ *  - "device pointer" means memory the GPU can address (cudaMalloc / torch CUDA tensors).
+ *    Entry points marked "device or host" accept either; host memory is staged through the
+ *    library's own device buffers, with the copies ordered on the handle's stream.
+ *  - Every entry point returns an sstep_status and never aborts, throws or traps.  A
+ *    description of the last failure on the calling thread is returned by sstep_last_error().
+ *  - Work is ordered on the CUDA stream given at set-up (passed as void*; NULL = the legacy
+ *    default stream).  sstep_solve* return after the solve has finished on that stream.
+ *  - Not thread-safe per handle: one handle must not be used from two threads at once.
+ */
+#ifndef SSTEP_H
+#define SSTEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSTEP_API __attribute__((visibility("default")))
+#else
+#define SSTEP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sstep_ctx* sstep_handle; /* opaque, owned by the library */
+
+typedef enum {
+  SSTEP_OK = 0,
+  SSTEP_NOT_CONVERGED = 1,  /* max_outer reached; x and info are still filled */
+  SSTEP_ERR_INVALID = 2,    /* bad argument or descriptor */
+  SSTEP_ERR_BREAKDOWN = 3,  /* Gram diagonal <= 0 or non-finite (W_ii, pAp) */
+  SSTEP_ERR_NONFINITE = 4,  /* non-finite residual norm */
+  SSTEP_ERR_CUDA = 5,       /* a CUDA runtime call failed */
+  SSTEP_ERR_OOM = 6,        /* device allocation failed */
+  SSTEP_ERR_UNSUPPORTED = 7 /* valid request this build does not implement */
+} sstep_status;
+
+/* ------------------------------------------------------------------ operator A */
+enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1 };
+
+/* The SPD matrix A of Ax = b (Section 1).
+ * CSR: n rows, rowptr[n+1] (int64), colind[nnz] (int32, 0-based), vals[nnz]; device or host
+ *      pointers; copied into library-owned device memory at set-up (the caller may free them
+ *      afterwards).  Each row must hold its diagonal entry when the Jacobi preconditioner is used.
+ * STENCIL: matrix-free finite-difference operator on the interior points of an nx*ny*nz grid
+ *      (row index i + nx*(j + ny*k); Dirichlet neighbours dropped).  points = 5 (2D, nz = 1),
+ *      7 or 27 (3D).  weights: NULL for the Poisson weights (diagonal 4 / 6 / 26, neighbours -1),
+ *      or `points` host doubles in the order of increasing linear offset (for 7 points:
+ *      -z, -y, -x, centre, +x, +y, +z; for 27: dz-major, then dy, then dx). */
+typedef struct {
+  int kind;
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* vals;
+  int64_t nnz;
+  int nx, ny, nz, points;
+  const double* weights;
+} sstep_matrix;
+
+/* ------------------------------------------------------------------ preconditioner M */
+/* The paper treats M^{-1} as a black box (Section 4): NONE is M = I (the CG-S runs of
+ * Section 6.1), JACOBI is M = diag(A). */
+enum { SSTEP_PREC_NONE = 0, SSTEP_PREC_JACOBI = 1 };
+typedef struct {
+  int kind;
+} sstep_precond;
+
+/* ------------------------------------------------------------------ options */
+enum {
+  SSTEP_ALGO_ONESYNC = 0, /* Algorithm 1 with the Gram blocks of [Q_k, Z_{k+1}] formed in one
+                             reduction per outer iteration (W_{k+1} assembled from them and beta) */
+  SSTEP_ALGO_LITERAL = 1, /* Algorithm 1 line by line: W, b1 after the update, b2 after the MPK */
+  SSTEP_ALGO_PCG = 2      /* classical preconditioned CG (Hestenes-Stiefel), the comparator */
+};
+enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1 };
+
+typedef struct {
+  int s;              /* step size, 1 <= s <= 16 (Algorithm 1 "step size s") */
+  int sweeps;         /* nu, FGS sweeps per reduced solve (Algorithm 1 "number of FGS sweeps") */
+  double rtol;        /* tau: stop when ||r|| <= tau ||b|| (Algorithm 1, line 9) */
+  int max_outer;      /* k_max (outer iterations; PCG: iterations) */
+  int algo;           /* SSTEP_ALGO_* */
+  int gram_solver;    /* SSTEP_GRAM_FGS, or SSTEP_GRAM_CHOLESKY (exact reduced solves, Section 3.3) */
+  int power_iters;    /* power-method cap (Section 2: 50) */
+  double power_tol;   /* power-method relative-change stop (Section 2: 1e-3); <= 0 runs power_iters */
+  double lambda_min;  /* lower end of the Chebyshev interval (Section 2 uses 0); < 0 = Gershgorin bound */
+  double lambda_max;  /* > 0: used as given; otherwise estimated by the power method at set-up */
+  const double* power_v0; /* start vector of the power method (n doubles, device or host); NULL =
+                             U[-1,1) from SplitMix64 with seed 1 in index order */
+  int check_every;    /* outer iterations between host reads of the stop flag (0 = automatic) */
+} sstep_opts;
+
+typedef struct {
+  int status;             /* sstep_status of the solve */
+  int outer_iters;        /* executed x/r updates (outer iterations; PCG: iterations) */
+  int inner_equiv;        /* outer_iters * s (PCG: iterations) */
+  double relres;          /* ||r|| / ||b|| of the recursively updated residual at exit */
+  double relres_true;     /* ||b - A x|| / ||b|| at exit */
+  double lambda_max;      /* lambda_max used for the Chebyshev basis */
+  double lambda_min;      /* lambda_min used */
+  double ms_setup;        /* wall time of sstep_setup (operator copy, Jacobi, power method) */
+  double ms_solve;        /* wall time of the solve, host-to-host */
+  long long launches;     /* kernels launched by the solve (graph replays count every node,
+                             including launches after convergence that return at entry) */
+} sstep_info;
+
+/* Fill *o with the defaults: s = 4, sweeps = 2, rtol = 1e-8, max_outer = 10000, one-sync,
+ * FGS, power_iters = 50, power_tol = 1e-3, lambda_min = 0, lambda_max = 0 (estimate). */
+SSTEP_API void sstep_default_opts(sstep_opts* o);
+
+/* Build a solver for A (Section 2: "estimate lambda_max once, before starting"): copies A to the
+ * device, forms M^{-1}, runs the power method on M^{-1}A when o->lambda_max <= 0, derives the
+ * Chebyshev scalars c_alpha = 2/(lmax-lmin), c_sigma = (lmax+lmin)/(lmax-lmin), c_gamma = 1, and
+ * allocates the basis blocks Z, AZ, Q, AQ (4 s vectors) and x, r, b buffers.
+ * nsys must be 1.  stream: cudaStream_t passed as void*.  On error *out is NULL. */
+SSTEP_API sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,
+                         const sstep_opts* o, void* stream, sstep_handle* out);
+
+/* Solve A x = b (Algorithm 1, or classical PCG when algo = SSTEP_ALGO_PCG).
+ * b: n doubles (device or host).  x: n doubles (device or host), x^(0) on entry, solution on
+ * exit.  b = 0 gives x = 0 with 0 iterations; ||r^(0)|| <= tau ||b|| gives 0 iterations.
+ * info may be NULL.  Returns the solve status (also in info->status). */
+SSTEP_API sstep_status sstep_solve(sstep_handle h, const double* b, double* x, sstep_info* info);
+
+/* Solve nrhs systems with the same A one after another: b[i], x[i] as in sstep_solve;
+ * infos may be NULL or hold nrhs entries.  Returns the first non-OK status, else SSTEP_OK. */
+SSTEP_API sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const double* const* b,
+                                 double* const* x, sstep_info* infos);
+
+/* Release everything the handle owns (NULL is accepted). */
+SSTEP_API sstep_status sstep_free(sstep_handle h);
+
+/* Static description of a status code. */
+SSTEP_API const char* sstep_status_string(sstep_status s);
+/* Description of the last failure on the calling thread ("" if none). */
+SSTEP_API const char* sstep_last_error(void);
+
+/* ------------------------------------------------------------------ hot-path steps
+ * The steps of one outer iteration, exposed one by one on an existing handle (its operator,
+ * preconditioner, Chebyshev scalars and stream).  All pointers are device pointers with
+ * leading dimension n; the calls are asynchronous on the handle's stream. */
+
+/* Algorithm 2 (MPK for the Chebyshev basis): from residual r, write
+ * Z = [z_1 .. z_s] with z_j = T_{j-1}(A_hat) M^{-1} r and AZ = [A z_1 .. A z_s]
+ * (the columns 2..s+1 of the paper's P; column 1 of P is r itself).
+ * s_override in 1..16 replaces the handle's s (0 keeps it).  The recurrence runs on z
+ * directly: z_{q+1} = 2 c_alpha M^{-1}(A z_q) - 2 c_sigma z_q - c_gamma z_{q-1}. */
+SSTEP_API sstep_status sstep_mpk(sstep_handle h, const double* r, double* Z, double* AZ, int s_override);
+
+/* Block Gram products (Algorithm 1 lines 5 and 12): for e = 0..ne-1,
+ * out[e] = sum_i L[pairs[2e]][i] * R[pairs[2e+1]][i], i < n.  L: nl device pointers to n-vectors,
+ * R: nr device pointers; pairs: 2*ne host ints; out: ne doubles (device).  nl, nr <= 40,
+ * ne <= 512.  Deterministic: the same inputs and launch give bit-identical sums.
+ * stream: cudaStream_t as void*. */
+SSTEP_API sstep_status sstep_block_gram(int64_t n, int nl, const double* const* L, int nr,
+                              const double* const* R, int ne, const int* pairs, double* out,
+                              void* stream);
+
+/* nu FGS sweeps from 0 on W X = B for nrhs right-hand sides (Section 3.1, Eq. fgs-iteration on
+ * W itself: W = D + L_W + L_W^T).  W: s x s column-major, B and X: s x nrhs column-major, all
+ * device pointers; 1 <= s <= 16, 1 <= nrhs <= 16.  Breakdown (W_ii <= 0 or non-finite) is
+ * written to *status_dev (device int, may be NULL) as SSTEP_ERR_BREAKDOWN, else SSTEP_OK.
+ * solver = SSTEP_GRAM_CHOLESKY solves exactly instead.  stream: cudaStream_t as void*. */
+SSTEP_API sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu, int solver,
+                       double* X, int* status_dev, void* stream);
+
+/* Algorithm 1 lines 7-8 and 15 fused: with beta (s x s) and alpha (s) in device memory,
+ * Q <- Z + Q beta, AQ <- AZ + AQ beta, x <- x + Q alpha, r <- r - AQ alpha (new Q, AQ),
+ * and *rr_out = ||r||^2 (device double).  beta may be NULL (first outer iteration: Q <- Z,
+ * AQ <- AZ).  Blocks have leading dimension n. */
+SSTEP_API sstep_status sstep_block_update(sstep_handle h, const double* Z, const double* AZ, double* Q,
+                                double* AQ, const double* alpha, const double* beta, double* x,
+                                double* r, double* rr_out, int s_override);
+
+/* y = A x with the handle's operator (device pointers). */
+SSTEP_API sstep_status sstep_spmv(sstep_handle h, const double* x, double* y);
+
+/* lambda_max and lambda_min used by the handle, and the Chebyshev scalars of Section 2. */
+SSTEP_API sstep_status sstep_get_basis_info(sstep_handle h, double* lambda_min, double* lambda_max,
+                                  double* c_alpha, double* c_sigma, double* c_gamma,
+                                  int* power_iters_run);
+
+/* Residual history of the last solve: relres[k] = ||r^(k)|| / ||b|| for k = 0..iters
+ * (recursively updated residual after each outer iteration).  relres: host array of maxlen
+ * doubles; *count receives the number written. */
+SSTEP_API sstep_status sstep_get_history(sstep_handle h, double* relres, int maxlen, int* count);
+
+/* Device time per phase of one outer iteration, measured with CUDA events on the handle's
+ * stream: starting from x = 0 for right-hand side b (device or host, n doubles), runs the first
+ * outer iteration and then `iters` more without a stop test, launched one by one.  ms (host,
+ * 4 doubles) receives the averages per outer iteration: PCG-S one-sync: [MPK (all s steps),
+ * Gram reduction + reduced solves, block update, sum]; PCG: [A p and p^T A p, x/r update with
+ * r^T z, direction update, sum].  The handle's own x, r and basis blocks are overwritten; the
+ * literal form returns SSTEP_ERR_UNSUPPORTED. */
+SSTEP_API sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSTEP_H */

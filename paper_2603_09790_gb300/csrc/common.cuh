@@ -1,0 +1,281 @@
+// common.cuh -- internal definitions shared by the translation units of libsstep.so.
+// Device-side control block, deterministic grid reductions, operator descriptors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sstep.h"
+
+namespace sstep {
+
+constexpr int kMaxS = 16;          // largest step size
+constexpr int kMaxEntries = 1088;  // largest number of Gram entries per reduction (s = 16, full)
+constexpr int kMaxGramVecs = 40;   // largest number of vectors on one side of a Gram product
+constexpr int kThreads = 256;      // threads per CTA of the streaming kernels
+constexpr int kMaxCtas = 2048;     // upper bound on CTAs of a reduction kernel (partials buffer)
+constexpr int kNumTickets = 8;
+
+enum Ticket { TK_GRAM = 0, TK_UPDATE = 1, TK_OP = 2, TK_NORM = 3, TK_PCG1 = 4, TK_PCG2 = 5 };
+
+// Reduced-system mode of the Gram kernel's tail (run by the last CTA after the reduction).
+enum GramMode {
+  GM_SUMS = 0,           // only write the reduced sums
+  GM_ONESYNC_FIRST = 1,  // k = 0: W = Z^T AZ, b1 = Z^T r, alpha = FGS(W, b1)
+  GM_ONESYNC = 2,        // beta = FGS(W_k, -Q^T AZ); W_{k+1} = ...; alpha = FGS(W_{k+1}, b1)
+  GM_LITERAL_W = 3,      // W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)          (lines 5-6)
+  GM_LITERAL_B2 = 4      // beta = FGS(W, -Q^T AZ)                              (lines 12-13)
+};
+
+// Update kernel modes (Algorithm 1 lines 7-8 and 15).
+enum UpdMode {
+  UM_FIRST = 0,  // Q = Z, AQ = AZ, then x += Q alpha, r -= AQ alpha
+  UM_FUSED = 1,  // Q = Z + Q beta, AQ = AZ + AQ beta, then x += Q alpha, r -= AQ alpha
+  UM_XR = 2,     // x += Q alpha, r -= AQ alpha only                  (literal lines 7-8)
+  UM_QAQ = 3     // Q = Z + Q beta, AQ = AZ + AQ beta only            (literal line 15)
+};
+
+// Device-resident control block of one solve.  Written only by the last CTA of a reduction
+// kernel (or by single-CTA kernels); read at kernel entry by every CTA of later kernels.
+struct Ctrl {
+  double nb2;        // ||b||^2
+  double rtol2;      // rtol^2
+  double tol2;       // (rtol ||b||)^2, set by the initial-residual kernel
+  double rr;         // ||r||^2 of the current residual
+  double rr0;        // ||r^(0)||^2
+  double rz;         // PCG: r^T z
+  double pcg_alpha, pcg_beta;
+  double lam, inv_scale, power_tol;  // power method: estimate, 1/previous estimate, stop tolerance
+  int power_done, power_iters, power_max;
+  int done;          // 1: stop (converged, failed or capped)
+  int status;        // sstep_status
+  int iters;         // executed updates
+  int max_iters;
+  int s, nu, solver, full_gram;
+  int first_pending; // 1 while the next outer iteration is the first one
+  double alpha[kMaxS];
+  double beta[kMaxS * kMaxS];    // column-major s x s
+  double W[kMaxS * kMaxS];       // W_k used for alpha_k (and for beta_k)
+  double sums[kMaxEntries];      // reduced Gram sums of the last reduction
+  unsigned int ticket[kNumTickets];
+};
+
+// ---------------------------------------------------------------- operator descriptors
+
+struct StencilOp {
+  int nx, ny, nz, points;
+  int poisson;       // 1: off-diagonal weights all -1 (fast path)
+  double w[27];      // weights in order of increasing linear offset
+  double wc;         // centre weight
+};
+
+struct CsrOp {
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* vals;
+};
+
+// Preconditioner: dinv == nullptr means the uniform scalar dinv_u (M = I gives dinv_u = 1).
+struct Prec {
+  const double* dinv;
+  double dinv_u;
+};
+
+__device__ __forceinline__ double prec_d(const Prec& M, int64_t i) {
+  return M.dinv ? __ldg(M.dinv + i) : M.dinv_u;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0.  Fixed order.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* NV * 32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sh[k * 32 + lane] : 0.0;
+      v[k] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic grid reduction: every CTA contributes NV values; the last CTA to arrive sums
+// the per-CTA partials in a fixed order and returns true (result in `tot`, valid in all of
+// its threads).  No CTA waits for another: the last arriving CTA does the final step.
+template <int NV>
+__device__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* ticket,
+                              double (&tot)[NV]) {
+  __shared__ double sh[NV * 32];
+  __shared__ bool last;
+  // Grids may be 1D, 2D or 3D: partials are indexed by the linear block index.
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (size_t)b * NV + k);
+  }
+  block_sum<NV>(acc, sh);
+  __shared__ double res[NV];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) res[k] = acc[k];
+    *ticket = 0u;  // re-arm for the next launch (stream order separates launches)
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = res[k];
+  return true;
+}
+
+// Stop test of Algorithm 1 line 9 on ||r||^2 (also used by PCG), executed by one thread.
+__device__ __forceinline__ void stop_test(Ctrl* c, double rr) {
+  c->rr = rr;
+  c->iters += 1;
+  if (!(rr == rr) || rr > 1.79e308) {
+    c->status = SSTEP_ERR_NONFINITE;
+    c->done = 1;
+  } else if (rr <= c->tol2) {
+    c->status = SSTEP_OK;
+    c->done = 1;
+  } else if (c->iters >= c->max_iters) {
+    c->status = SSTEP_NOT_CONVERGED;
+    c->done = 1;
+  }
+}
+
+}  // namespace sstep
+
+// ---------------------------------------------------------------- host-side launchers
+// (defined in the kernel translation units, called by the API translation unit)
+namespace sstep {
+
+struct OpDesc {
+  int kind;  // SSTEP_MATRIX_*
+  StencilOp st;
+  CsrOp csr;
+  int64_t n;
+};
+
+// Epilogue selector of the operator kernels.
+enum OpEpi {
+  EP_SPMV = 0,      // y = A u
+  EP_MPK = 1,       // Az = A u;  znext = c1 M^{-1}(A u) - c2 u - c3 zprev
+  EP_MPK_FIRST = 2, // u = r: z1 = M^{-1} r;  Az = A z1;  z2 = c1 M^{-1} Az - c2 z1
+  EP_RESID = 3,     // r = b - A u; reductions ||r||^2, ||b||^2   (initial residual)
+  EP_POWER = 4,     // y = scale * M^{-1} A u; reduction ||y||^2
+  EP_PCG_AP = 5,    // Ap = A p; reduction p^T Ap
+  EP_TRUERES = 6    // reduction ||b - A u||^2 (no store)
+};
+
+struct EpiArgs {
+  int epi;
+  const double* u;      // operator input
+  double* y;            // A u (stored when non-null)
+  double* znext;        // MPK: next basis vector
+  double* z1;           // MPK first step: z1 output
+  const double* zprev;  // MPK: z_{q-1} (null on the second basis vector)
+  const double* b;      // residual epilogues
+  double c1, c2, c3;    // recurrence coefficients
+  Prec M;
+  Ctrl* ctrl;
+  double* partials;
+};
+
+cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st);
+
+struct GramArgs {
+  int64_t n;
+  int nl, nr, ne;
+  const double* L[kMaxGramVecs];
+  const double* R[kMaxGramVecs];
+  unsigned short pairs[kMaxEntries];  // (l << 8) | r
+  int mode;           // GramMode
+  Ctrl* ctrl;
+  double* partials;
+  double* out;        // optional copy of the sums (GM_SUMS)
+};
+cudaError_t launch_gram(const GramArgs& g, cudaStream_t st);
+cudaError_t gram_init();  // sets the Gram kernels' dynamic shared-memory limit (call outside capture)
+// Pair list of a Gram mode (returns ne; fills nl, nr), and the CTA count of launch_gram.
+int gram_pairs(int mode, int s, int full, unsigned short* pairs, int* nl, int* nr);
+int gram_ctas();
+int update_ctas(int64_t n);
+int pcg_ctas(int64_t n);
+int gershgorin_ctas(int64_t n);
+
+struct UpdArgs {
+  int64_t n, ld;
+  int s, mode;
+  const double* Z;
+  const double* AZ;
+  double* Q;
+  double* AQ;
+  double* x;
+  double* r;
+  const double* alpha;  // device (s)
+  const double* beta;   // device (s x s, column-major)
+  Ctrl* ctrl;           // stop test + rr (may be null: then rr_out)
+  double* rr_out;
+  double* partials;
+  unsigned int* ticket;
+  double* hist;         // optional ||r||/||b|| history
+};
+cudaError_t launch_update(const UpdArgs& u, cudaStream_t st);
+
+cudaError_t launch_fgs_standalone(int s, const double* W, int nrhs, const double* B, int nu,
+                                  int solver, double* X, int* status_dev, cudaStream_t st);
+
+struct PcgArgs {
+  int64_t n;
+  double* x;
+  double* r;
+  double* p;
+  const double* Ap;
+  Prec M;
+  Ctrl* ctrl;
+  double* partials;
+  double* hist;
+};
+cudaError_t launch_pcg_update(const PcgArgs& a, cudaStream_t st);   // x, r, z, rz, rr, beta
+cudaError_t launch_pcg_pdir(const PcgArgs& a, cudaStream_t st);     // p = z + beta p
+cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);     // z = M^-1 r, p = z, rz
+
+cudaError_t launch_fill_splitmix(double* v, int64_t n, uint64_t seed, cudaStream_t st);
+cudaError_t launch_jacobi_csr(const CsrOp& A, double* dinv, int* bad, cudaStream_t st);
+cudaError_t launch_csr_check(const CsrOp& A, int64_t nnz, int* bad, cudaStream_t st);
+cudaError_t launch_norm2(const double* v, int64_t n, Ctrl* c, double* partials, int which,
+                         cudaStream_t st);
+cudaError_t launch_gershgorin_csr(const CsrOp& A, int jacobi, double* out_min, cudaStream_t st);
+
+int operator_grid_ctas(const OpDesc& A);  // CTAs of one operator launch (partials sizing)
+
+}  // namespace sstep

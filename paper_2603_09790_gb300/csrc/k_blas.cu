@@ -1,0 +1,764 @@
+// k_blas.cu -- tall-skinny block kernels of PCG-S and the PCG comparator.
+//
+//  * k_gram: one pass over n rows forms every requested dot product L_a^T R_b (Algorithm 1
+//    lines 5 and 12-13; in the one-reduction form, all blocks of [Q_k Z_{k+1}]^T
+//    [AQ_k AZ_{k+1} r]).  Rows are staged in shared memory in tiles of 256; each thread owns a
+//    few (entry, row-phase) slots, so every FP64 multiply-add of the product is issued once.
+//    Per-CTA partials are summed in a fixed order by the last CTA to finish (no grid barrier,
+//    bit-reproducible), and that same CTA then solves the reduced systems: FGS sweeps of
+//    Section 3.1 (Eq. fgs-iteration) for beta and alpha, and the assembly of W_{k+1}.
+//  * k_update: Algorithm 1 lines 7-8 and 15 in one pass: Q <- Z + Q beta, AQ <- AZ + AQ beta,
+//    x <- x + Q alpha, r <- r - AQ alpha, ||r||^2 and the stop test of line 9.
+//  * PCG vector kernels (x/r/z update with r^T z and ||r||^2; direction update).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace sstep {
+
+namespace {
+
+constexpr int kGramRows = 256;  // rows per shared-memory tile
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// ---------------------------------------------------------------- reduced-system tail
+
+// nu forward Gauss-Seidel sweeps from x = 0 on W x = b (W: s x s column-major in shared
+// memory), Eq. (fgs-iteration) in its plain form on W.  One thread per right-hand side.
+__device__ void fgs_column(int s, const double* W, const double* rinv, const double* b, int nu,
+                           double* x, int stride) {
+  for (int i = 0; i < s; ++i) x[i * stride] = 0.0;
+  for (int sw = 0; sw < nu; ++sw) {
+    for (int i = 0; i < s; ++i) {
+      double a0 = b[i], a1 = 0.0;
+      int j = 0;
+      for (; j + 1 < s; j += 2) {
+        if (j != i) a0 = fma(-W[i + j * s], x[j * stride], a0);
+        if (j + 1 != i) a1 = fma(-W[i + (j + 1) * s], x[(j + 1) * stride], a1);
+      }
+      if (j < s && j != i) a0 = fma(-W[i + j * s], x[j * stride], a0);
+      x[i * stride] = (a0 + a1) * rinv[i];
+    }
+  }
+}
+
+// Dense Cholesky factorisation in place (lower triangle of L, column-major), one thread.
+__device__ bool chol_factor(int s, const double* W, double* L) {
+  for (int j = 0; j < s; ++j) {
+    double d = W[j + j * s];
+    for (int k = 0; k < j; ++k) d -= L[j + k * s] * L[j + k * s];
+    if (!(d > 0.0) || d > 1.79e308) return false;
+    const double ljj = sqrt(d);
+    L[j + j * s] = ljj;
+    for (int i = j + 1; i < s; ++i) {
+      double v = W[i + j * s];
+      for (int k = 0; k < j; ++k) v -= L[i + k * s] * L[j + k * s];
+      L[i + j * s] = v / ljj;
+    }
+  }
+  return true;
+}
+
+__device__ void chol_column(int s, const double* L, const double* b, double* x, int stride) {
+  double y[kMaxS];
+  for (int i = 0; i < s; ++i) {
+    double v = b[i];
+    for (int k = 0; k < i; ++k) v -= L[i + k * s] * y[k];
+    y[i] = v / L[i + i * s];
+  }
+  for (int i = s - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < s; ++k) v -= L[k + i * s] * x[k * stride];
+    x[i * stride] = v / L[i + i * s];
+  }
+}
+
+// Solve W X = B for nrhs columns (B, X column-major s x nrhs in shared memory) with nu FGS
+// sweeps or exactly (Cholesky).  Executed by the whole CTA; returns false on breakdown.
+__device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs, int nu,
+                              int solver, double* X, double* scratch /* s*s + s */) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    for (int i = 0; i < s; ++i) {
+      const double d = W[i + i * s];
+      if (!(d > 0.0) || d > 1.79e308) ok = 0;
+    }
+    for (int i = 0; i < s * s; ++i)
+      if (!(W[i] == W[i]) || fabs(W[i]) > 1.79e308) ok = 0;
+    if (ok) {
+      if (solver == SSTEP_GRAM_CHOLESKY) {
+        if (!chol_factor(s, W, scratch)) ok = 0;
+      } else {
+        for (int i = 0; i < s; ++i) scratch[s * s + i] = 1.0 / W[i + i * s];
+      }
+    }
+  }
+  __syncthreads();
+  if (!ok) return false;
+  if ((int)threadIdx.x < nrhs) {
+    const int c = threadIdx.x;
+    if (solver == SSTEP_GRAM_CHOLESKY) chol_column(s, scratch, B + c * s, X + c * s, 1);
+    else fgs_column(s, W, scratch + s * s, B + c * s, nu, X + c * s, 1);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Entry layout of the Gram reductions (shared by the host, which lists the pairs, and by the
+// tail, which reads them back).  Blocks are s x s; symmetric blocks keep i <= j only unless
+// `full` is set.
+struct Layout {
+  int s, full;
+  __host__ __device__ int nsym() const { return full ? s * s : s * (s + 1) / 2; }
+  __host__ __device__ int sym(int i, int j) const {  // index inside a symmetric block
+    if (full) return i + j * s;
+    if (i > j) { int t = i; i = j; j = t; }
+    return j * (j + 1) / 2 + i;  // packed upper triangle, column by column
+  }
+};
+
+// GM_ONESYNC entry order: G1 = Q^T AQ (sym), G2 = Q^T AZ (s^2), [G3 = Z^T AQ (s^2) if full],
+// G4 = Z^T AZ (sym), g5 = Q^T r (s), g6 = Z^T r (s).
+struct OneSyncIdx {
+  Layout L;
+  __host__ __device__ int g1(int i, int j) const { return L.sym(i, j); }
+  __host__ __device__ int g2(int i, int j) const { return L.nsym() + i + j * L.s; }
+  __host__ __device__ int g3(int i, int j) const {  // Z^T AQ, or (Q^T AZ)^T when not full
+    return L.full ? L.nsym() + L.s * L.s + i + j * L.s : g2(j, i);
+  }
+  __host__ __device__ int g4base() const { return L.nsym() + L.s * L.s * (L.full ? 2 : 1); }
+  __host__ __device__ int g4(int i, int j) const { return g4base() + L.sym(i, j); }
+  __host__ __device__ int g5(int i) const { return g4base() + L.nsym() + i; }
+  __host__ __device__ int g6(int i) const { return g5(L.s) + i; }
+  __host__ __device__ int count() const { return g6(L.s); }
+};
+
+// The tail: executed by the last CTA after the reduction, with the sums in shared memory.
+__device__ void gram_tail(const GramArgs& g, const double* sums, double* sh) {
+  Ctrl* c = g.ctrl;
+  const int s = c->s, nu = c->nu, solver = c->solver;
+  const Layout L{s, c->full_gram};
+  double* W = sh;               // s*s
+  double* Bm = W + s * s;       // s*s  right-hand sides
+  double* X = Bm + s * s;       // s*s  solutions
+  double* T = X + s * s;        // s*s
+  double* G1 = T + s * s;       // s*s
+  double* G2 = G1 + s * s;      // s*s
+  double* G3 = G2 + s * s;      // s*s
+  double* b1 = G3 + s * s;      // s
+  double* scr = b1 + s;         // s*s + s
+  const int tid = threadIdx.x;
+  bool ok = true;
+  if (g.mode == GM_ONESYNC_FIRST || g.mode == GM_LITERAL_W) {
+    // W = V^T AV (V = Z_0 or Q_k), b1 = V^T r;  alpha = FGS(W, b1)       (lines 5-6)
+    for (int e = tid; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      W[e] = sums[L.sym(i, j)];
+    }
+    for (int i = tid; i < s; i += blockDim.x) b1[i] = sums[L.nsym() + i];
+    __syncthreads();
+    ok = reduced_solve(s, W, b1, 1, nu, solver, X, scr);
+    if (ok) {
+      for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = X[i];
+      for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
+    }
+  } else if (g.mode == GM_LITERAL_B2) {
+    // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (lines 12-13)
+    for (int e = tid; e < s * s; e += blockDim.x) {
+      W[e] = c->W[e];
+      Bm[e] = -sums[e];  // entry e = i + j*s is q_i^T az_j
+    }
+    __syncthreads();
+    ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
+    if (ok)
+      for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
+  } else if (g.mode == GM_ONESYNC) {
+    const OneSyncIdx I{L};
+    for (int e = tid; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      W[e] = c->W[e];                 // W_k (the matrix alpha_k was computed with)
+      G1[e] = sums[I.g1(i, j)];       // Q_k^T AQ_k
+      G2[e] = sums[I.g2(i, j)];       // Q_k^T AZ_{k+1}
+      G3[e] = sums[I.g3(i, j)];       // Z_{k+1}^T AQ_k
+      Bm[e] = -G2[e];
+    }
+    __syncthreads();
+    // beta_k = FGS(W_k, -Q_k^T AZ_{k+1})                                   (lines 12-13)
+    ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
+    if (ok) {
+      for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
+      // T = G1 beta
+      for (int e = tid; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        double v = 0.0;
+        for (int l = 0; l < s; ++l) v = fma(G1[i + l * s], X[l + j * s], v);
+        T[e] = v;
+      }
+      __syncthreads();
+      // W_{k+1} = (Z + Q beta)^T (AZ + AQ beta) = G4 + G3 beta + beta^T G2 + beta^T G1 beta
+      for (int e = tid; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        double v = sums[I.g4(i, j)];
+        for (int l = 0; l < s; ++l) {
+          v = fma(G3[i + l * s], X[l + j * s], v);
+          v = fma(X[l + i * s], G2[l + j * s], v);
+          v = fma(X[l + i * s], T[l + j * s], v);
+        }
+        Bm[e] = v;  // reuse as W_{k+1}
+      }
+      // b1 = Q_{k+1}^T r = Z^T r + beta^T Q^T r
+      for (int i = tid; i < s; i += blockDim.x) {
+        double v = sums[I.g6(i)];
+        for (int l = 0; l < s; ++l) v = fma(X[l + i * s], sums[I.g5(l)], v);
+        b1[i] = v;
+      }
+      __syncthreads();
+      for (int e = tid; e < s * s; e += blockDim.x) W[e] = Bm[e];
+      __syncthreads();
+      // alpha_{k+1} = FGS(W_{k+1}, b1)                                     (lines 5-6)
+      ok = reduced_solve(s, W, b1, 1, nu, solver, T, scr);
+      if (ok) {
+        for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = T[i];
+        for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && !ok) {
+    c->status = SSTEP_ERR_BREAKDOWN;
+    c->done = 1;
+  }
+}
+
+// ---------------------------------------------------------------- Gram kernel
+
+template <int EPT>
+__global__ void __launch_bounds__(kThreads) k_gram(GramArgs g, int nch, int rp) {
+  if (g.ctrl && g.ctrl->done) return;
+  extern __shared__ double sm[];
+  const int ldS = kGramRows + 1;  // odd stride: columns fall in different banks
+  const int ncols = g.nl + g.nr;
+  const int tid = threadIdx.x;
+  const int ch = tid % nch, ph = tid / nch;
+  const bool active = ph < rp;
+  int la[EPT], ra[EPT];
+  double acc[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int e = ch * EPT + k;
+    acc[k] = 0.0;
+    if (e < g.ne) {
+      la[k] = g.pairs[e] >> 8;
+      ra[k] = g.nl + (g.pairs[e] & 255);
+    } else {
+      la[k] = ra[k] = -1;
+    }
+  }
+  for (int64_t tile = blockIdx.x; tile * kGramRows < g.n; tile += gridDim.x) {
+    const int64_t p0 = tile * kGramRows;
+    const int rows = (int)(g.n - p0 < kGramRows ? g.n - p0 : kGramRows);
+    for (int cix = 0; cix < ncols; ++cix) {
+      const double* v = cix < g.nl ? g.L[cix] : g.R[cix - g.nl];
+      for (int p = tid; p < kGramRows; p += blockDim.x)
+        sm[cix * ldS + p] = p < rows ? __ldg(v + p0 + p) : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+      for (int p = ph; p < rows; p += rp) {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k)
+          if (la[k] >= 0) acc[k] = fma(sm[la[k] * ldS + p], sm[ra[k] * ldS + p], acc[k]);
+      }
+    }
+    __syncthreads();
+  }
+  // CTA reduction over row phases, in phase order.
+  double* red = sm;  // rp * ne doubles
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = ch * EPT + k;
+      if (e < g.ne) red[ph * g.ne + e] = acc[k];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < g.ne; e += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < rp; ++q) v += red[q * g.ne + e];
+    g.partials[(size_t)blockIdx.x * g.ne + e] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(&g.ctrl->ticket[TK_GRAM], 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // Fixed-order sum over CTAs: entry e is summed by threads e, e+ne, ... over CTA slices,
+  // then the slices are added in slice order.
+  const int per = max(1, (int)blockDim.x / g.ne);  // threads per entry
+  double* part = sm;                                // per * ne
+  double* sums = sm + per * g.ne;                   // ne
+  if (tid < per * g.ne) {
+    const int e = tid % g.ne, sl = tid / g.ne;
+    const int nb = gridDim.x;
+    const int b0 = (int)((int64_t)nb * sl / per), b1 = (int)((int64_t)nb * (sl + 1) / per);
+    double v = 0.0;
+    for (int b = b0; b < b1; ++b) v += __ldcg(g.partials + (size_t)b * g.ne + e);
+    part[sl * g.ne + e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < g.ne; e += blockDim.x) {
+    double v = 0.0;
+    for (int sl = 0; sl < per; ++sl) v += part[sl * g.ne + e];
+    sums[e] = v;
+  }
+  __syncthreads();
+  if (tid == 0) g.ctrl->ticket[TK_GRAM] = 0u;
+  for (int e = tid; e < g.ne; e += blockDim.x) {
+    g.ctrl->sums[e] = sums[e];
+    if (g.out) g.out[e] = sums[e];
+  }
+  if (g.mode != GM_SUMS) gram_tail(g, sums, sums + g.ne);
+}
+
+// ---------------------------------------------------------------- fused block update
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(kThreads) k_update(UpdArgs u) {
+  if (u.ctrl && u.ctrl->done) return;
+  __shared__ double sb[S * S], sa[S];
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = u.beta ? u.beta[e] : 0.0;
+  for (int e = threadIdx.x; e < S; e += blockDim.x) sa[e] = u.alpha ? u.alpha[e] : 0.0;
+  __syncthreads();
+  double rr = 0.0;
+  const int64_t ld = u.ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < u.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double q[S], aq[S];
+    if constexpr (MODE == UM_FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q[j] = __ldg(u.Z + j * ld + i);
+        aq[j] = __ldg(u.AZ + j * ld + i);
+        u.Q[j * ld + i] = q[j];
+        u.AQ[j * ld + i] = aq[j];
+      }
+    } else if constexpr (MODE == UM_FUSED || MODE == UM_QAQ) {
+      double qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = u.Q[l * ld + i];
+        ao[l] = u.AQ[l * ld + i];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        double vq = __ldg(u.Z + j * ld + i), va = __ldg(u.AZ + j * ld + i);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          vq = fma(qo[l], sb[l + j * S], vq);
+          va = fma(ao[l], sb[l + j * S], va);
+        }
+        q[j] = vq;
+        aq[j] = va;
+        u.Q[j * ld + i] = vq;
+        u.AQ[j * ld + i] = va;
+      }
+    } else {  // UM_XR
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q[j] = u.Q[j * ld + i];
+        aq[j] = u.AQ[j * ld + i];
+      }
+    }
+    if constexpr (MODE != UM_QAQ) {
+      double dx = 0.0, dr = 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        dx = fma(q[j], sa[j], dx);
+        dr = fma(aq[j], sa[j], dr);
+      }
+      u.x[i] += dx;
+      const double ri = u.r[i] - dr;
+      u.r[i] = ri;
+      rr = fma(ri, ri, rr);
+    }
+  }
+  if constexpr (MODE != UM_QAQ) {
+    double v[1] = {rr}, tot[1];
+    if (grid_sum_last<1>(v, u.partials, u.ticket, tot)) {
+      if (threadIdx.x == 0) {
+        if (u.ctrl) {
+          stop_test(u.ctrl, tot[0]);
+          if (u.hist) u.hist[u.ctrl->iters] = sqrt(tot[0] / u.ctrl->nb2);
+        }
+        if (u.rr_out) *u.rr_out = tot[0];
+      }
+    }
+  }
+}
+
+template <int S>
+cudaError_t launch_update_s(const UpdArgs& u, int grid, cudaStream_t st) {
+  switch (u.mode) {
+    case UM_FIRST: k_update<S, UM_FIRST><<<grid, kThreads, 0, st>>>(u); break;
+    case UM_FUSED: k_update<S, UM_FUSED><<<grid, kThreads, 0, st>>>(u); break;
+    case UM_XR: k_update<S, UM_XR><<<grid, kThreads, 0, st>>>(u); break;
+    case UM_QAQ: k_update<S, UM_QAQ><<<grid, kThreads, 0, st>>>(u); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- standalone reduced solve
+
+__global__ void k_fgs_standalone(int s, const double* W, int nrhs, const double* B, int nu,
+                                 int solver, double* X, int* status) {
+  __shared__ double sh[5 * kMaxS * kMaxS + 2 * kMaxS];
+  double* Ws = sh;
+  double* Bs = Ws + s * s;
+  double* Xs = Bs + s * nrhs;
+  double* scr = Xs + s * nrhs;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) Ws[e] = W[e];
+  for (int e = threadIdx.x; e < s * nrhs; e += blockDim.x) Bs[e] = B[e];
+  __syncthreads();
+  const bool ok = reduced_solve(s, Ws, Bs, nrhs, nu, solver, Xs, scr);
+  for (int e = threadIdx.x; e < s * nrhs; e += blockDim.x) X[e] = ok ? Xs[e] : 0.0;
+  if (threadIdx.x == 0 && status) *status = ok ? SSTEP_OK : SSTEP_ERR_BREAKDOWN;
+}
+
+// ---------------------------------------------------------------- PCG vector kernels
+
+// x += alpha p; r -= alpha Ap; z = M^{-1} r; reductions r^T z and ||r||^2; then the stop
+// test and beta = (r^T z)_new / (r^T z)_old in the last CTA.
+__global__ void __launch_bounds__(kThreads) k_pcg_update(PcgArgs a) {
+  if (a.ctrl->done) return;
+  const double al = a.ctrl->pcg_alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = a.p[i];
+    a.x[i] = fma(al, pi, a.x[i]);
+    const double ri = fma(-al, __ldg(a.Ap + i), a.r[i]);
+    a.r[i] = ri;
+    const double zi = prec_d(a.M, i) * ri;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  double v[2] = {rz, rr}, tot[2];
+  if (grid_sum_last<2>(v, a.partials, &a.ctrl->ticket[TK_PCG2], tot)) {
+    if (threadIdx.x == 0) {
+      Ctrl* c = a.ctrl;
+      stop_test(c, tot[1]);
+      if (a.hist) a.hist[c->iters] = sqrt(tot[1] / c->nb2);
+      c->pcg_beta = tot[0] / c->rz;
+      c->rz = tot[0];
+    }
+  }
+}
+
+// p = M^{-1} r + beta p
+__global__ void __launch_bounds__(kThreads) k_pcg_pdir(PcgArgs a) {
+  if (a.ctrl->done) return;
+  const double be = a.ctrl->pcg_beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a.p[i] = fma(be, a.p[i], prec_d(a.M, i) * a.r[i]);
+}
+
+// z = M^{-1} r; p = z; rz = r^T z  (after the initial residual)
+__global__ void __launch_bounds__(kThreads) k_pcg_init(PcgArgs a) {
+  if (a.ctrl->done) return;
+  double rz = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = a.r[i];
+    const double zi = prec_d(a.M, i) * ri;
+    a.p[i] = zi;
+    rz = fma(ri, zi, rz);
+  }
+  double v[1] = {rz}, tot[1];
+  if (grid_sum_last<1>(v, a.partials, &a.ctrl->ticket[TK_PCG2], tot)) {
+    if (threadIdx.x == 0) a.ctrl->rz = tot[0];
+  }
+}
+
+// ---------------------------------------------------------------- utilities
+
+// U[-1,1) from SplitMix64 (Steele, Lea, Flood 2014): output k mixes seed + (k+1) * golden gamma.
+__global__ void k_fill_splitmix(double* v, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    v[i] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+  }
+}
+
+// CSR sanity: rowptr[0] = 0, rowptr[n] = nnz, rowptr non-decreasing, 0 <= colind < n.
+// Every read is clamped to the arrays' extents, so bad input only sets *bad.
+__global__ void k_csr_check(CsrOp A, int64_t nnz, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+    if ((i == 0 && k0 != 0) || (i == A.n - 1 && k1 != nnz) || k0 < 0 || k1 < k0 || k1 > nnz) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = A.colind[k];
+      if (c < 0 || (int64_t)c >= A.n) {
+        atomicExch(bad, 1);
+        break;
+      }
+    }
+  }
+}
+
+__global__ void k_jacobi_csr(CsrOp A, double* dinv, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    int found = 0;
+    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k)
+      if (A.colind[k] == i) { d += A.vals[k]; found = 1; }
+    if (!found || !(d > 0.0)) {
+      atomicExch(bad, 1);
+      dinv[i] = 0.0;
+    } else {
+      dinv[i] = 1.0 / d;
+    }
+  }
+}
+
+// Per-CTA minimum of the Gershgorin lower bounds of M^{-1}A (host takes the final minimum).
+__global__ void k_gershgorin_csr(CsrOp A, int jacobi, double* out) {
+  __shared__ double sh[kThreads];
+  double lo = 1.0e308;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0, off = 0.0;
+    for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+      if (A.colind[k] == i) d += A.vals[k];
+      else off += fabs(A.vals[k]);
+    }
+    const double b = jacobi ? 1.0 - off / d : d - off;
+    lo = fmin(lo, b);
+  }
+  sh[threadIdx.x] = lo;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// ||v||^2 -> ctrl: which = 0 sets the power method's first scale 1/||v0||.
+__global__ void __launch_bounds__(kThreads) k_norm2(const double* v, int64_t n, Ctrl* c,
+                                                    double* partials, int which) {
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a = fma(v[i], v[i], a);
+  double w[1] = {a}, tot[1];
+  if (grid_sum_last<1>(w, partials, &c->ticket[TK_NORM], tot)) {
+    if (threadIdx.x == 0) {
+      if (which == 0) c->inv_scale = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
+      else c->sums[0] = tot[0];
+    }
+  }
+}
+
+int stream_ctas(int64_t n, int per_sm) {
+  const int64_t want = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
+}
+
+}  // namespace
+
+// Host-side pair lists of the Gram modes (same layout as the tail reads back).
+int gram_pairs(int mode, int s, int full, unsigned short* pairs, int* nl, int* nr) {
+  const Layout L{s, full};
+  int ne = 0;
+  auto sym = [&](int lo, int ro) {  // symmetric block: L[lo+i] . R[ro+j]
+    if (full) {
+      for (int j = 0; j < s; ++j)
+        for (int i = 0; i < s; ++i) pairs[ne++] = (unsigned short)(((lo + i) << 8) | (ro + j));
+    } else {
+      for (int j = 0; j < s; ++j)
+        for (int i = 0; i <= j; ++i) pairs[ne++] = (unsigned short)(((lo + i) << 8) | (ro + j));
+    }
+  };
+  auto gen = [&](int lo, int ro) {
+    for (int j = 0; j < s; ++j)
+      for (int i = 0; i < s; ++i) pairs[ne++] = (unsigned short)(((lo + i) << 8) | (ro + j));
+  };
+  auto vec = [&](int lo, int rcol) {
+    for (int i = 0; i < s; ++i) pairs[ne++] = (unsigned short)(((lo + i) << 8) | rcol);
+  };
+  (void)L;
+  switch (mode) {
+    case GM_ONESYNC_FIRST:  // L = Z, R = [AZ, r]
+    case GM_LITERAL_W:      // L = Q, R = [AQ, r]
+      *nl = s;
+      *nr = s + 1;
+      sym(0, 0);
+      vec(0, s);
+      break;
+    case GM_LITERAL_B2:  // L = Q, R = AZ
+      *nl = s;
+      *nr = s;
+      gen(0, 0);
+      break;
+    case GM_ONESYNC:  // L = [Q, Z], R = [AQ, AZ, r]
+      *nl = 2 * s;
+      *nr = 2 * s + 1;
+      sym(0, 0);        // G1 = Q^T AQ
+      gen(0, s);        // G2 = Q^T AZ
+      if (full) gen(s, 0);  // G3 = Z^T AQ
+      sym(s, s);        // G4 = Z^T AZ
+      vec(0, 2 * s);    // g5 = Q^T r
+      vec(s, 2 * s);    // g6 = Z^T r
+      break;
+    default:
+      return -1;
+  }
+  return ne;
+}
+
+int gram_ctas() { return sm_count() * 2; }
+
+cudaError_t launch_gram(const GramArgs& g, cudaStream_t st) {
+  if (g.ne < 1 || g.ne > kMaxEntries || g.nl < 1 || g.nr < 1 || g.nl + g.nr > 2 * kMaxGramVecs)
+    return cudaErrorInvalidValue;
+  // Choose entries-per-thread so that (chunks x row phases x EPT) covers ne with few idle slots.
+  int best_ept = 1, best_nch = g.ne, best_rp = std::max(1, kThreads / g.ne);
+  double best = -1.0;
+  for (int ept = 1; ept <= 8; ++ept) {
+    const int nch = (g.ne + ept - 1) / ept;
+    if (nch > kThreads) continue;
+    const int rp = kThreads / nch;
+    const double eff = (double)g.ne * rp / ((double)kThreads * ept);
+    if (eff > best + 1e-9) {
+      best = eff;
+      best_ept = ept;
+      best_nch = nch;
+      best_rp = rp;
+    }
+  }
+  if (best < 0.0) return cudaErrorInvalidValue;
+  const int ncols = g.nl + g.nr;
+  size_t smem = sizeof(double) * (size_t)ncols * (kGramRows + 1);
+  const size_t red = sizeof(double) * ((size_t)best_rp * g.ne + (size_t)kThreads + (size_t)g.ne +
+                                       12 * kMaxS * kMaxS);
+  smem = std::max(smem, red);
+  const int grid = gram_ctas();
+  switch (best_ept) {
+#define CASE(E) \
+  case E: k_gram<E><<<grid, kThreads, smem, st>>>(g, best_nch, best_rp); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gram_init() {
+  static int done = 0;
+  if (done) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (optin <= 0) optin = 48 * 1024;
+  cudaError_t e = cudaSuccess;
+  // The dynamic limit plus the kernel's static shared memory may not exceed the opt-in size.
+#define SET(E)                                                                              \
+  if (e == cudaSuccess) {                                                                   \
+    cudaFuncAttributes fa{};                                                                \
+    e = cudaFuncGetAttributes(&fa, k_gram<E>);                                              \
+    if (e == cudaSuccess)                                                                   \
+      e = cudaFuncSetAttribute(k_gram<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                               optin - (int)fa.sharedSizeBytes);                            \
+  }
+  SET(1) SET(2) SET(3) SET(4) SET(5) SET(6) SET(7) SET(8)
+#undef SET
+  if (e == cudaSuccess) done = 1;
+  return e;
+}
+
+int update_ctas(int64_t n) { return stream_ctas(n, 4); }
+
+cudaError_t launch_update(const UpdArgs& u, cudaStream_t st) {
+  const int grid = update_ctas(u.n);
+  switch (u.s) {
+#define CASE(S) \
+  case S: return launch_update_s<S>(u, grid, st);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fgs_standalone(int s, const double* W, int nrhs, const double* B, int nu,
+                                  int solver, double* X, int* status_dev, cudaStream_t st) {
+  k_fgs_standalone<<<1, 32, 0, st>>>(s, W, nrhs, B, nu, solver, X, status_dev);
+  return cudaGetLastError();
+}
+
+int pcg_ctas(int64_t n) { return stream_ctas(n, 8); }
+
+cudaError_t launch_pcg_update(const PcgArgs& a, cudaStream_t st) {
+  k_pcg_update<<<pcg_ctas(a.n), kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_pdir(const PcgArgs& a, cudaStream_t st) {
+  k_pcg_pdir<<<pcg_ctas(a.n), kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st) {
+  k_pcg_init<<<pcg_ctas(a.n), kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_splitmix(double* v, int64_t n, uint64_t seed, cudaStream_t st) {
+  k_fill_splitmix<<<stream_ctas(n, 4), kThreads, 0, st>>>(v, n, seed);
+  return cudaGetLastError();
+}
+cudaError_t launch_csr_check(const CsrOp& A, int64_t nnz, int* bad, cudaStream_t st) {
+  k_csr_check<<<stream_ctas(A.n, 4), kThreads, 0, st>>>(A, nnz, bad);
+  return cudaGetLastError();
+}
+cudaError_t launch_jacobi_csr(const CsrOp& A, double* dinv, int* bad, cudaStream_t st) {
+  k_jacobi_csr<<<stream_ctas(A.n, 4), kThreads, 0, st>>>(A, dinv, bad);
+  return cudaGetLastError();
+}
+cudaError_t launch_norm2(const double* v, int64_t n, Ctrl* c, double* partials, int which,
+                         cudaStream_t st) {
+  k_norm2<<<stream_ctas(n, 4), kThreads, 0, st>>>(v, n, c, partials, which);
+  return cudaGetLastError();
+}
+int gershgorin_ctas(int64_t n) { return stream_ctas(n, 4); }
+cudaError_t launch_gershgorin_csr(const CsrOp& A, int jacobi, double* out_min, cudaStream_t st) {
+  k_gershgorin_csr<<<gershgorin_ctas(A.n), kThreads, 0, st>>>(A, jacobi, out_min);
+  return cudaGetLastError();
+}
+
+}  // namespace sstep

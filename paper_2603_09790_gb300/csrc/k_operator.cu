@@ -1,0 +1,425 @@
+// k_operator.cu -- y = A u for the stencil and CSR operators, with fused epilogues:
+// one Matrix-Powers-Kernel step (Algorithm 2: SpMV + M^{-1} + Chebyshev three-term
+// recurrence), initial residual, power-method step (Section 2), the PCG product A p, and the
+// true residual norm.
+//
+// Stencil operators (5/7/27 points) are matrix-free.  A CTA owns a 32 x 8 tile of the xy plane
+// and marches through a chunk of z planes (2.5D blocking): the current plane with its one-point
+// xy halo is staged in shared memory, the z neighbours of the thread's own column travel in
+// registers.  Each input value is read from HBM once per sweep; halo values of neighbouring
+// tiles come from L2.  The 27-point Poisson operator (HPCG, Section 6) uses sum factorisation
+// of the 3x3x3 box: 27 u - box(u) costs 7.5 FP64 operations per point instead of 26.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace sstep {
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+// ---------------------------------------------------------------- epilogues
+
+template <int EPI>
+struct EpiNV { static constexpr int v = 1; };
+template <>
+struct EpiNV<EP_RESID> { static constexpr int v = 2; };
+
+template <int EPI>
+__device__ __forceinline__ constexpr bool epi_reduces() {
+  return EPI == EP_RESID || EPI == EP_POWER || EPI == EP_PCG_AP || EPI == EP_TRUERES;
+}
+
+// y: (A u)_i where u is the (possibly M^{-1}-scaled) operator input; uc: that input at i.
+template <int EPI>
+__device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t i, double y, double uc,
+                                         double* red) {
+  if constexpr (EPI == EP_SPMV) {
+    e.y[i] = y;
+  } else if constexpr (EPI == EP_MPK || EPI == EP_MPK_FIRST) {
+    if constexpr (EPI == EP_MPK_FIRST) e.z1[i] = uc;  // z_1 = M^{-1} r
+    e.y[i] = y;                                        // A z_q  (column q+1 of P)
+    if (e.znext) {
+      const double d = prec_d(e.M, i);
+      const double t = e.zprev ? -e.c3 * __ldg(e.zprev + i) : 0.0;
+      e.znext[i] = fma(e.c1 * d, y, fma(-e.c2, uc, t));
+    }
+  } else if constexpr (EPI == EP_RESID) {
+    const double bi = __ldg(e.b + i);
+    const double ri = bi - y;
+    e.y[i] = ri;
+    red[0] = fma(ri, ri, red[0]);
+    red[1] = fma(bi, bi, red[1]);
+  } else if constexpr (EPI == EP_POWER) {
+    // v_{l-1} = y_{l-1} / lambda_{l-1} is normalised on the fly: scale by 1/lambda_{l-1}
+    const double yi = e.ctrl->inv_scale * prec_d(e.M, i) * y;
+    e.y[i] = yi;
+    red[0] = fma(yi, yi, red[0]);
+  } else if constexpr (EPI == EP_PCG_AP) {
+    e.y[i] = y;
+    red[0] = fma(uc, y, red[0]);
+  } else if constexpr (EPI == EP_TRUERES) {
+    const double ri = __ldg(e.b + i) - y;
+    red[0] = fma(ri, ri, red[0]);
+  }
+}
+
+// Kernel-entry early exit: later launches of a finished solve do nothing.
+template <int EPI>
+__device__ __forceinline__ bool skip(const EpiArgs& e) {
+  if (!e.ctrl) return false;
+  if constexpr (EPI == EP_POWER) return e.ctrl->power_done != 0;
+  if constexpr (EPI == EP_TRUERES || EPI == EP_SPMV) return false;
+  return e.ctrl->done != 0;
+}
+
+// Finishing step of the reduction, run by one thread of the last CTA.
+template <int EPI>
+__device__ void finish(const EpiArgs& e, const double* tot) {
+  Ctrl* c = e.ctrl;
+  if constexpr (EPI == EP_RESID) {
+    c->rr = tot[0];
+    c->rr0 = tot[0];
+    c->nb2 = tot[1];
+    c->tol2 = c->rtol2 * tot[1];
+    if (!(tot[0] == tot[0]) || tot[0] > 1.79e308 || !(tot[1] == tot[1])) {
+      c->status = SSTEP_ERR_NONFINITE;
+      c->done = 1;
+    } else if (tot[1] == 0.0 || tot[0] <= c->tol2) {
+      c->status = SSTEP_OK;
+      c->done = 1;
+    }
+  } else if constexpr (EPI == EP_POWER) {
+    // Section 2: stop when |lambda^(l) - lambda^(l-1)| < tol |lambda^(l)| or at the cap.
+    const double lam = sqrt(tot[0]);
+    c->power_iters += 1;
+    const bool conv = c->power_iters > 1 && c->power_tol > 0.0 &&
+                      fabs(lam - c->lam) < c->power_tol * fabs(lam);
+    c->lam = lam;
+    c->inv_scale = lam > 0.0 ? 1.0 / lam : 0.0;
+    if (conv || c->power_iters >= c->power_max || !(lam > 0.0)) c->power_done = 1;
+  } else if constexpr (EPI == EP_PCG_AP) {
+    const double pAp = tot[0];
+    if (!(pAp > 0.0) || pAp > 1.79e308) {
+      c->status = SSTEP_ERR_BREAKDOWN;
+      c->done = 1;
+    } else {
+      c->pcg_alpha = c->rz / pAp;
+    }
+  } else if constexpr (EPI == EP_TRUERES) {
+    c->sums[0] = tot[0];
+  }
+}
+
+template <int EPI>
+__device__ __forceinline__ void reduce_and_finish(const EpiArgs& e, double* red) {
+  if constexpr (epi_reduces<EPI>()) {
+    constexpr int NV = EpiNV<EPI>::v;
+    double v[NV], tot[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = red[k];
+    const int ticket = (EPI == EP_PCG_AP) ? TK_PCG1 : TK_OP;
+    if (grid_sum_last<NV>(v, e.partials, &e.ctrl->ticket[ticket], tot)) {
+      if (threadIdx.x == 0) finish<EPI>(e, tot);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 5/7-point stencil
+
+// SCALE: multiply every loaded input value by M^{-1} (MPK first step, non-uniform M).
+template <int PTS, bool POISSON, int EPI, bool SCALE>
+__global__ void __launch_bounds__(TX * TY) k_stencil7(StencilOp op, EpiArgs e, int zc) {
+  if (skip<EPI>(e)) return;
+  __shared__ double t[TY + 2][TX + 2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int nx = op.nx, ny = op.ny, nz = op.nz;
+  const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int64_t pxy = (int64_t)nx * ny;
+  const bool in = x < nx && y < ny;
+  const int64_t col = (int64_t)y * nx + x;
+  const double* __restrict__ u = e.u;
+  auto ld = [&](int64_t idx) -> double {
+    double v = __ldg(u + idx);
+    if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
+    return v;
+  };
+  double red[2] = {0.0, 0.0};
+  double ub = 0.0, uc = 0.0, ua = 0.0;
+  if (PTS == 7 && in && z0 >= 1) ub = ld(col + (int64_t)(z0 - 1) * pxy);
+  if (in && z0 < nz) uc = ld(col + (int64_t)z0 * pxy);
+  if (PTS == 7 && in && z0 + 1 < nz) ua = ld(col + (int64_t)(z0 + 1) * pxy);
+  for (int z = z0; z < z1; ++z) {
+    const int64_t pz = (int64_t)z * pxy;
+    t[ty + 1][tx + 1] = uc;
+    if (tx == 0) t[ty + 1][0] = (x >= 1 && y < ny) ? ld(pz + col - 1) : 0.0;
+    if (tx == TX - 1) t[ty + 1][TX + 1] = (x + 1 < nx && y < ny) ? ld(pz + col + 1) : 0.0;
+    if (ty == 0) t[0][tx + 1] = (y >= 1 && x < nx) ? ld(pz + col - nx) : 0.0;
+    if (ty == TY - 1) t[TY + 1][tx + 1] = (y + 1 < ny && x < nx) ? ld(pz + col + nx) : 0.0;
+    __syncthreads();
+    if (in) {
+      double a;
+      if constexpr (POISSON) {
+        double s = (t[ty + 1][tx] + t[ty + 1][tx + 2]) + (t[ty][tx + 1] + t[ty + 2][tx + 1]);
+        if constexpr (PTS == 7) s += ub + ua;
+        a = fma(op.wc, uc, -s);
+      } else if constexpr (PTS == 7) {
+        a = op.w[0] * ub;
+        a = fma(op.w[1], t[ty][tx + 1], a);
+        a = fma(op.w[2], t[ty + 1][tx], a);
+        a = fma(op.w[3], uc, a);
+        a = fma(op.w[4], t[ty + 1][tx + 2], a);
+        a = fma(op.w[5], t[ty + 2][tx + 1], a);
+        a = fma(op.w[6], ua, a);
+      } else {
+        a = op.w[0] * t[ty][tx + 1];
+        a = fma(op.w[1], t[ty + 1][tx], a);
+        a = fma(op.w[2], uc, a);
+        a = fma(op.w[3], t[ty + 1][tx + 2], a);
+        a = fma(op.w[4], t[ty + 2][tx + 1], a);
+      }
+      double ucc = uc;
+      if constexpr (EPI == EP_MPK_FIRST && !SCALE) {  // uniform M^{-1}: A (d r) = d (A r)
+        a *= e.M.dinv_u;
+        ucc *= e.M.dinv_u;
+      }
+      epilogue<EPI>(e, pz + col, a, ucc, red);
+    }
+    __syncthreads();
+    if constexpr (PTS == 7) {
+      ub = uc;
+      uc = ua;
+      ua = (in && z + 2 < nz) ? ld(col + (int64_t)(z + 2) * pxy) : 0.0;
+    }
+  }
+  reduce_and_finish<EPI>(e, red);
+}
+
+// ---------------------------------------------------------------- 27-point stencil
+
+// POISSON: y = 27 u - box3x3x3(u) by sum factorisation (row sums in x, column sums in y,
+// plane sums in z kept in registers).  General constant weights: 27 products per point.
+template <bool POISSON, int EPI, bool SCALE>
+__global__ void __launch_bounds__(TX * TY) k_stencil27(StencilOp op, EpiArgs e, int zc) {
+  if (skip<EPI>(e)) return;
+  __shared__ double pl[3][TY + 2][TX + 2];  // planes z-1, z, z+1 (general weights)
+  __shared__ double rs[TY + 2][TX];         // x row sums of the newest plane (Poisson)
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int nx = op.nx, ny = op.ny, nz = op.nz;
+  const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int64_t pxy = (int64_t)nx * ny;
+  const bool in = x < nx && y < ny;
+  const double* __restrict__ u = e.u;
+  auto ld = [&](int xx, int yy, int zz) -> double {
+    if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) return 0.0;
+    const int64_t idx = (int64_t)zz * pxy + (int64_t)yy * nx + xx;
+    double v = __ldg(u + idx);
+    if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
+    return v;
+  };
+  // Stage plane zz (with xy halo) into slot `s` of pl.
+  auto stage = [&](int slot, int zz) {
+    double (*p)[TX + 2] = pl[slot];
+    p[ty + 1][tx + 1] = ld(x, y, zz);
+    if (tx == 0) {
+      p[ty + 1][0] = ld(x - 1, y, zz);
+      if (ty == 0) p[0][0] = ld(x - 1, y - 1, zz);
+      if (ty == TY - 1) p[TY + 1][0] = ld(x - 1, y + 1, zz);
+    }
+    if (tx == TX - 1) {
+      p[ty + 1][TX + 1] = ld(x + 1, y, zz);
+      if (ty == 0) p[0][TX + 1] = ld(x + 1, y - 1, zz);
+      if (ty == TY - 1) p[TY + 1][TX + 1] = ld(x + 1, y + 1, zz);
+    }
+    if (ty == 0) p[0][tx + 1] = ld(x, y - 1, zz);
+    if (ty == TY - 1) p[TY + 1][tx + 1] = ld(x, y + 1, zz);
+  };
+  double red[2] = {0.0, 0.0};
+  if constexpr (POISSON) {
+    // s2 = column (y) sums of x row sums, for planes z-1, z, z+1 of the thread's column.
+    auto plane_s2 = [&](int zz) -> double {
+      stage(0, zz);
+      __syncthreads();
+      rs[ty + 1][tx] = pl[0][ty + 1][tx] + pl[0][ty + 1][tx + 1] + pl[0][ty + 1][tx + 2];
+      if (ty == 0) rs[0][tx] = pl[0][0][tx] + pl[0][0][tx + 1] + pl[0][0][tx + 2];
+      if (ty == TY - 1)
+        rs[TY + 1][tx] = pl[0][TY + 1][tx] + pl[0][TY + 1][tx + 1] + pl[0][TY + 1][tx + 2];
+      __syncthreads();
+      const double v = rs[ty][tx] + rs[ty + 1][tx] + rs[ty + 2][tx];
+      __syncthreads();
+      return v;
+    };
+    double sb = plane_s2(z0 - 1);
+    double sc = plane_s2(z0);
+    double uc = ld(x, y, z0);
+    for (int z = z0; z < z1; ++z) {
+      const double sa = plane_s2(z + 1);
+      const double ua = ld(x, y, z + 1);
+      if (in) {
+        const double box = (sb + sc) + sa;
+        double a = fma(op.wc + 1.0, uc, -box);  // 26 u - (box - u) with wc = 26
+        double ucc = uc;
+        if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
+          a *= e.M.dinv_u;
+          ucc *= e.M.dinv_u;
+        }
+        epilogue<EPI>(e, (int64_t)z * pxy + (int64_t)y * nx + x, a, ucc, red);
+      }
+      sb = sc;
+      sc = sa;
+      uc = ua;
+    }
+  } else {
+    stage(0, z0 - 1);
+    stage(1, z0);
+    for (int z = z0; z < z1; ++z) {
+      const int sm = (z - z0) % 3, s0 = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
+      stage(sp, z + 1);
+      __syncthreads();
+      if (in) {
+        double a = 0.0;
+        int k = 0;
+        const int slots[3] = {sm, s0, sp};
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) a = fma(op.w[k++], pl[slots[dz]][ty + dy][tx + dx], a);
+        double ucc = pl[s0][ty + 1][tx + 1];
+        if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
+          a *= e.M.dinv_u;
+          ucc *= e.M.dinv_u;
+        }
+        epilogue<EPI>(e, (int64_t)z * pxy + (int64_t)y * nx + x, a, ucc, red);
+      }
+      __syncthreads();
+    }
+  }
+  reduce_and_finish<EPI>(e, red);
+}
+
+// ---------------------------------------------------------------- CSR
+
+constexpr int kCsrCtasPerSm = 8;
+
+template <int EPI, bool SCALE>
+__global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
+  if (skip<EPI>(e)) return;
+  double red[2] = {0.0, 0.0};
+  const double* __restrict__ u = e.u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+    double a = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      double v = __ldg(u + c);
+      if constexpr (SCALE) v *= __ldg(e.M.dinv + c);
+      a = fma(__ldg(A.vals + k), v, a);
+    }
+    double uc = __ldg(u + i);
+    if constexpr (SCALE) uc *= __ldg(e.M.dinv + i);
+    if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
+      a *= e.M.dinv_u;
+      uc *= e.M.dinv_u;
+    }
+    epilogue<EPI>(e, i, a, uc, red);
+  }
+  reduce_and_finish<EPI>(e, red);
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+struct StencilGrid {
+  dim3 grid;
+  int zc;
+};
+
+StencilGrid stencil_grid(const StencilOp& op) {
+  const int gx = (op.nx + TX - 1) / TX, gy = (op.ny + TY - 1) / TY;
+  const int64_t txy = (int64_t)gx * gy;
+  // Aim for about 16 CTAs per SM in total while keeping z chunks of >= 8 planes.
+  int64_t want_z = std::max<int64_t>(1, (int64_t)num_sms() * 16 / std::max<int64_t>(1, txy));
+  want_z = std::min<int64_t>(want_z, std::max(1, op.nz / 8));
+  int zc = (int)((op.nz + want_z - 1) / want_z);
+  if (zc < 1) zc = 1;
+  int gz = (op.nz + zc - 1) / zc;
+  return {dim3(gx, gy, gz), zc};
+}
+
+template <int EPI, bool SCALE>
+cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t st) {
+  StencilGrid g = stencil_grid(op);
+  const int threads = TX * TY;
+  if (op.points == 27) {
+    if (op.poisson) k_stencil27<true, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+    else k_stencil27<false, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+  } else if (op.points == 7) {
+    if (op.poisson) k_stencil7<7, true, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+    else k_stencil7<7, false, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+  } else {
+    if (op.poisson) k_stencil7<5, true, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+    else k_stencil7<5, false, EPI, SCALE><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+  }
+  return cudaGetLastError();
+}
+
+int csr_ctas(int64_t n) {
+  int64_t want = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * kCsrCtasPerSm));
+}
+
+template <int EPI, bool SCALE>
+cudaError_t launch_csr(const CsrOp& A, const EpiArgs& e, cudaStream_t st) {
+  k_csr<EPI, SCALE><<<csr_ctas(A.n), kThreads, 0, st>>>(A, e);
+  return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t dispatch(const OpDesc& A, const EpiArgs& e, cudaStream_t st) {
+  // Per-entry scaling by M^{-1} is needed only when the first MPK step applies a
+  // non-uniform M^{-1} before the operator.
+  const bool scale = (EPI == EP_MPK_FIRST) && e.M.dinv != nullptr;
+  if (A.kind == SSTEP_MATRIX_STENCIL) {
+    return scale ? launch_stencil<EPI, true>(A.st, e, st) : launch_stencil<EPI, false>(A.st, e, st);
+  }
+  return scale ? launch_csr<EPI, true>(A.csr, e, st) : launch_csr<EPI, false>(A.csr, e, st);
+}
+
+}  // namespace
+
+int operator_grid_ctas(const OpDesc& A) {
+  if (A.kind == SSTEP_MATRIX_STENCIL) {
+    StencilGrid g = stencil_grid(A.st);
+    return (int)(g.grid.x * g.grid.y * g.grid.z);
+  }
+  return csr_ctas(A.csr.n);
+}
+
+cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st) {
+  switch (e.epi) {
+    case EP_SPMV: return dispatch<EP_SPMV>(A, e, st);
+    case EP_MPK: return dispatch<EP_MPK>(A, e, st);
+    case EP_MPK_FIRST: return dispatch<EP_MPK_FIRST>(A, e, st);
+    case EP_RESID: return dispatch<EP_RESID>(A, e, st);
+    case EP_POWER: return dispatch<EP_POWER>(A, e, st);
+    case EP_PCG_AP: return dispatch<EP_PCG_AP>(A, e, st);
+    case EP_TRUERES: return dispatch<EP_TRUERES>(A, e, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sstep

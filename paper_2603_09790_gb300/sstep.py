@@ -1,0 +1,303 @@
+"""Python binding of libsstep.so (include/sstep.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts torch tensors (CUDA or
+CPU) and numpy arrays to raw pointers and sizes, calls the C ABI, and raises on error.  It
+fails loudly when the library has not been built: there is no CPU fallback.
+
+Names follow the C ABI: ``setup``/``solve``/``solve_batched``/``free`` (wrapped by
+:class:`Solver`), ``mpk``, ``block_gram``, ``fgs``, ``block_update``, ``spmv``,
+``get_basis_info``, ``get_history``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsstep.so")
+
+OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED = range(8)
+MATRIX_CSR, MATRIX_STENCIL = 0, 1
+PREC = {"none": 0, "jacobi": 1}
+ALGO = {"onesync": 0, "literal": 1, "pcg": 2}
+GRAM = {"fgs": 0, "cholesky": 1}
+
+
+class SstepError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sstep status {status}: {msg}")
+        self.status = status
+
+
+class _Matrix(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("vals", C.c_void_p), ("nnz", C.c_int64), ("nx", C.c_int), ("ny", C.c_int),
+                ("nz", C.c_int), ("points", C.c_int), ("weights", C.c_void_p)]
+
+
+class _Precond(C.Structure):
+    _fields_ = [("kind", C.c_int)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("s", C.c_int), ("sweeps", C.c_int), ("rtol", C.c_double), ("max_outer", C.c_int),
+                ("algo", C.c_int), ("gram_solver", C.c_int), ("power_iters", C.c_int),
+                ("power_tol", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
+                ("power_v0", C.c_void_p), ("check_every", C.c_int)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_equiv", C.c_int),
+                ("relres", C.c_double), ("relres_true", C.c_double), ("lambda_max", C.c_double),
+                ("lambda_min", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
+                ("launches", C.c_longlong)]
+
+
+_lib = None
+
+
+def load():
+    """Load libsstep.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libsstep.so is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "sstep_default_opts": (None, [P]),
+        "sstep_setup": (I, [P, I, P, P, P, P]),
+        "sstep_solve": (I, [P, P, P, P]),
+        "sstep_solve_batched": (I, [P, I, P, P, P]),
+        "sstep_free": (I, [P]),
+        "sstep_status_string": (C.c_char_p, [I]),
+        "sstep_last_error": (C.c_char_p, []),
+        "sstep_mpk": (I, [P, P, P, P, I]),
+        "sstep_block_gram": (I, [I64, I, P, I, P, I, P, P, P]),
+        "sstep_fgs": (I, [I, P, I, P, I, I, P, P, P]),
+        "sstep_block_update": (I, [P, P, P, P, P, P, P, P, P, P, I]),
+        "sstep_spmv": (I, [P, P, P]),
+        "sstep_get_basis_info": (I, [P, P, P, P, P, P, P]),
+        "sstep_get_history": (I, [P, P, I, P]),
+        "sstep_profile": (I, [P, P, I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != OK:
+        lib = load()
+        msg = lib.sstep_last_error().decode() or lib.sstep_status_string(status).decode()
+        raise SstepError(status, msg)
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+@dataclass
+class Stencil:
+    """Matrix-free stencil operator on the interior of an nx x ny x nz grid."""
+    nx: int
+    ny: int
+    nz: int = 1
+    points: int = 7
+    weights: Optional[Sequence[float]] = None
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+
+@dataclass
+class CSR:
+    """CSR operator: rowptr int64 (n+1), colind int32 (nnz), vals float64 (nnz); torch or numpy."""
+    rowptr: object
+    colind: object
+    vals: object
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def n(self):
+        return int(self.rowptr.shape[0]) - 1
+
+    @property
+    def nnz(self):
+        return int(self.colind.shape[0])
+
+
+@dataclass
+class Info:
+    status: int
+    outer_iters: int
+    inner_equiv: int
+    relres: float
+    relres_true: float
+    lambda_max: float
+    lambda_min: float
+    ms_setup: float
+    ms_solve: float
+    launches: int
+
+
+def _info(i: _Info) -> Info:
+    return Info(i.status, i.outer_iters, i.inner_equiv, i.relres, i.relres_true, i.lambda_max,
+                i.lambda_min, i.ms_setup, i.ms_solve, i.launches)
+
+
+class Solver:
+    """A handle of libsstep.so (sstep_setup ... sstep_free)."""
+
+    def __init__(self, A, *, precond="jacobi", s=4, sweeps=2, rtol=1e-8, max_outer=10000,
+                 algo="onesync", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
+                 lambda_max=0.0, power_v0=None, check_every=0, stream=None):
+        lib = load()
+        m = _Matrix()
+        self._weights = None
+        if isinstance(A, Stencil):
+            m.kind = MATRIX_STENCIL
+            m.n = A.n
+            m.nx, m.ny, m.nz, m.points = A.nx, A.ny, A.nz, A.points
+            if A.weights is not None:
+                self._weights = np.ascontiguousarray(A.weights, dtype=np.float64)
+                m.weights = self._weights.ctypes.data
+        elif isinstance(A, CSR):
+            m.kind = MATRIX_CSR
+            m.n = A.n
+            m.nnz = A.nnz
+            m.rowptr, m.colind, m.vals = _ptr(A.rowptr), _ptr(A.colind), _ptr(A.vals)
+        else:
+            raise TypeError("A must be a Stencil or a CSR")
+        self.n = int(m.n)
+        o = _Opts()
+        lib.sstep_default_opts(C.byref(o))
+        o.s, o.sweeps, o.rtol, o.max_outer = int(s), int(sweeps), float(rtol), int(max_outer)
+        o.algo, o.gram_solver = ALGO[algo], GRAM[gram]
+        o.power_iters, o.power_tol = int(power_iters), float(power_tol)
+        o.lambda_min, o.lambda_max = float(lambda_min), float(lambda_max)
+        o.power_v0 = _ptr(power_v0)
+        o.check_every = int(check_every)
+        self.s = int(s)
+        self.max_outer = int(max_outer)
+        pc = _Precond(PREC[precond])
+        h = C.c_void_p()
+        _check(lib.sstep_setup(C.byref(m), 1, C.byref(pc), C.byref(o), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    # -- lifecycle
+    def free(self):
+        if getattr(self, "_h", None):
+            load().sstep_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    # -- solves
+    def solve(self, b, x, check=True) -> Info:
+        """sstep_solve: x (x^(0) on entry) receives the solution; device or host buffers."""
+        info = _Info()
+        st = load().sstep_solve(self._h, _ptr(b), _ptr(x), C.byref(info))
+        if check and st not in (OK, NOT_CONVERGED):
+            _check(st)
+        return _info(info)
+
+    def solve_batched(self, bs, xs, check=True):
+        n = len(bs)
+        B = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+        X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+        infos = (_Info * n)()
+        st = load().sstep_solve_batched(self._h, n, B, X, infos)
+        if check and st not in (OK, NOT_CONVERGED):
+            _check(st)
+        return [_info(i) for i in infos]
+
+    # -- hot-path steps
+    def mpk(self, r, Z, AZ, s=0):
+        _check(load().sstep_mpk(self._h, _ptr(r), _ptr(Z), _ptr(AZ), int(s)))
+
+    def block_update(self, Z, AZ, Q, AQ, alpha, beta, x, r, rr_out, s=0):
+        _check(load().sstep_block_update(self._h, _ptr(Z), _ptr(AZ), _ptr(Q), _ptr(AQ), _ptr(alpha),
+                                         _ptr(beta), _ptr(x), _ptr(r), _ptr(rr_out), int(s)))
+
+    def spmv(self, x, y):
+        _check(load().sstep_spmv(self._h, _ptr(x), _ptr(y)))
+
+    def get_basis_info(self):
+        v = [C.c_double() for _ in range(5)]
+        it = C.c_int()
+        _check(load().sstep_get_basis_info(self._h, *[C.byref(t) for t in v], C.byref(it)))
+        lmin, lmax, ca, cs, cg = (t.value for t in v)
+        return dict(lambda_min=lmin, lambda_max=lmax, c_alpha=ca, c_sigma=cs, c_gamma=cg,
+                    power_iters=it.value)
+
+    def profile(self, b, iters=5):
+        """sstep_profile: average device ms per phase of one outer iteration (4 values)."""
+        ms = (C.c_double * 4)()
+        _check(load().sstep_profile(self._h, _ptr(b), int(iters), ms))
+        return list(ms)
+
+    def get_history(self):
+        buf = np.zeros(self.max_outer + 2)
+        cnt = C.c_int()
+        _check(load().sstep_get_history(self._h, buf.ctypes.data, buf.size, C.byref(cnt)))
+        return buf[: cnt.value].copy()
+
+
+def block_gram(L, R, pairs, out, stream=None):
+    """sstep_block_gram: out[e] = L[pairs[e][0]] . R[pairs[e][1]] (device vectors of length n)."""
+    n = int(L[0].numel())
+    Lp = (C.c_void_p * len(L))(*[_ptr(v) for v in L])
+    Rp = (C.c_void_p * len(R))(*[_ptr(v) for v in R])
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    _check(load().sstep_block_gram(n, len(L), Lp, len(R), Rp, pr.size // 2, pr.ctypes.data,
+                                   _ptr(out), _stream_ptr(stream)))
+
+
+def fgs(W, B, nu, X, solver="fgs", status=None, stream=None):
+    """sstep_fgs: nu FGS sweeps (or Cholesky) on W X = B; W (s, s) and B (nrhs, s) device tensors
+    in column-major order (row k of B is right-hand side k)."""
+    s = int(W.shape[0])
+    nrhs = int(B.shape[0])
+    _check(load().sstep_fgs(s, _ptr(W), nrhs, _ptr(B), int(nu), GRAM[solver], _ptr(X), _ptr(status),
+                            _stream_ptr(stream)))
