@@ -100,7 +100,11 @@ typedef struct {
   const double* power_v0; /* start vector of the power method (n doubles, device or host); NULL =
                              U[-1,1) from SplitMix64 with seed 1 in index order */
   int check_every;    /* outer iterations between host reads of the stop flag (0 = automatic) */
+  int gram_blocks;    /* SSTEP_GRAM_BLOCKS_FULL: every Gram block as computed (Algorithm 1);
+                         SSTEP_GRAM_BLOCKS_SYM: upper triangles of Q^T AQ, Z^T AZ and
+                         Z^T AQ = (Q^T AZ)^T (fewer products).  Cholesky always uses FULL. */
 } sstep_opts;
+enum { SSTEP_GRAM_BLOCKS_FULL = 0, SSTEP_GRAM_BLOCKS_SYM = 1 };
 
 typedef struct {
   int status;             /* sstep_status of the solve */

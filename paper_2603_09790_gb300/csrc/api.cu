@@ -96,6 +96,11 @@ sstep_status alloc(double** p, int64_t count) {
 
 // ---------------------------------------------------------------- kernel sequences
 
+// Every Gram block as computed (Algorithm 1), or the symmetric shortcut (opt-in).
+int full_blocks(const sstep_ctx* h) {
+  return (h->o.gram_solver == SSTEP_GRAM_CHOLESKY || h->o.gram_blocks != SSTEP_GRAM_BLOCKS_SYM) ? 1 : 0;
+}
+
 EpiArgs epi_base(sstep_ctx* h, int epi) {
   EpiArgs e{};
   e.epi = epi;
@@ -142,7 +147,7 @@ sstep_status run_gram(sstep_ctx* h, int mode) {
   g.ctrl = h->ctrl;
   g.partials = h->partials;
   int nl = 0, nr = 0;
-  g.ne = gram_pairs(mode, s, h->o.gram_solver == SSTEP_GRAM_CHOLESKY ? 1 : 0, g.pairs, &nl, &nr);
+  g.ne = gram_pairs(mode, s, full_blocks(h), g.pairs, &nl, &nr);
   g.nl = nl;
   g.nr = nr;
   auto cols = [&](const double* base, int k, const double** dst) {
@@ -256,7 +261,7 @@ sstep_status reset_ctrl(sstep_ctx* h) {
   c->s = h->s;
   c->nu = h->o.sweeps;
   c->solver = h->o.gram_solver;
-  c->full_gram = h->o.gram_solver == SSTEP_GRAM_CHOLESKY ? 1 : 0;
+  c->full_gram = full_blocks(h);
   c->power_tol = h->o.power_tol;
   c->power_max = h->o.power_iters;
   CK(cudaMemcpyAsync(h->ctrl, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->st));
@@ -678,6 +683,7 @@ void sstep_default_opts(sstep_opts* o) {
   o->lambda_max = 0.0;
   o->power_v0 = nullptr;
   o->check_every = 0;
+  o->gram_blocks = SSTEP_GRAM_BLOCKS_FULL;
 }
 
 sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,

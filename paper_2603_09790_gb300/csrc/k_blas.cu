@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(kThreads) k_gram(GramArgs g, int nch, int rp) 
   const int per = max(1, (int)blockDim.x / g.ne);  // threads per entry
   double* part = sm;                                // per * ne
   double* sums = sm + per * g.ne;                   // ne
-  if (tid < per * g.ne) {
-    const int e = tid % g.ne, sl = tid / g.ne;
+  for (int idx = tid; idx < per * g.ne; idx += blockDim.x) {  // ne may exceed blockDim.x
+    const int e = idx % g.ne, sl = idx / g.ne;
     const int nb = gridDim.x;
     const int b0 = (int)((int64_t)nb * sl / per), b1 = (int)((int64_t)nb * (sl + 1) / per);
     double v = 0.0;
