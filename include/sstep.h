@@ -172,6 +172,21 @@ SSTEP_API sstep_status sstep_block_gram(int64_t n, int nl, const double* const* 
                               const double* const* R, int ne, const int* pairs, double* out,
                               void* stream);
 
+/* sstep_block_gram without any device allocation.  The paper has no counterpart: this is a
+ * library convenience for callers that cannot allocate device memory when they call it, for
+ * example programs whose framework already holds the device's memory in its own pool (an extra
+ * cudaMalloc fails or fragments it) or latency-sensitive callers that must not pay for the
+ * allocator or for a free that waits on the device.  Same arguments and result as
+ * sstep_block_gram; the caller still passes L, R and out.  Scratch comes from one fixed area of
+ * about 1.06 MB compiled into the library, kept on every GPU that loads it until exit.  Limits:
+ * ne <= 256 (else SSTEP_ERR_INVALID with a message), devices with at most 256 SMs (else
+ * SSTEP_ERR_UNSUPPORTED).  The first call on a device looks up the area's address.  All calls
+ * share the area: calls that overlap on the GPU (different streams, or threads without
+ * ordering) race and return wrong sums, so order them. */
+SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, const double* const* L, int nr,
+                                                const double* const* R, int ne, const int* pairs,
+                                                double* out, void* stream);
+
 /* nu FGS sweeps from 0 on W X = B for nrhs right-hand sides (Section 3.1, Eq. fgs-iteration on
  * W itself: W = D + L_W + L_W^T).  W: s x s column-major, B and X: s x nrhs column-major, all
  * device pointers; 1 <= s <= 16, 1 <= nrhs <= 16.  Breakdown (W_ii <= 0 or non-finite) is

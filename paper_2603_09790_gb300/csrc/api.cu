@@ -664,6 +664,8 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
 
 }  // namespace
 
+void sstep::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ================================================================== C ABI
 
 extern "C" {

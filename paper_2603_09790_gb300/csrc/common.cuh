@@ -278,4 +278,7 @@ cudaError_t launch_gershgorin_csr(const CsrOp& A, int jacobi, double* out_min, c
 
 int operator_grid_ctas(const OpDesc& A);  // CTAs of one operator launch (partials sizing)
 
+// Sets the calling thread's message returned by sstep_last_error() (defined in api.cu).
+void set_last_error(const char* msg);
+
 }  // namespace sstep

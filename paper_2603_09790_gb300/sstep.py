@@ -87,6 +87,7 @@ def load():
         "sstep_get_basis_info": (I, [P, P, P, P, P, P, P]),
         "sstep_get_history": (I, [P, P, I, P]),
         "sstep_profile": (I, [P, P, I, P]),
+        "sstep_block_gram_noalloc": (I, [I64, I, P, I, P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -293,6 +294,18 @@ def block_gram(L, R, pairs, out, stream=None):
     pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
     _check(load().sstep_block_gram(n, len(L), Lp, len(R), Rp, pr.size // 2, pr.ctypes.data,
                                    _ptr(out), _stream_ptr(stream)))
+
+
+def block_gram_noalloc(L, R, pairs, out, stream=None):
+    """sstep_block_gram_noalloc: the same products as block_gram for callers that cannot
+    allocate device memory at call time; scratch is a fixed area inside the library (at most
+    256 products per call; calls overlapping on the GPU race)."""
+    n = int(L[0].numel())
+    Lp = (C.c_void_p * len(L))(*[_ptr(v) for v in L])
+    Rp = (C.c_void_p * len(R))(*[_ptr(v) for v in R])
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    _check(load().sstep_block_gram_noalloc(n, len(L), Lp, len(R), Rp, pr.size // 2, pr.ctypes.data,
+                                           _ptr(out), _stream_ptr(stream)))
 
 
 def fgs(W, B, nu, X, solver="fgs", status=None, stream=None):
