@@ -42,8 +42,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=256, help="grid edge (n^3 unknowns)")
-    p.add_argument("--s", type=int, default=2)
+    p.add_argument("--s", type=int, default=4)
     p.add_argument("--sweeps", type=int, default=3)
+    p.add_argument("--algo", choices=["literal", "onesync"], default="literal")
     p.add_argument("--form", choices=["stencil", "csr"], default="stencil")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--extra", default="", help="extra s-step configs to time, e.g. '4:3,4:30'")
@@ -111,18 +112,25 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- algorithmic work per kernel
 
-def kernel_work(s, n, points=7):
-    """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes)."""
+def kernel_work(s, n, points=7, sym_blocks=False):
+    """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes).
+
+    A multiply-add counts 2 flops.  Literal form (default): b2 = -Q^T AZ (s^2 products),
+    line 15 fused with W = Q^T AQ and b1 = Q^T r (2 s^2 + s^2 + s multiply-adds), x/r update
+    (2 s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products, or 2 s^2 + 3 s with
+    the symmetric shortcut) and one update pass (2 s^2 + 2 s + 1)."""
     V = 8.0 * n
     sp_flops = {5: 5, 7: 7, 27: 27}[points]  # Poisson: (points-1) adds + 1 multiply per row
     rec = 4  # z_{q+1} = c1 d (Az) - c2 z_q - z_{q-1}: 2 multiplies + 2 adds
-    ne = 2 * s * s + 3 * s  # Gram entries of the one-reduction form
+    ne = (2 * s * s + 3 * s) if sym_blocks else (4 * s * s + 2 * s)
     mpk_bytes = (4 * (s - 1) + 2) * V if s > 1 else 3 * V
     return {
-        "mpk_step": {"bytes": mpk_bytes / s, "flops": (sp_flops + rec) * n, "launches_per_outer": s},
-        "gram": {"bytes": (4 * s + 1) * V, "flops": 2.0 * ne * n, "launches_per_outer": 1},
-        "update": {"bytes": (6 * s + 4) * V, "flops": 2.0 * (2 * s * s + 2 * s + 1) * n,
-                   "launches_per_outer": 1},
+        "mpk_step": {"bytes": mpk_bytes / s, "flops": (sp_flops + rec) * n},
+        "gram_b2": {"bytes": 2 * s * V, "flops": 2.0 * s * s * n},
+        "update_w": {"bytes": (6 * s + 1) * V, "flops": 2.0 * (3 * s * s + s) * n},
+        "update_xr": {"bytes": (2 * s + 4) * V, "flops": (2.0 * (2 * s + 1) + 2) * n},
+        "gram": {"bytes": (4 * s + 1) * V, "flops": 2.0 * ne * n},
+        "update": {"bytes": (6 * s + 4) * V, "flops": 2.0 * (2 * s * s + 2 * s + 1) * n},
         "pcg_spmv_dot": {"bytes": 2 * V, "flops": (sp_flops + 2) * n},
         "pcg_update": {"bytes": 6 * V, "flops": 10.0 * n},
         "pcg_pdir": {"bytes": 3 * V, "flops": 3.0 * n},
@@ -156,7 +164,7 @@ def hbm_peak():
 
 # ---------------------------------------------------------------- oracle (CPU) timing
 
-def oracle_sample(n_edge, s, nu, gpu_lambda=None, outer_sample=2):
+def oracle_sample(n_edge, s, nu, gpu_lambda=None, outer_sample=2, algo="literal"):
     """Time the oracle on bounded samples of the workload and extrapolate to a whole solve.
 
     Returns (seconds_per_solve, description, details).  The extrapolation multiplies the
@@ -175,7 +183,7 @@ def oracle_sample(n_edge, s, nu, gpu_lambda=None, outer_sample=2):
     t_power = (time.perf_counter() - t) / 2 * 20  # 20 power iterations
     lam = gpu_lambda if gpu_lambda else lam2
     t = time.perf_counter()
-    O.pcgs(A, b, s=s, nu=nu, rtol=0.0, max_outer=outer_sample, algo="onesync", lambda_max=lam)
+    O.pcgs(A, b, s=s, nu=nu, rtol=0.0, max_outer=outer_sample, algo=algo, lambda_max=lam)
     t_outer_s = (time.perf_counter() - t) / outer_sample
     t = time.perf_counter()
     O.pcg(A, b, rtol=0.0, max_iters=4 * outer_sample)
@@ -197,7 +205,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     counts = oracle_counts()
-    key = f"s{args.s}nu{args.sweeps}"
+    key = f"{args.algo}_s{args.s}nu{args.sweeps}"
     if args.n != 256 or key not in counts:
         print(json.dumps({"impl": "reference", "unavailable":
                           f"no recorded oracle iteration count for n={args.n}, {key}"}))
@@ -205,7 +213,8 @@ def run_reference(args):
     N_outer = counts[key]["iters"]
     times = []
     for k in range(args.warmup + args.steps):
-        t_power, t_outer, _ = oracle_sample(args.n, args.s, args.sweeps, outer_sample=1)
+        t_power, t_outer, _ = oracle_sample(args.n, args.s, args.sweeps, outer_sample=1,
+                                            algo=args.algo)
         if k >= args.warmup:
             times.append(t_power + t_outer * N_outer)
     v = float(np.mean(times))
@@ -214,8 +223,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"poisson7_{args.n}^3_csr_jacobi_s{args.s}_nu{args.sweeps}_rtol1e-8",
-                   "algo": "PCG-S one-reduction form, FP64 oracle (plain C, sequential)"},
+        "config": {"workload": f"poisson7_{args.n}^3_{args.form}_jacobi_s{args.s}_nu{args.sweeps}",
+                   "algo": f"PCG-S {args.algo} form, FP64 oracle (plain C, sequential)"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"per step: 1 outer iteration + 2 power iterations of the oracle "
                                    f"at {args.n}^3, extrapolated to 20 power iterations and the oracle's "
@@ -292,7 +301,7 @@ def main():
         return ms, infos
 
     # ---- s-step (headline)
-    S = sstep.Solver(A, s=args.s, sweeps=args.sweeps, algo="onesync", **common)
+    S = sstep.Solver(A, s=args.s, sweeps=args.sweeps, algo=args.algo, **common)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
     gpu_id = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     sampler = ClockSampler(("GPU-" + str(gpu_id)) if gpu_id else local)
@@ -343,7 +352,7 @@ def main():
     extra = {}
     for item in filter(None, args.extra.split(",")):
         s_, nu_ = (int(v) for v in item.split(":"))
-        E = sstep.Solver(A, s=s_, sweeps=nu_, algo="onesync", **common)
+        E = sstep.Solver(A, s=s_, sweeps=nu_, algo=args.algo, **common)
         ems, einfos = timed_solves(E, xd, 1, 1)
         extra[f"s{s_}_nu{nu_}"] = {"s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
                                    "relres_true": einfos[0].relres_true}
@@ -352,27 +361,37 @@ def main():
     # ---- roofline of each kernel from the phase times
     work = kernel_work(args.s, n)
     hbm, hbm_src = hbm_peak()
+    if args.algo == "literal":
+        phases = {"mpk": ph[0], "gram_b2": ph[1], "update_w": ph[2], "update_xr": ph[3]}
+        kernels = (("mpk_step", ph[0] / args.s), ("gram_b2", ph[1]), ("update_w", ph[2]),
+                   ("update_xr", ph[3]))
+        phase_kernel = {"mpk": "mpk_step", "gram_b2": "gram_b2", "update_w": "update_w",
+                        "update_xr": "update_xr"}
+    else:
+        phases = {"mpk": ph[0], "gram": ph[1], "update": ph[2]}
+        kernels = (("mpk_step", ph[0] / args.s), ("gram", ph[1]), ("update", ph[2]))
+        phase_kernel = {"mpk": "mpk_step", "gram": "gram", "update": "update"}
     per = {}
-    for name, t_ms, launches in (("mpk_step", ph[0] / args.s, args.s), ("gram", ph[1], 1),
-                                 ("update", ph[2], 1), ("pcg_spmv_dot", pph[0], 1),
-                                 ("pcg_update", pph[1], 1), ("pcg_pdir", pph[2], 1)):
+    for name, t_ms in kernels + (("pcg_spmv_dot", pph[0]), ("pcg_update", pph[1]),
+                                 ("pcg_pdir", pph[2])):
         w = work[name]
         per[name] = {"ms_per_launch": t_ms, "GB_s": w["bytes"] / (t_ms * 1e-3) / 1e9,
                      "TFLOP_s": w["flops"] / (t_ms * 1e-3) / 1e12,
                      "hbm_frac": w["bytes"] / (t_ms * 1e-3) / 1e9 / hbm,
                      "fp64_frac": w["flops"] / (t_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
-    share = {"mpk": ph[0], "gram": ph[1], "update": ph[2]}
-    dom = max(share, key=share.get)
-    dom_kernel = {"mpk": "mpk_step", "gram": "gram", "update": "update"}[dom]
+    dom = max(phases, key=phases.get)
+    dom_kernel = phase_kernel[dom]
     d = per[dom_kernel]
-    workload = f"poisson7_{N}^3_{args.form}_jacobi_s{args.s}_nu{args.sweeps}"
-    src = source_hash("paper_2603_09790_gb300/csrc/k_blas.cu", "paper_2603_09790_gb300/csrc/k_operator.cu",
-                      "paper_2603_09790_gb300/csrc/common.cuh")
+    workload = f"poisson7_{N}^3_{args.form}_jacobi_{args.algo}_s{args.s}_nu{args.sweeps}"
+    # the counters stay valid only while the kernel's source is the one they were taken on
+    kfile = "k_operator.cu" if dom_kernel == "mpk_step" else "k_blas.cu"
+    src = source_hash("paper_2603_09790_gb300/csrc/" + kfile, "paper_2603_09790_gb300/csrc/common.cuh")
     traffic = load_traffic(dom_kernel, workload, src)
     roofline = {"bound": "alu", "kernel": dom_kernel, "achieved": d["TFLOP_s"],
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": d["TFLOP_s"] / FP64_PEAK_TFLOPS,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "traffic": traffic, "algorithmic_bytes": work[dom_kernel]["bytes"],
+                "algorithmic_flops": work[dom_kernel]["flops"],
                 "hbm_GB_s": d["GB_s"], "hbm_peak_GB_s": hbm, "hbm_peak_source": hbm_src,
                 "hbm_frac": d["hbm_frac"],
                 "timing": "CUDA events on the solver's stream between the phases of 5 outer "
@@ -383,7 +402,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload, "n": n, "grid": list(dims), "stencil": 7, "form": args.form,
-                   "precond": "jacobi", "s": args.s, "sweeps": args.sweeps, "rtol": 1e-8,
+                   "precond": "jacobi", "algo": args.algo, "s": args.s, "sweeps": args.sweeps,
+                   "rtol": 1e-8,
                    "power_iters": 20, "lambda_min": basis["lambda_min"],
                    "lambda_max": basis["lambda_max"], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (each vector 134 MB; working set > 4 GB)"},
@@ -396,12 +416,13 @@ def main():
         "e2e": {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(info.launches),
-        "phase_ms_per_outer": {"mpk": ph[0], "gram": ph[1], "update": ph[2]},
+        "phase_ms_per_outer": phases,
         "per_kernel": per, "roofline": roofline, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_power, t_outer, t_pcg = oracle_sample(N, args.s, args.sweeps, basis["lambda_max"])
-        counts = oracle_counts().get(f"s{args.s}nu{args.sweeps}")
+        t_power, t_outer, t_pcg = oracle_sample(N, args.s, args.sweeps, basis["lambda_max"],
+                                                algo=args.algo)
+        counts = oracle_counts().get(f"{args.algo}_s{args.s}nu{args.sweeps}")
         n_outer = counts["iters"] if counts and N == 256 else info.outer_iters
         v = t_power + t_outer * n_outer
         line["cpu_baseline"] = {

@@ -81,7 +81,10 @@ typedef struct {
 enum {
   SSTEP_ALGO_ONESYNC = 0, /* Algorithm 1 with the Gram blocks of [Q_k, Z_{k+1}] formed in one
                              reduction per outer iteration (W_{k+1} assembled from them and beta) */
-  SSTEP_ALGO_LITERAL = 1, /* Algorithm 1 line by line: W, b1 after the update, b2 after the MPK */
+  SSTEP_ALGO_LITERAL = 1, /* Algorithm 1 as printed: W = Q^T AQ, b1 = Q^T r formed from the updated
+                             blocks (line 15 and lines 5-6 fused in one pass), b2 after the MPK.
+                             Fewer FP64 products than the one-reduction form (2s^2 + s against
+                             4s^2 + 2s per outer iteration); the default */
   SSTEP_ALGO_PCG = 2      /* classical preconditioned CG (Hestenes-Stiefel), the comparator */
 };
 enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1 };
@@ -120,7 +123,7 @@ typedef struct {
                              including launches after convergence that return at entry) */
 } sstep_info;
 
-/* Fill *o with the defaults: s = 4, sweeps = 2, rtol = 1e-8, max_outer = 10000, one-sync,
+/* Fill *o with the defaults: s = 4, sweeps = 2, rtol = 1e-8, max_outer = 10000, literal form,
  * FGS, power_iters = 50, power_tol = 1e-3, lambda_min = 0, lambda_max = 0 (estimate). */
 SSTEP_API void sstep_default_opts(sstep_opts* o);
 
@@ -219,10 +222,11 @@ SSTEP_API sstep_status sstep_get_history(sstep_handle h, double* relres, int max
 /* Device time per phase of one outer iteration, measured with CUDA events on the handle's
  * stream: starting from x = 0 for right-hand side b (device or host, n doubles), runs the first
  * outer iteration and then `iters` more without a stop test, launched one by one.  ms (host,
- * 4 doubles) receives the averages per outer iteration: PCG-S one-sync: [MPK (all s steps),
- * Gram reduction + reduced solves, block update, sum]; PCG: [A p and p^T A p, x/r update with
- * r^T z, direction update, sum].  The handle's own x, r and basis blocks are overwritten; the
- * literal form returns SSTEP_ERR_UNSUPPORTED. */
+ * 5 doubles) receives the averages per outer iteration of 4 phases and their sum:
+ * literal form: [MPK (all s steps), b2 = -Q^T AZ with beta, line 15 fused with W, b1 and alpha,
+ * x/r update with the stop test]; one-reduction form: [MPK, Gram reduction with the reduced
+ * solves, block update, 0]; PCG: [A p with p^T A p, x/r/z update, direction update, 0].
+ * The handle's own x, r and basis blocks are overwritten. */
 SSTEP_API sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* ms);
 
 #ifdef __cplusplus

@@ -96,9 +96,11 @@ sstep_status alloc(double** p, int64_t count) {
 
 // ---------------------------------------------------------------- kernel sequences
 
-// Every Gram block as computed (Algorithm 1), or the symmetric shortcut (opt-in).
+// Every Gram block as computed (Algorithm 1), or the symmetric shortcut (opt-in, one-reduction
+// form only: the literal form always forms W = Q^T AQ in full, as line 5 prints it).
 int full_blocks(const sstep_ctx* h) {
-  return (h->o.gram_solver == SSTEP_GRAM_CHOLESKY || h->o.gram_blocks != SSTEP_GRAM_BLOCKS_SYM) ? 1 : 0;
+  return (h->o.algo == SSTEP_ALGO_LITERAL || h->o.gram_solver == SSTEP_GRAM_CHOLESKY ||
+          h->o.gram_blocks != SSTEP_GRAM_BLOCKS_SYM) ? 1 : 0;
 }
 
 EpiArgs epi_base(sstep_ctx* h, int epi) {
@@ -132,6 +134,7 @@ sstep_status run_mpk(sstep_ctx* h, const double* r, double* Z, double* AZ, int s
     }
     e.y = AZ + (q - 1) * ld;
     e.znext = q < s ? Z + q * ld : nullptr;
+    e.a1u = e.c1 * h->M.dinv_u;
     CK(launch_operator(h->op, e, h->st));
     ++h->nlaunch;
   }
@@ -141,6 +144,16 @@ sstep_status run_mpk(sstep_ctx* h, const double* r, double* Z, double* AZ, int s
 sstep_status run_gram(sstep_ctx* h, int mode) {
   const int s = h->s;
   const int64_t ld = h->ld;
+  if (full_blocks(h)) {
+    cudaError_t e = launch_gram_tiled(mode, s, h->n, ld, h->Q, h->AQ, h->Z, h->AZ, h->r, h->ctrl,
+                                      h->partials, h->st);
+    if (e == cudaSuccess) {
+      ++h->nlaunch;
+      return SSTEP_OK;
+    }
+    if (e != cudaErrorNotSupported) CK(e);
+    cudaGetLastError();
+  }
   GramArgs g{};
   g.n = h->n;
   g.mode = mode;
@@ -204,6 +217,26 @@ sstep_status run_update(sstep_ctx* h, int mode) {
   return SSTEP_OK;
 }
 
+// Line 15 (Q <- Z + Q beta, AQ <- AZ + AQ beta; first: Q <- Z, AQ <- AZ as in line 3) followed
+// by lines 5-6 (W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)).  Fused in one pass for s <= 8.
+sstep_status run_upd_w(sstep_ctx* h, bool first) {
+  UpdGramArgs a{h->n, h->ld, h->Z, h->AZ, h->Q, h->AQ, h->r, h->ctrl, h->partials};
+  cudaError_t e = launch_upd_gram(a, h->s, first, h->st);
+  if (e == cudaSuccess) {
+    ++h->nlaunch;
+    return SSTEP_OK;
+  }
+  if (e != cudaErrorNotSupported) CK(e);
+  cudaGetLastError();
+  if (first) {
+    CK(cudaMemcpyAsync(h->Q, h->Z, sizeof(double) * h->ld * h->s, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->AQ, h->AZ, sizeof(double) * h->ld * h->s, cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CKS(run_update(h, UM_QAQ));
+  }
+  return run_gram(h, GM_LITERAL_W);
+}
+
 // One outer iteration k >= 1 of each algorithm (what the graph captures).
 sstep_status outer_iteration(sstep_ctx* h, int algo) {
   if (algo == SSTEP_ALGO_ONESYNC) {
@@ -211,11 +244,11 @@ sstep_status outer_iteration(sstep_ctx* h, int algo) {
     CKS(run_gram(h, GM_ONESYNC));
     CKS(run_update(h, UM_FUSED));
   } else if (algo == SSTEP_ALGO_LITERAL) {
-    CKS(run_gram(h, GM_LITERAL_W));       // lines 5-6
-    CKS(run_update(h, UM_XR));            // lines 7-9
+    // One outer iteration of Algorithm 1 starting at line 10 (the first update ran before):
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // lines 10-11
-    CKS(run_gram(h, GM_LITERAL_B2));      // lines 12-13
-    CKS(run_update(h, UM_QAQ));           // line 15
+    CKS(run_gram(h, GM_LITERAL_B2));                     // lines 12-13: b2, beta
+    CKS(run_upd_w(h, false));                            // line 15, then lines 5-6: W, b1, alpha
+    CKS(run_update(h, UM_XR));                           // lines 7-9
   } else {
     EpiArgs e = epi_base(h, EP_PCG_AP);
     e.u = h->p;
@@ -579,9 +612,11 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
       CKS(run_update(h, UM_FIRST));
     }
   } else if (algo == SSTEP_ALGO_LITERAL) {
-    CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // lines 2-3
-    CK(cudaMemcpyAsync(h->Q, h->Z, sizeof(double) * h->ld * h->s, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->AQ, h->AZ, sizeof(double) * h->ld * h->s, cudaMemcpyDeviceToDevice, h->st));
+    if (maxit > 0) {
+      CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // line 2
+      CKS(run_upd_w(h, true));                            // line 3, lines 5-6
+      CKS(run_update(h, UM_XR));                          // lines 7-9
+    }
   } else {
     PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, h->hist};
     CK(launch_pcg_init(a, h->st));
@@ -590,7 +625,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   CKS(ensure_graph(h, algo));
   // Replay the captured outer iteration; poll the stop flag one batch behind.
   const int B = auto_check_every(h);
-  int launched = (algo == SSTEP_ALGO_ONESYNC) ? 1 : 0;
+  int launched = (algo == SSTEP_ALGO_PCG) ? 0 : 1;  // PCG-S ran its first outer iteration above
   bool finished = false;
   Ctrl* hc = h->hctrl;
   int* flags = h->poll_flags;
@@ -677,7 +712,7 @@ void sstep_default_opts(sstep_opts* o) {
   o->sweeps = 2;
   o->rtol = 1e-8;
   o->max_outer = 10000;
-  o->algo = SSTEP_ALGO_ONESYNC;
+  o->algo = SSTEP_ALGO_LITERAL;
   o->gram_solver = SSTEP_GRAM_FGS;
   o->power_iters = 50;
   o->power_tol = 1e-3;
@@ -869,7 +904,6 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   g_err.clear();
   if (!h || !b || !ms || iters < 1) return fail(SSTEP_ERR_INVALID, "bad profile arguments");
   const int algo = h->o.algo;
-  if (algo == SSTEP_ALGO_LITERAL) return fail(SSTEP_ERR_UNSUPPORTED, "profile: one-sync or PCG only");
   CK(cudaMemcpyAsync(h->b, b, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
   CK(cudaMemsetAsync(h->x, 0, sizeof(double) * h->n, h->st));
   CKS(reset_ctrl(h));
@@ -887,48 +921,69 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_gram(h, GM_ONESYNC_FIRST));
     CKS(run_update(h, UM_FIRST));
+  } else if (algo == SSTEP_ALGO_LITERAL) {
+    CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
+    CKS(run_upd_w(h, true));
+    CKS(run_update(h, UM_XR));
   } else {
     PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, nullptr};
     CK(launch_pcg_init(a, h->st));
   }
-  cudaEvent_t ev[4];
+  constexpr int kPh = 4;
+  cudaEvent_t ev[kPh + 1];
   for (auto& e : ev) CK(cudaEventCreate(&e));
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[kPh] = {0.0, 0.0, 0.0, 0.0};
   sstep_status st = SSTEP_OK;
+  auto ok = [&](sstep_status v) { if (st == SSTEP_OK) st = v; };
+  auto okc = [&](cudaError_t v) { if (st == SSTEP_OK && v != cudaSuccess) st = fail(SSTEP_ERR_CUDA, cudaGetErrorString(v)); };
   for (int k = 0; k < iters && st == SSTEP_OK; ++k) {
     cudaEventRecord(ev[0], h->st);
     if (algo == SSTEP_ALGO_ONESYNC) {
-      st = run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl);
+      ok(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
       cudaEventRecord(ev[1], h->st);
-      if (st == SSTEP_OK) st = run_gram(h, GM_ONESYNC);
+      ok(run_gram(h, GM_ONESYNC));
       cudaEventRecord(ev[2], h->st);
-      if (st == SSTEP_OK) st = run_update(h, UM_FUSED);
+      ok(run_update(h, UM_FUSED));
+      cudaEventRecord(ev[3], h->st);
+    } else if (algo == SSTEP_ALGO_LITERAL) {
+      ok(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
+      cudaEventRecord(ev[1], h->st);
+      ok(run_gram(h, GM_LITERAL_B2));
+      cudaEventRecord(ev[2], h->st);
+      ok(run_upd_w(h, false));
+      cudaEventRecord(ev[3], h->st);
+      ok(run_update(h, UM_XR));
     } else {
       EpiArgs e = epi_base(h, EP_PCG_AP);
       e.u = h->p;
       e.y = h->Ap;
       PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, nullptr};
-      if (launch_operator(h->op, e, h->st) != cudaSuccess) st = SSTEP_ERR_CUDA;
+      okc(launch_operator(h->op, e, h->st));
       cudaEventRecord(ev[1], h->st);
-      if (launch_pcg_update(a, h->st) != cudaSuccess) st = SSTEP_ERR_CUDA;
+      okc(launch_pcg_update(a, h->st));
       cudaEventRecord(ev[2], h->st);
-      if (launch_pcg_pdir(a, h->st) != cudaSuccess) st = SSTEP_ERR_CUDA;
+      okc(launch_pcg_pdir(a, h->st));
+      cudaEventRecord(ev[3], h->st);
     }
-    cudaEventRecord(ev[3], h->st);
-    cudaError_t e = cudaEventSynchronize(ev[3]);
-    if (e != cudaSuccess) st = fail(SSTEP_ERR_CUDA, cudaGetErrorString(e));
-    for (int p = 0; p < 3 && st == SSTEP_OK; ++p) {
+    cudaEventRecord(ev[4], h->st);
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) okc(e);
+    for (int p = 0; p < kPh && st == SSTEP_OK; ++p) {
       float t = 0.f;
       cudaEventElapsedTime(&t, ev[p], ev[p + 1]);
       acc[p] += t;
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  if (st != SSTEP_OK) return st == SSTEP_ERR_CUDA && g_err.empty() ? fail(st, "profile launch failed") : st;
+  if (st != SSTEP_OK) return st;
   CKS(read_ctrl(h));
   if (h->hctrl->done) return fail(SSTEP_ERR_BREAKDOWN, "profile: the iteration stopped early");
-  for (int p = 0; p < 3; ++p) ms[p] = acc[p] / iters;
-  ms[3] = ms[0] + ms[1] + ms[2];
+  double sum = 0.0;
+  for (int p = 0; p < kPh; ++p) {
+    ms[p] = acc[p] / iters;
+    sum += ms[p];
+  }
+  ms[kPh] = sum;
   return SSTEP_OK;
 }
 

@@ -205,6 +205,7 @@ struct EpiArgs {
   const double* zprev;  // MPK: z_{q-1} (null on the second basis vector)
   const double* b;      // residual epilogues
   double c1, c2, c3;    // recurrence coefficients
+  double a1u;           // c1 * M^{-1} when M^{-1} is a uniform scalar
   Prec M;
   Ctrl* ctrl;
   double* partials;
@@ -224,6 +225,37 @@ struct GramArgs {
   double* out;        // optional copy of the sums (GM_SUMS)
 };
 cudaError_t launch_gram(const GramArgs& g, cudaStream_t st);
+
+// Register-tiled Gram products for the structured modes (every block formed, s <= 8).
+constexpr int kTileMaxR = 8, kTileMaxC = 17, kMaxTiles = 4;
+constexpr int kTiledSmem = 8 * 72 > 1100 ? 8 * 72 : 1100;  // warp partials / sums + tail scratch
+struct GramTiles {
+  int64_t n;
+  int ntiles, mode, ne;
+  const double* x[kMaxTiles][kTileMaxR];
+  const double* y[kMaxTiles][kTileMaxC];
+  short out[kMaxTiles][kTileMaxR * kTileMaxC];  // entry of product (i, j), -1 = not needed
+  Ctrl* ctrl;
+  double* partials;
+};
+// Line 15 fused with line 5 of the next outer iteration (see k_upd_gram), s <= 8.
+struct UpdGramArgs {
+  int64_t n, ld;
+  const double* Z;
+  const double* AZ;
+  double* Q;
+  double* AQ;
+  const double* r;
+  Ctrl* ctrl;
+  double* partials;
+};
+cudaError_t launch_upd_gram(const UpdGramArgs& a, int s, bool first, cudaStream_t st);
+
+// Builds the tiles of a Gram mode from the solver's blocks (leading dimension ld) and launches;
+// returns cudaErrorNotSupported when the mode/s has no tiled form (caller falls back).
+cudaError_t launch_gram_tiled(int mode, int s, int64_t n, int64_t ld, const double* Q,
+                              const double* AQ, const double* Z, const double* AZ, const double* r,
+                              Ctrl* ctrl, double* partials, cudaStream_t st);
 cudaError_t gram_init();  // sets the Gram kernels' dynamic shared-memory limit (call outside capture)
 // Pair list of a Gram mode (returns ne; fills nl, nr), and the CTA count of launch_gram.
 int gram_pairs(int mode, int s, int full, unsigned short* pairs, int* nl, int* nr);

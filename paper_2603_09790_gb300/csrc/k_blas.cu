@@ -145,8 +145,7 @@ struct OneSyncIdx {
 };
 
 // The tail: executed by the last CTA after the reduction, with the sums in shared memory.
-__device__ void gram_tail(const GramArgs& g, const double* sums, double* sh) {
-  Ctrl* c = g.ctrl;
+__device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
   const int s = c->s, nu = c->nu, solver = c->solver;
   const Layout L{s, c->full_gram};
   double* W = sh;               // s*s
@@ -160,7 +159,7 @@ __device__ void gram_tail(const GramArgs& g, const double* sums, double* sh) {
   double* scr = b1 + s;         // s*s + s
   const int tid = threadIdx.x;
   bool ok = true;
-  if (g.mode == GM_ONESYNC_FIRST || g.mode == GM_LITERAL_W) {
+  if (mode == GM_ONESYNC_FIRST || mode == GM_LITERAL_W) {
     // W = V^T AV (V = Z_0 or Q_k), b1 = V^T r;  alpha = FGS(W, b1)       (lines 5-6)
     for (int e = tid; e < s * s; e += blockDim.x) {
       const int i = e % s, j = e / s;
@@ -173,7 +172,7 @@ __device__ void gram_tail(const GramArgs& g, const double* sums, double* sh) {
       for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = X[i];
       for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
     }
-  } else if (g.mode == GM_LITERAL_B2) {
+  } else if (mode == GM_LITERAL_B2) {
     // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (lines 12-13)
     for (int e = tid; e < s * s; e += blockDim.x) {
       W[e] = c->W[e];
@@ -183,7 +182,7 @@ __device__ void gram_tail(const GramArgs& g, const double* sums, double* sh) {
     ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
     if (ok)
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
-  } else if (g.mode == GM_ONESYNC) {
+  } else if (mode == GM_ONESYNC) {
     const OneSyncIdx I{L};
     for (int e = tid; e < s * s; e += blockDim.x) {
       const int i = e % s, j = e / s;
@@ -333,7 +332,177 @@ __global__ void __launch_bounds__(kThreads) k_gram(GramArgs g, int nch, int rp) 
     g.ctrl->sums[e] = sums[e];
     if (g.out) g.out[e] = sums[e];
   }
-  if (g.mode != GM_SUMS) gram_tail(g, sums, sums + g.ne);
+  if (g.mode != GM_SUMS) gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
+}
+
+// ---------------------------------------------------------------- register-tiled Gram kernel
+
+// Tall-skinny products X^T Y with every product of an NR x NC tile accumulated in registers:
+// a thread streams rows (points) p with a grid stride, loads NR + NC values per row and
+// issues NR * NC independent FP64 FMAs, so the FP64 pipe is fed without shared memory or
+// barriers in the main loop.  blockIdx.y selects the tile; all tiles of a launch have the
+// same shape.  Partials per CTA are written in a fixed order and the last CTA to finish sums
+// them (fixed order), then solves the reduced systems exactly as k_gram does.
+template <int NR, int NC>
+__global__ void __launch_bounds__(kThreads, 1) k_gram_tiled(GramTiles g) {
+  if (g.ctrl->done) return;
+  constexpr int K = NR * NC;
+  const int t = blockIdx.y;
+  const double* xp[NR];
+  const double* yp[NC];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) xp[i] = g.x[t][i];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) yp[j] = g.y[t][j];
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += stride) {
+    double xv[NR], yv[NC];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) xv[i] = __ldg(xp[i] + p);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) yv[j] = __ldg(yp[j] + p);
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[i * NC + j] = fma(xv[i], yv[j], acc[i * NC + j]);
+  }
+  // CTA reduction: warp shuffles, then the warps in order.
+  __shared__ double buf[kTiledSmem];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) buf[wid * K + k] = v;
+  }
+  __syncthreads();
+  const unsigned int cta = blockIdx.x + gridDim.x * blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    g.partials[(size_t)cta * K + k] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int tk = atomicAdd(&g.ctrl->ticket[TK_GRAM], 1u);
+    last = (tk == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double* sums = buf;  // ne entries, then the tail's scratch
+  for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
+    const int tt = idx / K, k = idx % K;
+    const int e = g.out[tt][k];
+    if (e < 0) continue;
+    double v = 0.0;
+    for (unsigned int bx = 0; bx < gridDim.x; ++bx)
+      v += __ldcg(g.partials + ((size_t)tt * gridDim.x + bx) * K + k);
+    sums[e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) g.ctrl->ticket[TK_GRAM] = 0u;
+  for (int e = threadIdx.x; e < g.ne; e += blockDim.x) g.ctrl->sums[e] = sums[e];
+  gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
+}
+
+// ---------------------------------------------------------------- update fused with line 5
+
+// Algorithm 1 line 15 of outer iteration k fused with line 5 of iteration k+1, in one pass:
+// Q <- Z + Q beta, AQ <- AZ + AQ beta (FIRST: Q <- Z, AQ <- AZ, Algorithm 1 line 3), then
+// W = Q^T AQ and b1 = Q^T r accumulated in registers from the new columns while they are in
+// registers.  The last CTA sums the per-CTA partials in a fixed order and solves
+// alpha = FGS(W, b1) (line 6).  Entries: W_ij at i + j s, b1_i at s^2 + i.
+template <int S, bool FIRST>
+__global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
+  if (a.ctrl->done) return;
+  constexpr int K = S * S + S;
+  __shared__ double sb[S * S];
+  __shared__ double buf[kTiledSmem];
+  if (!FIRST)
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = a.ctrl->beta[e];
+  __syncthreads();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const int64_t ld = a.ld;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
+    double qn[S], an[S];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        qn[j] = __ldg(a.Z + j * ld + p);
+        an[j] = __ldg(a.AZ + j * ld + p);
+      }
+    } else {
+      double qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = a.Q[l * ld + p];
+        ao[l] = a.AQ[l * ld + p];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        double vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          vq = fma(qo[l], sb[l + j * S], vq);
+          va = fma(ao[l], sb[l + j * S], va);
+        }
+        qn[j] = vq;
+        an[j] = va;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      a.Q[j * ld + p] = qn[j];
+      a.AQ[j * ld + p] = an[j];
+    }
+    const double rp = __ldg(a.r + p);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc[i + j * S] = fma(qn[i], an[j], acc[i + j * S]);
+      acc[S * S + i] = fma(qn[i], rp, acc[S * S + i]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) buf[wid * K + k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    a.partials[(size_t)blockIdx.x * K + k] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int tk = atomicAdd(&a.ctrl->ticket[TK_GRAM], 1u);
+    last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double* sums = buf;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (unsigned int bx = 0; bx < gridDim.x; ++bx) v += __ldcg(a.partials + (size_t)bx * K + k);
+    sums[k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.ctrl->ticket[TK_GRAM] = 0u;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = sums[e];
+  gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + K);
 }
 
 // ---------------------------------------------------------------- fused block update
@@ -678,6 +847,154 @@ cudaError_t launch_gram(const GramArgs& g, cudaStream_t st) {
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+namespace {
+
+template <int NR, int NC>
+cudaError_t launch_tiled_shape(const GramTiles& g, cudaStream_t st) {
+  static int occ = 0;
+  if (!occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_tiled<NR, NC>, kThreads, 0);
+    if (occ < 1) occ = 1;
+  }
+  const int64_t want = ((int64_t)sm_count() * occ + g.ntiles - 1) / g.ntiles;
+  const int64_t rows = (g.n + kThreads - 1) / kThreads;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, rows));
+  k_gram_tiled<NR, NC><<<dim3(gx, g.ntiles), kThreads, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+template <int NR>
+cudaError_t launch_tiled_nr(const GramTiles& g, int nc, cudaStream_t st) {
+  if (nc == NR) return launch_tiled_shape<NR, NR>(g, st);
+  if (nc == NR + 1) return launch_tiled_shape<NR, NR + 1>(g, st);
+  if constexpr (NR <= 4) {  // the two-tile one-reduction layout is used up to s = 4
+    if (nc == 2 * NR + 1) return launch_tiled_shape<NR, 2 * NR + 1>(g, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tiled(int mode, int s, int64_t n, int64_t ld, const double* Q,
+                              const double* AQ, const double* Z, const double* AZ, const double* r,
+                              Ctrl* ctrl, double* partials, cudaStream_t st) {
+  if (s < 1 || s > kTileMaxR) return cudaErrorNotSupported;
+  GramTiles g{};
+  g.n = n;
+  g.mode = mode;
+  g.ctrl = ctrl;
+  g.partials = partials;
+  for (auto& tt : g.out)
+    for (auto& o : tt) o = -1;
+  const int s2 = s * s;
+  auto col = [&](const double* base, int j) { return base + (int64_t)j * ld; };
+  int nc = 0;
+  if (mode == GM_ONESYNC_FIRST || mode == GM_LITERAL_W) {
+    // W = V^T AV (entry i + j s), b1 = V^T r (entry s^2 + i); V = Z or Q
+    const double* V = mode == GM_ONESYNC_FIRST ? Z : Q;
+    const double* AV = mode == GM_ONESYNC_FIRST ? AZ : AQ;
+    g.ntiles = 1;
+    nc = s + 1;
+    for (int i = 0; i < s; ++i) g.x[0][i] = col(V, i);
+    for (int j = 0; j < s; ++j) g.y[0][j] = col(AV, j);
+    g.y[0][s] = r;
+    for (int i = 0; i < s; ++i) {
+      for (int j = 0; j < s; ++j) g.out[0][i * nc + j] = (short)(i + j * s);
+      g.out[0][i * nc + s] = (short)(s2 + i);
+    }
+    g.ne = s2 + s;
+  } else if (mode == GM_LITERAL_B2) {
+    g.ntiles = 1;  // Q^T AZ, entry i + j s
+    nc = s;
+    for (int i = 0; i < s; ++i) g.x[0][i] = col(Q, i);
+    for (int j = 0; j < s; ++j) g.y[0][j] = col(AZ, j);
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) g.out[0][i * nc + j] = (short)(i + j * s);
+    g.ne = s2;
+  } else if (mode == GM_ONESYNC) {
+    // Entries (every block formed): G1 = Q^T AQ, G2 = Q^T AZ, G3 = Z^T AQ, G4 = Z^T AZ
+    // (each i + j s after its base), g5 = Q^T r, g6 = Z^T r.
+    const int b1 = 0, b2 = s2, b3 = 2 * s2, b4 = 3 * s2, b5 = 4 * s2, b6 = 4 * s2 + s;
+    g.ne = 4 * s2 + 2 * s;
+    if (2 * s + 1 <= kTileMaxC && s <= 4) {
+      // two tiles: Q^T [AQ AZ r] and Z^T [AQ AZ r]
+      g.ntiles = 2;
+      nc = 2 * s + 1;
+      for (int t = 0; t < 2; ++t) {
+        const double* X = t == 0 ? Q : Z;
+        for (int i = 0; i < s; ++i) g.x[t][i] = col(X, i);
+        for (int j = 0; j < s; ++j) {
+          g.y[t][j] = col(AQ, j);
+          g.y[t][s + j] = col(AZ, j);
+        }
+        g.y[t][2 * s] = r;
+        for (int i = 0; i < s; ++i) {
+          for (int j = 0; j < s; ++j) {
+            g.out[t][i * nc + j] = (short)((t == 0 ? b1 : b3) + i + j * s);
+            g.out[t][i * nc + s + j] = (short)((t == 0 ? b2 : b4) + i + j * s);
+          }
+          g.out[t][i * nc + 2 * s] = (short)((t == 0 ? b5 : b6) + i);
+        }
+      }
+    } else {
+      // four tiles: {Q, Z}^T [AQ r] and {Q, Z}^T [AZ r]; r kept once per X
+      g.ntiles = 4;
+      nc = s + 1;
+      for (int t = 0; t < 4; ++t) {
+        const double* X = t < 2 ? Q : Z;
+        const double* Y = (t & 1) ? AZ : AQ;
+        const int base = t == 0 ? b1 : t == 1 ? b2 : t == 2 ? b3 : b4;
+        for (int i = 0; i < s; ++i) g.x[t][i] = col(X, i);
+        for (int j = 0; j < s; ++j) g.y[t][j] = col(Y, j);
+        g.y[t][s] = r;
+        for (int i = 0; i < s; ++i) {
+          for (int j = 0; j < s; ++j) g.out[t][i * nc + j] = (short)(base + i + j * s);
+          if (t == 0) g.out[t][i * nc + s] = (short)(b5 + i);
+          if (t == 2) g.out[t][i * nc + s] = (short)(b6 + i);
+        }
+      }
+    }
+  } else {
+    return cudaErrorNotSupported;
+  }
+  switch (s) {
+    case 1: return launch_tiled_nr<1>(g, nc, st);
+    case 2: return launch_tiled_nr<2>(g, nc, st);
+    case 3: return launch_tiled_nr<3>(g, nc, st);
+    case 4: return launch_tiled_nr<4>(g, nc, st);
+    case 5: return launch_tiled_nr<5>(g, nc, st);
+    case 6: return launch_tiled_nr<6>(g, nc, st);
+    case 7: return launch_tiled_nr<7>(g, nc, st);
+    case 8: return launch_tiled_nr<8>(g, nc, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+namespace {
+template <int S, bool FIRST>
+cudaError_t launch_upd_gram_s(const UpdGramArgs& a, cudaStream_t st) {
+  static int occ = 0;
+  if (!occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_upd_gram<S, FIRST>, kThreads, 0);
+    if (occ < 1) occ = 1;
+  }
+  const int64_t rows = (a.n + kThreads - 1) / kThreads;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, rows));
+  k_upd_gram<S, FIRST><<<gx, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_upd_gram(const UpdGramArgs& a, int s, bool first, cudaStream_t st) {
+  switch (s) {
+#define CASE(S) \
+  case S: return first ? launch_upd_gram_s<S, true>(a, st) : launch_upd_gram_s<S, false>(a, st);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return cudaErrorNotSupported;
+  }
 }
 
 cudaError_t gram_init() {

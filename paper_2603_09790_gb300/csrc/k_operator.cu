@@ -41,9 +41,12 @@ __device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t i, double y, 
     if constexpr (EPI == EP_MPK_FIRST) e.z1[i] = uc;  // z_1 = M^{-1} r
     e.y[i] = y;                                        // A z_q  (column q+1 of P)
     if (e.znext) {
-      const double d = prec_d(e.M, i);
-      const double t = e.zprev ? -e.c3 * __ldg(e.zprev + i) : 0.0;
-      e.znext[i] = fma(e.c1 * d, y, fma(-e.c2, uc, t));
+      // c1 M^{-1}: one product per point for a diagonal M, a kernel constant when uniform;
+      // c3 = gamma = 1 in the Chebyshev recurrence, so z_{q-1} enters without a product.
+      const double a = e.M.dinv ? e.c1 * __ldg(e.M.dinv + i) : e.a1u;
+      double t = 0.0;
+      if (e.zprev) t = e.c3 == 1.0 ? -__ldg(e.zprev + i) : -e.c3 * __ldg(e.zprev + i);
+      e.znext[i] = fma(a, y, fma(-e.c2, uc, t));
     }
   } else if constexpr (EPI == EP_RESID) {
     const double bi = __ldg(e.b + i);

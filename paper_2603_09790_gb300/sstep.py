@@ -181,7 +181,7 @@ class Solver:
     """A handle of libsstep.so (sstep_setup ... sstep_free)."""
 
     def __init__(self, A, *, precond="jacobi", s=4, sweeps=2, rtol=1e-8, max_outer=10000,
-                 algo="onesync", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
+                 algo="literal", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
                  lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", stream=None):
         lib = load()
         m = _Matrix()
@@ -275,7 +275,7 @@ class Solver:
 
     def profile(self, b, iters=5):
         """sstep_profile: average device ms per phase of one outer iteration (4 values)."""
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * 5)()
         _check(load().sstep_profile(self._h, _ptr(b), int(iters), ms))
         return list(ms)
 

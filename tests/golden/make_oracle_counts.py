@@ -4,7 +4,8 @@ lambda_max from 20 power iterations with start vector seed 1, Gershgorin lower b
 
 Calls only the oracle (and the seeded input module).  Slow: tens of minutes of one CPU core
 per configuration.  Usage: python tests/golden/make_oracle_counts.py [config ...]
-where config is "pcg" or "s<S>nu<NU>" (default: pcg s2nu3 s4nu3).
+where config is "pcg" or "<literal|onesync>_s<S>nu<NU>"
+(default: pcg literal_s4nu3 literal_s4nu30).
 """
 import json
 import os
@@ -32,8 +33,9 @@ def main(configs):
         if cfg == "pcg":
             r = O.pcg(A, b, rtol=1e-8)
         else:
-            s, nu = cfg[1:].split("nu")
-            r = O.pcgs(A, b, s=int(s), nu=int(nu), rtol=1e-8, algo="onesync", lambda_min=lmin,
+            algo, rest = cfg.split("_")
+            s, nu = rest[1:].split("nu")
+            r = O.pcgs(A, b, s=int(s), nu=int(nu), rtol=1e-8, algo=algo, lambda_min=lmin,
                        lambda_max=lam)
         rec = dict(iters=r.iters, status=r.status, relres=r.relres, relres_true=r.relres_true,
                    lambda_max=lam, lambda_min=lmin, seconds_1core=time.time() - t)
@@ -45,4 +47,4 @@ def main(configs):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["pcg", "s2nu3", "s4nu3"])
+    main(sys.argv[1:] or ["pcg", "literal_s4nu3", "literal_s4nu30"])

@@ -370,3 +370,41 @@ def test_solve_batched():
             xs1 = dev(np.zeros(csr.n))
             S.solve(dev(b), xs1)
             assert torch.equal(x, xs1)
+
+
+@pytest.fixture(scope="module")
+def big_problem():
+    """The 256^3 7-point workload the benchmark times (x_true seed 0, b = A x_true)."""
+    dims = (256, 256, 256)
+    csr = O.CSR(*I.poisson_csr(dims, 7))
+    xt, b = I.poisson_problem(dims, 7)
+    return dims, csr, b
+
+
+def test_full_size_mpk_and_two_outer_iterations(big_problem):
+    """At the benchmark's size and launch configuration: Algorithm 2 (s = 4) element by element,
+    and two outer iterations of Algorithm 1 (literal form, nu = 3) against the oracle."""
+    dims, csr, b = big_problem
+    n = csr.n
+    A = sstep.Stencil(*dims, points=7)
+    s = 4
+    with sstep.Solver(A, s=s, sweeps=3, rtol=0.0, max_outer=2, lambda_min=-1.0, power_iters=20,
+                      power_tol=0.0, power_v0=dev(I.power_start(n))) as S:
+        bi = S.get_basis_info()
+        bd = dev(b)
+        Z = torch.empty(s * n, dtype=torch.float64, device=DEV)
+        AZ = torch.empty(s * n, dtype=torch.float64, device=DEV)
+        S.mpk(bd, Z, AZ)
+        Zg, AZg = host(Z).reshape(s, n), host(AZ).reshape(s, n)
+        xd = dev(np.zeros(n))
+        info = S.solve(bd, xd)
+        x = host(xd)
+    Zo, Po = O.mpk(csr, "jacobi", b, s, bi["c_alpha"], bi["c_sigma"], bi["c_gamma"])
+    for j in range(s):
+        assert np.max(np.abs(Zg[j] - Zo[j])) <= 1e-12 * (j + 1) * np.abs(Zo[j]).max()
+        assert np.max(np.abs(AZg[j] - Po[j + 1])) <= 1e-12 * (j + 1) * np.abs(Po[j + 1]).max()
+    del Zg, AZg, Zo, Po
+    ref = O.pcgs(csr, b, s=s, nu=3, rtol=0.0, max_outer=2, algo="literal",
+                 lambda_min=bi["lambda_min"], lambda_max=bi["lambda_max"])
+    assert info.outer_iters == 2
+    assert relerr(x, ref.x) <= 1e-9
