@@ -198,6 +198,20 @@ def oracle_counts():
         return {}
 
 
+# ---------------------------------------------------------------- ranks
+
+def reduce_over_ranks(value, world, device):
+    """Max over ranks of a per-rank time (replicas: every rank solves its own copy of the
+    problem; the job's time per step is that of the slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -314,11 +328,7 @@ def main():
     ms, infos = timed_solves(S, xd, args.steps, 0)
     clocks = sampler.stop()
     ms_step = float(np.mean(ms))
-    ms_max = ms_step
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_over_ranks(ms_step, world, dev)
     info = infos[-1]
     basis = S.get_basis_info()
 

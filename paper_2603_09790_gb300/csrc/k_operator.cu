@@ -131,11 +131,40 @@ __device__ __forceinline__ void reduce_and_finish(const EpiArgs& e, double* red)
 
 // ---------------------------------------------------------------- 5/7-point stencil
 
-// SCALE: multiply every loaded input value by M^{-1} (MPK first step, non-uniform M).
+// A(u) at one point of a 5/7-point stencil: in-plane neighbours from the staged plane p
+// (with its one-point halo), z neighbours ub (z-1) and ua (z+1) from registers.
+template <int PTS, bool POISSON>
+__device__ __forceinline__ double stencil7_point(const StencilOp& op, const double (*p)[TX + 2],
+                                                 int tx, int ty, double ub, double uc, double ua) {
+  if constexpr (POISSON) {
+    double s = (p[ty + 1][tx] + p[ty + 1][tx + 2]) + (p[ty][tx + 1] + p[ty + 2][tx + 1]);
+    if constexpr (PTS == 7) s += ub + ua;
+    return fma(op.wc, uc, -s);
+  } else if constexpr (PTS == 7) {
+    double a = op.w[0] * ub;
+    a = fma(op.w[1], p[ty][tx + 1], a);
+    a = fma(op.w[2], p[ty + 1][tx], a);
+    a = fma(op.w[3], uc, a);
+    a = fma(op.w[4], p[ty + 1][tx + 2], a);
+    a = fma(op.w[5], p[ty + 2][tx + 1], a);
+    return fma(op.w[6], ua, a);
+  } else {
+    double a = op.w[0] * p[ty][tx + 1];
+    a = fma(op.w[1], p[ty + 1][tx], a);
+    a = fma(op.w[2], uc, a);
+    a = fma(op.w[3], p[ty + 1][tx + 2], a);
+    return fma(op.w[4], p[ty + 2][tx + 1], a);
+  }
+}
+
+// Two z planes per iteration, two sets of staged planes (one barrier per iteration), and the
+// next iteration's centre and halo values loaded into registers before the barrier so that
+// their latency overlaps the arithmetic.  SCALE: multiply every loaded input value by M^{-1}
+// (MPK first step with a non-uniform M).
 template <int PTS, bool POISSON, int EPI, bool SCALE>
 __global__ void __launch_bounds__(TX * TY) k_stencil7(StencilOp op, EpiArgs e, int zc) {
   if (skip<EPI>(e)) return;
-  __shared__ double t[TY + 2][TX + 2];
+  __shared__ double t[2][2][TY + 2][TX + 2];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
   const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
@@ -144,58 +173,71 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7(StencilOp op, EpiArgs e, i
   const bool in = x < nx && y < ny;
   const int64_t col = (int64_t)y * nx + x;
   const double* __restrict__ u = e.u;
-  auto ld = [&](int64_t idx) -> double {
+  // Halo duty: threads on the tile's x edges load the x-1 / x+1 column, those on its y edges
+  // the y-1 / y+1 row; outside the grid the value is 0 (Dirichlet neighbours dropped).
+  const int hx = tx == 0 ? -1 : (tx == TX - 1 ? 1 : 0);
+  const int hy = ty == 0 ? -1 : (ty == TY - 1 ? 1 : 0);
+  const bool hxok = hx != 0 && x + hx >= 0 && x + hx < nx && y < ny;
+  const bool hyok = hy != 0 && y + hy >= 0 && y + hy < ny && x < nx;
+  const int64_t hxoff = col + hx, hyoff = col + (int64_t)hy * nx;
+  auto ld = [&](int64_t off, int zz, bool ok) -> double {
+    if (!ok || zz < 0 || zz >= nz) return 0.0;
+    const int64_t idx = off + (int64_t)zz * pxy;
     double v = __ldg(u + idx);
     if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
     return v;
   };
   double red[2] = {0.0, 0.0};
-  double ub = 0.0, uc = 0.0, ua = 0.0;
-  if (PTS == 7 && in && z0 >= 1) ub = ld(col + (int64_t)(z0 - 1) * pxy);
-  if (in && z0 < nz) uc = ld(col + (int64_t)z0 * pxy);
-  if (PTS == 7 && in && z0 + 1 < nz) ua = ld(col + (int64_t)(z0 + 1) * pxy);
-  for (int z = z0; z < z1; ++z) {
-    const int64_t pz = (int64_t)z * pxy;
-    t[ty + 1][tx + 1] = uc;
-    if (tx == 0) t[ty + 1][0] = (x >= 1 && y < ny) ? ld(pz + col - 1) : 0.0;
-    if (tx == TX - 1) t[ty + 1][TX + 1] = (x + 1 < nx && y < ny) ? ld(pz + col + 1) : 0.0;
-    if (ty == 0) t[0][tx + 1] = (y >= 1 && x < nx) ? ld(pz + col - nx) : 0.0;
-    if (ty == TY - 1) t[TY + 1][tx + 1] = (y + 1 < ny && x < nx) ? ld(pz + col + nx) : 0.0;
+  double ub = ld(col, z0 - 1, in), uc = ld(col, z0, in);
+  double ua = ld(col, z0 + 1, in), ua2 = ld(col, z0 + 2, in);
+  double hx0 = ld(hxoff, z0, hxok), hx1 = ld(hxoff, z0 + 1, hxok);
+  double hy0 = ld(hyoff, z0, hyok), hy1 = ld(hyoff, z0 + 1, hyok);
+  int set = 0;
+  for (int z = z0; z < z1; z += 2) {
+    double (*P0)[TX + 2] = t[set][0];
+    double (*P1)[TX + 2] = t[set][1];
+    P0[ty + 1][tx + 1] = uc;
+    P1[ty + 1][tx + 1] = ua;
+    if (hx) {
+      P0[ty + 1][tx + 1 + hx] = hx0;
+      P1[ty + 1][tx + 1 + hx] = hx1;
+    }
+    if (hy) {
+      P0[ty + 1 + hy][tx + 1] = hy0;
+      P1[ty + 1 + hy][tx + 1] = hy1;
+    }
+    // next pair of planes: centres z+3, z+4 and halos of z+2, z+3
+    const double n3 = ld(col, z + 3, in), n4 = ld(col, z + 4, in);
+    const double nhx0 = ld(hxoff, z + 2, hxok), nhx1 = ld(hxoff, z + 3, hxok);
+    const double nhy0 = ld(hyoff, z + 2, hyok), nhy1 = ld(hyoff, z + 3, hyok);
     __syncthreads();
     if (in) {
-      double a;
-      if constexpr (POISSON) {
-        double s = (t[ty + 1][tx] + t[ty + 1][tx + 2]) + (t[ty][tx + 1] + t[ty + 2][tx + 1]);
-        if constexpr (PTS == 7) s += ub + ua;
-        a = fma(op.wc, uc, -s);
-      } else if constexpr (PTS == 7) {
-        a = op.w[0] * ub;
-        a = fma(op.w[1], t[ty][tx + 1], a);
-        a = fma(op.w[2], t[ty + 1][tx], a);
-        a = fma(op.w[3], uc, a);
-        a = fma(op.w[4], t[ty + 1][tx + 2], a);
-        a = fma(op.w[5], t[ty + 2][tx + 1], a);
-        a = fma(op.w[6], ua, a);
-      } else {
-        a = op.w[0] * t[ty][tx + 1];
-        a = fma(op.w[1], t[ty + 1][tx], a);
-        a = fma(op.w[2], uc, a);
-        a = fma(op.w[3], t[ty + 1][tx + 2], a);
-        a = fma(op.w[4], t[ty + 2][tx + 1], a);
-      }
-      double ucc = uc;
+      double a0 = stencil7_point<PTS, POISSON>(op, P0, tx, ty, ub, uc, ua);
+      double c0 = uc;
       if constexpr (EPI == EP_MPK_FIRST && !SCALE) {  // uniform M^{-1}: A (d r) = d (A r)
-        a *= e.M.dinv_u;
-        ucc *= e.M.dinv_u;
+        a0 *= e.M.dinv_u;
+        c0 *= e.M.dinv_u;
       }
-      epilogue<EPI>(e, pz + col, a, ucc, red);
+      epilogue<EPI>(e, (int64_t)z * pxy + col, a0, c0, red);
+      if (z + 1 < z1) {
+        double a1 = stencil7_point<PTS, POISSON>(op, P1, tx, ty, uc, ua, ua2);
+        double c1 = ua;
+        if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
+          a1 *= e.M.dinv_u;
+          c1 *= e.M.dinv_u;
+        }
+        epilogue<EPI>(e, (int64_t)(z + 1) * pxy + col, a1, c1, red);
+      }
     }
-    __syncthreads();
-    if constexpr (PTS == 7) {
-      ub = uc;
-      uc = ua;
-      ua = (in && z + 2 < nz) ? ld(col + (int64_t)(z + 2) * pxy) : 0.0;
-    }
+    ub = ua;
+    uc = ua2;
+    ua = n3;
+    ua2 = n4;
+    hx0 = nhx0;
+    hx1 = nhx1;
+    hy0 = nhy0;
+    hy1 = nhy1;
+    set ^= 1;
   }
   reduce_and_finish<EPI>(e, red);
 }
@@ -359,6 +401,7 @@ StencilGrid stencil_grid(const StencilOp& op) {
   want_z = std::min<int64_t>(want_z, std::max(1, op.nz / 8));
   int zc = (int)((op.nz + want_z - 1) / want_z);
   if (zc < 1) zc = 1;
+  if (zc > 1 && (zc & 1)) ++zc;  // the 5/7-point kernel advances two planes per iteration
   int gz = (op.nz + zc - 1) / zc;
   return {dim3(gx, gy, gz), zc};
 }
