@@ -47,7 +47,9 @@ def parse():
     p.add_argument("--algo", choices=["literal", "onesync"], default="literal")
     p.add_argument("--form", choices=["stencil", "csr"], default="stencil")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--extra", default="", help="extra s-step configs to time, e.g. '4:3,4:30'")
+    p.add_argument("--extra", default="4:30,4:3:fp32_rr,4:30:fp32_rr",
+                   help="extra s-step configs 's:nu[:precision]' to time once each, e.g. "
+                        "'4:30,4:3:fp32_rr' (precision fp64 or fp32_rr)")
     return p.parse_args()
 
 
@@ -360,12 +362,20 @@ def main():
 
     # ---- optional extra s-step configurations
     extra = {}
+    x_fp64 = torch.from_numpy(x_host).to(dev)  # the headline FP64 solution
+    xe = torch.zeros_like(xd)
     for item in filter(None, args.extra.split(",")):
-        s_, nu_ = (int(v) for v in item.split(":"))
-        E = sstep.Solver(A, s=s_, sweeps=nu_, algo=args.algo, **common)
-        ems, einfos = timed_solves(E, xd, 1, 1)
-        extra[f"s{s_}_nu{nu_}"] = {"s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
-                                   "relres_true": einfos[0].relres_true}
+        parts = item.split(":")
+        s_, nu_ = int(parts[0]), int(parts[1])
+        prec = parts[2] if len(parts) > 2 else "fp64"
+        E = sstep.Solver(A, s=s_, sweeps=nu_, algo="literal" if prec != "fp64" else args.algo,
+                         precision=prec, **common)
+        ems, einfos = timed_solves(E, xe, 1, 1)
+        err = float(torch.linalg.norm(xe - x_fp64) / torch.linalg.norm(x_fp64))
+        extra[f"s{s_}_nu{nu_}" + ("" if prec == "fp64" else "_" + prec)] = {
+            "s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
+            "relres_true": einfos[0].relres_true, "rel_diff_vs_fp64_solution": err,
+            "time_over_fp64_pcg": ems[0] / float(np.mean(pms))}
         E.free()
 
     # ---- roofline of each kernel from the phase times

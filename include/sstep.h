@@ -106,7 +106,14 @@ typedef struct {
   int gram_blocks;    /* SSTEP_GRAM_BLOCKS_FULL: every Gram block as computed (Algorithm 1);
                          SSTEP_GRAM_BLOCKS_SYM: upper triangles of Q^T AQ, Z^T AZ and
                          Z^T AQ = (Q^T AZ)^T (fewer products).  Cholesky always uses FULL. */
+  int precision;      /* SSTEP_PRECISION_FP64 (default), or SSTEP_PRECISION_FP32_RR: the basis
+                         Z, AZ, Q, AQ and the MPK SpMV in FP32; Gram sums, x and r increments in
+                         double-float on the FP32 pipe (TwoProd/TwoSum, ~48-bit); FGS in FP64;
+                         every rr_period outer iterations x is folded and r = b - A x is
+                         recomputed in FP64 (residual replacement).  Literal form, s <= 8. */
+  int rr_period;      /* outer iterations between residual replacements (<= 0: s) */
 } sstep_opts;
+enum { SSTEP_PRECISION_FP64 = 0, SSTEP_PRECISION_FP32_RR = 1 };
 enum { SSTEP_GRAM_BLOCKS_FULL = 0, SSTEP_GRAM_BLOCKS_SYM = 1 };
 
 typedef struct {

@@ -61,7 +61,7 @@ struct sstep_ctx {
   cudaStream_t st = nullptr;   // stream all work is ordered on (captures need a non-legacy one)
   bool own_stream = false;
   int64_t nlaunch = 0;         // kernel launches issued (graph replays count their nodes)
-  int64_t graph_nodes[3] = {0, 0, 0};
+  int64_t graph_nodes[4] = {0, 0, 0, 0};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int64_t n = 0, ld = 0;
   int s = 4;
@@ -80,8 +80,17 @@ struct sstep_ctx {
   double lmin = 0.0, lmax = 0.0, c_alpha = 0.0, c_sigma = 0.0, c_gamma = 1.0;
   int power_run = 0;
   double ms_setup = 0.0;
-  // graphs of one outer iteration, per algorithm
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  // mixed path (FP32 basis): blocks, FP32 copies of the operator, x/r increments
+  bool mixed = false;
+  int rr_period = 0;
+  int64_t ldf = 0;
+  float *Zf = nullptr, *AZf = nullptr, *Qf = nullptr, *AQf = nullptr;
+  float *rhi = nullptr, *rlo = nullptr, *xhi = nullptr, *xlo = nullptr;
+  float *valsf = nullptr, *dinvf = nullptr;
+  // graphs of one outer iteration, per algorithm (index 3: the mixed literal form, rr_period
+  // outer iterations followed by a residual replacement)
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t graph_nodes4 = 0;
   // host polling of the stop flag
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   int* poll_flags = nullptr;  // pinned, 4 ints
@@ -237,9 +246,106 @@ sstep_status run_upd_w(sstep_ctx* h, bool first) {
   return run_gram(h, GM_LITERAL_W);
 }
 
+// ---------------------------------------------------------------- FP32-basis path
+
+constexpr int kAlgoMixed = 3;  // graph index of the mixed literal form
+
+MixedArgs mixed_args(sstep_ctx* h) {
+  MixedArgs a{};
+  a.n = h->n;
+  a.ld = h->ldf;
+  a.Z = h->Zf;
+  a.AZ = h->AZf;
+  a.Q = h->Qf;
+  a.AQ = h->AQf;
+  a.rhi = h->rhi;
+  a.rlo = h->rlo;
+  a.xhi = h->xhi;
+  a.xlo = h->xlo;
+  a.ctrl = h->ctrl;
+  a.partials = h->partials;
+  a.hist = h->hist;
+  return a;
+}
+
+// Algorithm 2 in FP32 from r_hi (the FP32 value nearest r).
+sstep_status run_mpk_f32(sstep_ctx* h) {
+  const int64_t ld = h->ldf;
+  const int s = h->s;
+  MpkF32Args e{};
+  e.dinv = h->dinvf;
+  e.dinv_u = (float)h->M.dinv_u;
+  e.valsf = h->valsf;
+  e.ctrl = h->ctrl;
+  if (h->op.kind == SSTEP_MATRIX_STENCIL) {
+    for (int k = 0; k < h->op.st.points; ++k) e.w[k] = (float)h->op.st.w[k];
+    e.wc = (float)h->op.st.wc;
+  }
+  for (int q = 1; q <= s; ++q) {
+    e.first = q == 1;
+    if (q == 1) {
+      e.u = h->rhi;
+      e.z1 = h->Zf;
+      e.zprev = nullptr;
+      e.c1 = (float)h->c_alpha;
+      e.c2 = (float)h->c_sigma;
+    } else {
+      e.u = h->Zf + (q - 1) * ld;
+      e.z1 = nullptr;
+      e.zprev = h->Zf + (q - 2) * ld;
+      e.c1 = (float)(2.0 * h->c_alpha);
+      e.c2 = (float)(2.0 * h->c_sigma);
+    }
+    e.y = h->AZf + (q - 1) * ld;
+    e.znext = q < s ? h->Zf + q * ld : nullptr;
+    CK(launch_mpk_f32(h->op, e, h->st));
+    ++h->nlaunch;
+  }
+  return SSTEP_OK;
+}
+
+// Residual replacement in FP64: x += xhi + xlo (increments zeroed), r = b - A x split into
+// rhi + rlo, ||r||^2 and the stop test on it.
+sstep_status run_rr(sstep_ctx* h) {
+  CK(launch_fold_x(h->x, h->xhi, h->xlo, h->n, h->ctrl, h->st));
+  EpiArgs e = epi_base(h, EP_RR);
+  e.u = h->x;
+  e.y = nullptr;
+  e.b = h->b;
+  e.rhi = h->rhi;
+  e.rlo = h->rlo;
+  CK(launch_operator(h->op, e, h->st));
+  h->nlaunch += 2;
+  return SSTEP_OK;
+}
+
+// One outer iteration of the mixed literal form (lines 10-15, then 5-9).
+sstep_status mixed_outer(sstep_ctx* h) {
+  const MixedArgs a = mixed_args(h);
+  CKS(run_mpk_f32(h));
+  CK(launch_gram_b2_f32(a, h->s, h->st));
+  CK(launch_upd_gram_f32(a, h->s, false, h->st));
+  CK(launch_update_xr_f32(a, h->s, h->st));
+  h->nlaunch += h->s > 4 ? 4 : 3;
+  return SSTEP_OK;
+}
+
+// First outer iteration of the mixed form: lines 2-3 and 5-9.
+sstep_status mixed_first(sstep_ctx* h) {
+  const MixedArgs a = mixed_args(h);
+  CKS(run_mpk_f32(h));
+  CK(launch_upd_gram_f32(a, h->s, true, h->st));
+  CK(launch_update_xr_f32(a, h->s, h->st));
+  h->nlaunch += h->s > 4 ? 3 : 2;
+  return SSTEP_OK;
+}
+
 // One outer iteration k >= 1 of each algorithm (what the graph captures).
 sstep_status outer_iteration(sstep_ctx* h, int algo) {
-  if (algo == SSTEP_ALGO_ONESYNC) {
+  if (algo == kAlgoMixed) {
+    for (int k = 0; k < h->rr_period; ++k) CKS(mixed_outer(h));
+    CKS(run_rr(h));
+  } else if (algo == SSTEP_ALGO_ONESYNC) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_gram(h, GM_ONESYNC));
     CKS(run_update(h, UM_FUSED));
@@ -384,6 +490,15 @@ sstep_status validate_opts(const sstep_opts* o) {
   if (o->gram_solver < 0 || o->gram_solver > 1) return fail(SSTEP_ERR_INVALID, "unknown gram_solver");
   if (o->power_iters < 1 && !(o->lambda_max > 0.0))
     return fail(SSTEP_ERR_INVALID, "power_iters must be >= 1 when lambda_max is not given");
+  if (o->precision != SSTEP_PRECISION_FP64 && o->precision != SSTEP_PRECISION_FP32_RR)
+    return fail(SSTEP_ERR_INVALID, "unknown precision");
+  if (o->precision == SSTEP_PRECISION_FP32_RR) {
+    if (o->algo != SSTEP_ALGO_LITERAL)
+      return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path implements the literal form only");
+    if (o->s > 8) return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path supports s <= 8");
+    if (o->gram_solver != SSTEP_GRAM_FGS)
+      return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path uses FGS reduced solves");
+  }
   return SSTEP_OK;
 }
 
@@ -392,6 +507,9 @@ void destroy(sstep_ctx* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
+  void* fbufs[] = {h->Zf, h->AZf, h->Qf, h->AQf, h->rhi, h->rlo, h->xhi, h->xlo, h->valsf, h->dinvf};
+  for (void* p : fbufs)
+    if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
                   h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl};
   for (void* p : bufs)
@@ -569,6 +687,35 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   h->c_alpha = 2.0 / (h->lmax - h->lmin);
   h->c_sigma = (h->lmax + h->lmin) / (h->lmax - h->lmin);
   h->c_gamma = 1.0;
+
+  // ---- FP32-basis path: FP32 blocks and increments, FP32 copies of the operator
+  if (h->o.precision == SSTEP_PRECISION_FP32_RR) {
+    h->mixed = true;
+    h->rr_period = h->o.rr_period > 0 ? h->o.rr_period : h->s;
+    h->ldf = round_up(h->n, 64);
+    const int64_t lf = h->ldf;
+    auto fal = [&](float** p, int64_t count) -> cudaError_t {
+      return cudaMalloc((void**)p, sizeof(float) * (size_t)std::max<int64_t>(count, 1));
+    };
+    CK(fal(&h->Zf, lf * s));
+    CK(fal(&h->AZf, lf * s));
+    CK(fal(&h->Qf, lf * s));
+    CK(fal(&h->AQf, lf * s));
+    CK(fal(&h->rhi, lf));
+    CK(fal(&h->rlo, lf));
+    CK(fal(&h->xhi, lf));
+    CK(fal(&h->xlo, lf));
+    if (A->kind == SSTEP_MATRIX_CSR) {
+      CK(fal(&h->valsf, A->nnz));
+      CK(launch_d2f(h->vals, h->valsf, A->nnz, h->st));
+      if (h->dinv) {
+        CK(fal(&h->dinvf, lf));
+        CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
+      }
+    } else if (A->points == 27) {
+      return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path takes 27-point operators as CSR");
+    }
+  }
   CK(cudaStreamSynchronize(h->st));
   h->ms_setup = now_ms() - t0;
   return SSTEP_OK;
@@ -586,26 +733,34 @@ int auto_check_every(const sstep_ctx* h) {
 sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* info) {
   const double t0 = now_ms();
   const int64_t n = h->n;
-  const int algo = h->o.algo;
+  const int algo = h->mixed ? kAlgoMixed : h->o.algo;
   // Order against the caller's stream: inputs produced there are complete before we read.
   CK(cudaEventRecord(h->ev_in, h->user_stream));
   CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
   CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, cudaMemcpyDefault, h->st));
   CK(cudaMemcpyAsync(h->x, x, sizeof(double) * n, cudaMemcpyDefault, h->st));
+  if (h->mixed) {
+    CK(cudaMemsetAsync(h->xhi, 0, sizeof(float) * n, h->st));
+    CK(cudaMemsetAsync(h->xlo, 0, sizeof(float) * n, h->st));
+  }
   CKS(reset_ctrl(h));
   const int64_t launches0 = h->nlaunch;
-  // line 1: r^(0) = b - A x^(0); ||b||^2, ||r||^2
+  // line 1: r^(0) = b - A x^(0); ||b||^2, ||r||^2 (mixed path: r kept as FP32 hi + lo)
   {
     EpiArgs e = epi_base(h, EP_RESID);
     e.u = h->x;
-    e.y = h->r;
+    e.y = h->mixed ? nullptr : h->r;
     e.b = h->b;
+    e.rhi = h->mixed ? h->rhi : nullptr;
+    e.rlo = h->mixed ? h->rlo : nullptr;
     CK(launch_operator(h->op, e, h->st));
     ++h->nlaunch;
   }
   // first outer iteration (not captured: it differs from the rest)
   const int maxit = h->o.max_outer;
-  if (algo == SSTEP_ALGO_ONESYNC) {
+  if (algo == kAlgoMixed) {
+    if (maxit > 0) CKS(mixed_first(h));
+  } else if (algo == SSTEP_ALGO_ONESYNC) {
     if (maxit > 0) {
       CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
       CKS(run_gram(h, GM_ONESYNC_FIRST));
@@ -626,6 +781,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   // Replay the captured outer iteration; poll the stop flag one batch behind.
   const int B = auto_check_every(h);
   int launched = (algo == SSTEP_ALGO_PCG) ? 0 : 1;  // PCG-S ran its first outer iteration above
+  const int per_graph = (algo == kAlgoMixed) ? h->rr_period : 1;  // outer iterations per replay
   bool finished = false;
   Ctrl* hc = h->hctrl;
   int* flags = h->poll_flags;
@@ -634,7 +790,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   int batch = 0;
   sstep_status st = SSTEP_OK;
   while (!finished) {
-    const int todo = std::min(B, maxit - launched);
+    const int todo = std::min(B, (maxit - launched + per_graph - 1) / per_graph);
     if (todo > 0) {
       for (int k = 0; k < todo; ++k) {
         cudaError_t e = cudaGraphLaunch(h->gexec[algo], h->st);
@@ -644,7 +800,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
         }
       }
       if (st != SSTEP_OK) break;
-      launched += todo;
+      launched += todo * per_graph;
       h->nlaunch += (int64_t)todo * h->graph_nodes[algo];
       const int slot = batch & 1;
       CK(cudaMemcpyAsync(flags + 2 * slot, &h->ctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -661,6 +817,10 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   }
   CK(cudaStreamSynchronize(h->st));
   if (st != SSTEP_OK) return st;
+  if (h->mixed) {  // fold the last increments into the FP64 solution
+    CK(launch_fold_x(h->x, h->xhi, h->xlo, n, h->ctrl, h->st));
+    ++h->nlaunch;
+  }
   CKS(read_ctrl(h));
   // b = 0: x = 0
   if (hc->nb2 == 0.0) CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->st));
@@ -721,6 +881,8 @@ void sstep_default_opts(sstep_opts* o) {
   o->power_v0 = nullptr;
   o->check_every = 0;
   o->gram_blocks = SSTEP_GRAM_BLOCKS_FULL;
+  o->precision = SSTEP_PRECISION_FP64;
+  o->rr_period = 0;
 }
 
 sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,
@@ -903,9 +1065,13 @@ sstep_status sstep_get_basis_info(sstep_handle h, double* lambda_min, double* la
 sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* ms) {
   g_err.clear();
   if (!h || !b || !ms || iters < 1) return fail(SSTEP_ERR_INVALID, "bad profile arguments");
-  const int algo = h->o.algo;
+  const int algo = h->mixed ? kAlgoMixed : h->o.algo;
   CK(cudaMemcpyAsync(h->b, b, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
   CK(cudaMemsetAsync(h->x, 0, sizeof(double) * h->n, h->st));
+  if (h->mixed) {
+    CK(cudaMemsetAsync(h->xhi, 0, sizeof(float) * h->n, h->st));
+    CK(cudaMemsetAsync(h->xlo, 0, sizeof(float) * h->n, h->st));
+  }
   CKS(reset_ctrl(h));
   h->hctrl->rtol2 = 0.0;  // never converge while profiling
   h->hctrl->max_iters = 1 << 30;
@@ -913,11 +1079,15 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   {
     EpiArgs e = epi_base(h, EP_RESID);
     e.u = h->x;
-    e.y = h->r;
+    e.y = h->mixed ? nullptr : h->r;
     e.b = h->b;
+    e.rhi = h->mixed ? h->rhi : nullptr;
+    e.rlo = h->mixed ? h->rlo : nullptr;
     CK(launch_operator(h->op, e, h->st));
   }
-  if (algo == SSTEP_ALGO_ONESYNC) {
+  if (algo == kAlgoMixed) {
+    CKS(mixed_first(h));
+  } else if (algo == SSTEP_ALGO_ONESYNC) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_gram(h, GM_ONESYNC_FIRST));
     CKS(run_update(h, UM_FIRST));
@@ -938,7 +1108,16 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   auto okc = [&](cudaError_t v) { if (st == SSTEP_OK && v != cudaSuccess) st = fail(SSTEP_ERR_CUDA, cudaGetErrorString(v)); };
   for (int k = 0; k < iters && st == SSTEP_OK; ++k) {
     cudaEventRecord(ev[0], h->st);
-    if (algo == SSTEP_ALGO_ONESYNC) {
+    if (algo == kAlgoMixed) {
+      const MixedArgs a = mixed_args(h);
+      ok(run_mpk_f32(h));
+      cudaEventRecord(ev[1], h->st);
+      okc(launch_gram_b2_f32(a, h->s, h->st));
+      cudaEventRecord(ev[2], h->st);
+      okc(launch_upd_gram_f32(a, h->s, false, h->st));
+      cudaEventRecord(ev[3], h->st);
+      okc(launch_update_xr_f32(a, h->s, h->st));
+    } else if (algo == SSTEP_ALGO_ONESYNC) {
       ok(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
       cudaEventRecord(ev[1], h->st);
       ok(run_gram(h, GM_ONESYNC));

@@ -14,6 +14,9 @@ constexpr int kMaxGramVecs = 40;   // largest number of vectors on one side of a
 constexpr int kThreads = 256;      // threads per CTA of the streaming kernels
 constexpr int kMaxCtas = 2048;     // upper bound on CTAs of a reduction kernel (partials buffer)
 constexpr int kNumTickets = 8;
+// Register tiles of the Gram kernels: at most kMaxTiles tiles of kTileMaxR x kTileMaxC products.
+constexpr int kTileMaxR = 8, kTileMaxC = 17, kMaxTiles = 4;
+constexpr int kTiledSmem = 8 * 72 > 1100 ? 8 * 72 : 1100;  // warp partials / sums + tail scratch
 
 enum Ticket { TK_GRAM = 0, TK_UPDATE = 1, TK_OP = 2, TK_NORM = 3, TK_PCG1 = 4, TK_PCG2 = 5 };
 
@@ -193,7 +196,9 @@ enum OpEpi {
   EP_RESID = 3,     // r = b - A u; reductions ||r||^2, ||b||^2   (initial residual)
   EP_POWER = 4,     // y = scale * M^{-1} A u; reduction ||y||^2
   EP_PCG_AP = 5,    // Ap = A p; reduction p^T Ap
-  EP_TRUERES = 6    // reduction ||b - A u||^2 (no store)
+  EP_TRUERES = 6,   // reduction ||b - A u||^2 (no store)
+  EP_RR = 7         // residual replacement r = b - A u (FP64), split into FP32 hi + lo,
+                    // ||r||^2 and the stop test on it
 };
 
 struct EpiArgs {
@@ -204,6 +209,8 @@ struct EpiArgs {
   double* z1;           // MPK first step: z1 output
   const double* zprev;  // MPK: z_{q-1} (null on the second basis vector)
   const double* b;      // residual epilogues
+  float* rhi;           // residual epilogues of the mixed path: r split into FP32 hi + lo
+  float* rlo;
   double c1, c2, c3;    // recurrence coefficients
   double a1u;           // c1 * M^{-1} when M^{-1} is a uniform scalar
   Prec M;
@@ -212,6 +219,59 @@ struct EpiArgs {
 };
 
 cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st);
+
+// ---------------------------------------------------------------- FP32-basis (mixed) path
+// One MPK step with FP32 storage and arithmetic (Algorithm 2; recurrence on z).
+struct MpkF32Args {
+  const float* u;      // z_q (first step: r_hi, the FP32 value nearest r)
+  float* y;            // A z_q
+  float* znext;        // z_{q+1} (null on the last step)
+  float* z1;           // first step: z_1 = M^{-1} r
+  const float* zprev;  // z_{q-1} (null on the first two steps)
+  const float* dinv;   // non-uniform M^{-1} in FP32, or null
+  float dinv_u;        // uniform M^{-1}
+  float c1, c2;        // z_{q+1} = c1 M^{-1} (A z_q) - c2 z_q - z_{q-1}
+  float w[27];         // stencil weights in FP32
+  float wc;
+  const float* valsf;  // CSR values in FP32
+  int first;
+  Ctrl* ctrl;
+};
+cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st);
+
+// Blocks of the mixed path: Q, AQ, Z, AZ in FP32; x and r as FP64 plus FP32 (hi, lo)
+// increments; Gram sums accumulated in double-float (TwoProd + TwoSum on the FP32 pipe).
+struct MixedArgs {
+  int64_t n, ld;
+  const float* Z;
+  const float* AZ;
+  float* Q;
+  float* AQ;
+  float* rhi;   // r = rhi + rlo between residual replacements
+  float* rlo;
+  float* xhi;   // x = x64 + xhi + xlo between residual replacements
+  float* xlo;
+  Ctrl* ctrl;
+  double* partials;
+  double* hist;
+};
+// Tiles of FP32 Gram products (double-float accumulation); ylo: optional low part of a column.
+struct GramTilesF {
+  int64_t n;
+  int ntiles, mode, ne;
+  const float* x[kMaxTiles][kTileMaxR];
+  const float* y[kMaxTiles][kTileMaxC];
+  const float* ylo[kMaxTiles][kTileMaxC];
+  short out[kMaxTiles][kTileMaxR * kTileMaxC];
+  Ctrl* ctrl;
+  double* partials;
+};
+cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st);
+cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st);
+cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st);
+cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
+// x64 += xhi + xlo; xhi = xlo = 0 (before a residual replacement and at the end)
+cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl, cudaStream_t st);
 
 struct GramArgs {
   int64_t n;
@@ -227,8 +287,6 @@ struct GramArgs {
 cudaError_t launch_gram(const GramArgs& g, cudaStream_t st);
 
 // Register-tiled Gram products for the structured modes (every block formed, s <= 8).
-constexpr int kTileMaxR = 8, kTileMaxC = 17, kMaxTiles = 4;
-constexpr int kTiledSmem = 8 * 72 > 1100 ? 8 * 72 : 1100;  // warp partials / sums + tail scratch
 struct GramTiles {
   int64_t n;
   int ntiles, mode, ne;

@@ -505,6 +505,327 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + K);
 }
 
+// ---------------------------------------------------------------- mixed path (FP32 basis)
+
+// Error-free transformations on the FP32 pipe: TwoProd via FMA (a*b = p + e exactly) and
+// Knuth's TwoSum.  A (hi, lo) pair accumulates products of FP32 numbers with about 48 bits,
+// so Gram sums of FP32 vectors carry FP64-class accuracy while the narrow FP64 pipe of this
+// part stays idle.  Intrinsics keep the compiler from contracting the sequences.
+__device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// (ah, al) += (bh, bl), renormalised.
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float lo = __fadd_rn(err, __fadd_rn(al, bl));
+  const float h = __fadd_rn(s, lo);
+  ah = h;
+  al = __fsub_rn(lo, __fsub_rn(h, s));
+}
+
+// Per-thread (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the last CTA.
+// Returns true in the last CTA, with the K sums in buf[0..K).
+template <int K>
+__device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
+                             double* partials, unsigned int* ticket) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum((double)hi[k] + (double)lo[k]);
+    if (lane == 0) buf[wid * K + k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    partials[(size_t)blockIdx.x * K + k] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (unsigned int bx = 0; bx < gridDim.x; ++bx) v += __ldcg(partials + (size_t)bx * K + k);
+    buf[k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// b2 = -Q^T AZ (line 12) from FP32 blocks, then beta = FGS(W, b2) (line 13).
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1) k_gram_b2f(MixedArgs a) {
+  if (a.ctrl->done) return;
+  constexpr int K = S * S;
+  __shared__ double buf[kTiledSmem];
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+  const int64_t ld = a.ld;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float q[S], z[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) q[i] = __ldg(a.Q + i * ld + p);
+#pragma unroll
+    for (int j = 0; j < S; ++j) z[j] = __ldg(a.AZ + j * ld + p);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], q[i], z[j]);
+  }
+  if (!df_grid_sums<K>(hi, lo, buf, a.partials, &a.ctrl->ticket[TK_GRAM])) return;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = buf[e];
+  gram_tail(GM_LITERAL_B2, a.ctrl, buf, buf + K);
+}
+
+// Line 15 in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r accumulated in
+// double-float (r = rhi + rlo), then alpha = FGS(W, b1) in the last CTA (lines 5-6).
+template <int S, bool FIRST>
+__global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
+  if (a.ctrl->done) return;
+  constexpr int K = S * S + S;
+  __shared__ float sb[S * S];
+  __shared__ double buf[kTiledSmem];
+  if (!FIRST)
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+  __syncthreads();
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+  const int64_t ld = a.ld;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float qn[S], an[S];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        qn[j] = __ldg(a.Z + j * ld + p);
+        an[j] = __ldg(a.AZ + j * ld + p);
+      }
+    } else {
+      float qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = a.Q[l * ld + p];
+        ao[l] = a.AQ[l * ld + p];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          vq = fmaf(qo[l], sb[l + j * S], vq);
+          va = fmaf(ao[l], sb[l + j * S], va);
+        }
+        qn[j] = vq;
+        an[j] = va;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      a.Q[j * ld + p] = qn[j];
+      a.AQ[j * ld + p] = an[j];
+    }
+    const float rh = __ldg(a.rhi + p), rl = __ldg(a.rlo + p);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
+      df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
+      lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
+    }
+  }
+  if (!df_grid_sums<K>(hi, lo, buf, a.partials, &a.ctrl->ticket[TK_GRAM])) return;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = buf[e];
+  gram_tail(GM_LITERAL_W, a.ctrl, buf, buf + K);
+}
+
+// Lines 7-9: x += Q alpha, r -= AQ alpha with x, r kept as FP32 (hi, lo) increments between
+// residual replacements, ||r||^2 in double-float, stop test in the last CTA.
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
+  if (a.ctrl->done) return;
+  __shared__ float ah[S], al[S];
+  __shared__ double buf[kTiledSmem];
+  if (threadIdx.x < S) {
+    const double v = a.ctrl->alpha[threadIdx.x];
+    const float h = __double2float_rn(v);
+    ah[threadIdx.x] = h;
+    al[threadIdx.x] = __double2float_rn(v - (double)h);
+  }
+  __syncthreads();
+  float rrh[1] = {0.0f}, rrl[1] = {0.0f};
+  const int64_t ld = a.ld;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const float q = __ldg(a.Q + j * ld + p), aq = __ldg(a.AQ + j * ld + p);
+      df_acc_prod(dxh, dxl, q, ah[j]);
+      dxl = fmaf(q, al[j], dxl);
+      df_acc_prod(drh, drl, aq, ah[j]);
+      drl = fmaf(aq, al[j], drl);
+    }
+    float xh = a.xhi[p], xl = a.xlo[p], rh = a.rhi[p], rl = a.rlo[p];
+    df_add(xh, xl, dxh, dxl);
+    df_add(rh, rl, -drh, -drl);
+    a.xhi[p] = xh;
+    a.xlo[p] = xl;
+    a.rhi[p] = rh;
+    a.rlo[p] = rl;
+    df_acc_prod(rrh[0], rrl[0], rh, rh);
+    rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
+  }
+  if (!df_grid_sums<1>(rrh, rrl, buf, a.partials, &a.ctrl->ticket[TK_UPDATE])) return;
+  if (threadIdx.x == 0) {
+    stop_test(a.ctrl, buf[0]);
+    if (a.hist) a.hist[a.ctrl->iters] = sqrt(buf[0] / a.ctrl->nb2);
+  }
+}
+
+// Line 15 alone in FP32 (FIRST: Q = Z, AQ = AZ) for step sizes whose fused form would not fit
+// in registers; W and b1 then come from k_gram_df.
+template <int S, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
+  if (a.ctrl->done) return;
+  __shared__ float sb[S * S];
+  if (!FIRST)
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+  __syncthreads();
+  const int64_t ld = a.ld;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        a.Q[j * ld + p] = __ldg(a.Z + j * ld + p);
+        a.AQ[j * ld + p] = __ldg(a.AZ + j * ld + p);
+      }
+    } else {
+      float qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = a.Q[l * ld + p];
+        ao[l] = a.AQ[l * ld + p];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          vq = fmaf(qo[l], sb[l + j * S], vq);
+          va = fmaf(ao[l], sb[l + j * S], va);
+        }
+        a.Q[j * ld + p] = vq;
+        a.AQ[j * ld + p] = va;
+      }
+    }
+  }
+}
+
+// Register-tiled Gram products of FP32 vectors with double-float accumulation (the FP32
+// counterpart of k_gram_tiled).  A column may carry a second FP32 vector (ylo) holding the
+// low part of an FP64 vector split as hi + lo.
+template <int NR, int NC>
+__global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
+  if (g.ctrl->done) return;
+  constexpr int K = NR * NC;
+  __shared__ double buf[kTiledSmem];
+  const int t = blockIdx.y;
+  const float* xp[NR];
+  const float* yp[NC];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) xp[i] = g.x[t][i];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) yp[j] = g.y[t][j];
+  const float* ylo = g.ylo[t][NC - 1];  // only the last column may carry a low part
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float xv[NR], yv[NC], yl[NC];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) xv[i] = __ldg(xp[i] + p);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      yv[j] = __ldg(yp[j] + p);
+      yl[j] = 0.0f;
+    }
+    if (ylo) yl[NC - 1] = __ldg(ylo + p);
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i], yv[j]);
+        lo[i * NC + j] = fmaf(xv[i], yl[j], lo[i * NC + j]);
+      }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum((double)hi[k] + (double)lo[k]);
+    if (lane == 0) buf[wid * K + k] = v;
+  }
+  __syncthreads();
+  const unsigned int cta = blockIdx.x + gridDim.x * blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    g.partials[(size_t)cta * K + k] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(&g.ctrl->ticket[TK_GRAM], 1u) == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double* sums = buf;
+  for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
+    const int tt = idx / K, k = idx % K;
+    const int e = g.out[tt][k];
+    if (e < 0) continue;
+    double v = 0.0;
+    for (unsigned int bx = 0; bx < gridDim.x; ++bx)
+      v += __ldcg(g.partials + ((size_t)tt * gridDim.x + bx) * K + k);
+    sums[e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) g.ctrl->ticket[TK_GRAM] = 0u;
+  for (int e = threadIdx.x; e < g.ne; e += blockDim.x) g.ctrl->sums[e] = sums[e];
+  gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fold_x(double* x, float* xh, float* xl, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (double)xh[i] + (double)xl[i];
+    xh[i] = 0.0f;
+    xl[i] = 0.0f;
+  }
+}
+
 // ---------------------------------------------------------------- fused block update
 
 template <int S, int MODE>
@@ -995,6 +1316,166 @@ cudaError_t launch_upd_gram(const UpdGramArgs& a, int s, bool first, cudaStream_
 #undef CASE
     default: return cudaErrorNotSupported;
   }
+}
+
+namespace {
+template <typename KernelT>
+int occ_grid(KernelT k, int64_t n, int& cache) {
+  if (!cache) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache, k, kThreads, 0);
+    if (cache < 1) cache = 1;
+  }
+  const int64_t rows = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * cache, rows));
+}
+}  // namespace
+
+namespace {
+
+template <int NR, int NC>
+cudaError_t launch_gram_df_shape(const GramTilesF& g, cudaStream_t st) {
+  static int occ = 0;
+  if (!occ) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_df<NR, NC>, kThreads, 0);
+    if (occ < 1) occ = 1;
+  }
+  const int64_t want = ((int64_t)sm_count() * occ + g.ntiles - 1) / g.ntiles;
+  const int64_t rows = (g.n + kThreads - 1) / kThreads;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, rows));
+  k_gram_df<NR, NC><<<dim3(gx, g.ntiles), kThreads, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// 2 x 2 tiles of X^T [Y | r]: X = s FP32 columns, Y = s FP32 columns (entries i + j s),
+// r = rhi + rlo (entries s^2 + i, kept from the tiles of the first column half), as the
+// literal-form layouts expect.  Padding rows/columns point at column 0 and are not kept.
+cudaError_t launch_gram_df_split(int mode, const MixedArgs& a, int s, const float* X,
+                                 const float* Y, bool with_r, cudaStream_t st) {
+  GramTilesF g{};
+  g.n = a.n;
+  g.mode = mode;
+  g.ctrl = a.ctrl;
+  g.partials = a.partials;
+  g.ntiles = 4;
+  const int h = (s + 1) / 2;
+  const int nr = h, nc = h + (with_r ? 1 : 0);
+  g.ne = s * s + (with_r ? s : 0);
+  for (auto& tt : g.out)
+    for (auto& o : tt) o = -1;
+  for (int t = 0; t < 4; ++t) {
+    const int i0 = (t >> 1) * h, j0 = (t & 1) * h;
+    for (int ri = 0; ri < nr; ++ri) {
+      const int i = i0 + ri;
+      g.x[t][ri] = X + (int64_t)(i < s ? i : 0) * a.ld;
+    }
+    for (int c = 0; c < h; ++c) {
+      const int j = j0 + c;
+      g.y[t][c] = Y + (int64_t)(j < s ? j : 0) * a.ld;
+      for (int ri = 0; ri < nr; ++ri) {
+        const int i = i0 + ri;
+        if (i < s && j < s) g.out[t][ri * nc + c] = (short)(i + j * s);
+      }
+    }
+    if (with_r) {
+      g.y[t][h] = a.rhi;
+      g.ylo[t][h] = a.rlo;
+      if (j0 == 0)
+        for (int ri = 0; ri < nr; ++ri) {
+          const int i = i0 + ri;
+          if (i < s) g.out[t][ri * nc + h] = (short)(s * s + i);
+        }
+    }
+  }
+  switch (nr * 16 + nc) {
+    case 3 * 16 + 3: return launch_gram_df_shape<3, 3>(g, st);
+    case 3 * 16 + 4: return launch_gram_df_shape<3, 4>(g, st);
+    case 4 * 16 + 4: return launch_gram_df_shape<4, 4>(g, st);
+    case 4 * 16 + 5: return launch_gram_df_shape<4, 5>(g, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
+  if (s > 4) return launch_gram_df_split(GM_LITERAL_B2, a, s, a.Q, a.AZ, false, st);
+  switch (s) {
+#define CASE(S)                                                            \
+  case S: {                                                                \
+    static int occ = 0;                                                    \
+    k_gram_b2f<S><<<occ_grid(k_gram_b2f<S>, a.n, occ), kThreads, 0, st>>>(a); \
+    return cudaGetLastError();                                             \
+  }
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st) {
+  if (s > 4) {  // line 15 and lines 5-6 as two passes (the fused form would spill)
+    const int grid = update_ctas(a.n);
+    switch (s) {
+#define CASE(S)                                                                   \
+  case S:                                                                         \
+    if (first) k_upd_qaq_f<S, true><<<grid, kThreads, 0, st>>>(a);                \
+    else k_upd_qaq_f<S, false><<<grid, kThreads, 0, st>>>(a);                     \
+    break;
+      CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+      default: return cudaErrorNotSupported;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_gram_df_split(GM_LITERAL_W, a, s, a.Q, a.AQ, true, st);
+  }
+  switch (s) {
+#define CASE(S)                                                                            \
+  case S: {                                                                                \
+    if (first) {                                                                           \
+      static int occ = 0;                                                                  \
+      k_upd_gramf<S, true><<<occ_grid(k_upd_gramf<S, true>, a.n, occ), kThreads, 0, st>>>(a); \
+    } else {                                                                               \
+      static int occ = 0;                                                                  \
+      k_upd_gramf<S, false><<<occ_grid(k_upd_gramf<S, false>, a.n, occ), kThreads, 0, st>>>(a); \
+    }                                                                                      \
+    return cudaGetLastError();                                                             \
+  }
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st) {
+  const int grid = update_ctas(a.n);
+  switch (s) {
+#define CASE(S) \
+  case S: k_update_xrf<S><<<grid, kThreads, 0, st>>>(a); return cudaGetLastError();
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return cudaErrorNotSupported;
+  }
+}
+
+namespace {
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+}  // namespace
+
+cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
+  k_d2f<<<stream_ctas(n, 4), kThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl,
+                          cudaStream_t st) {
+  (void)ctrl;
+  k_fold_x<<<stream_ctas(n, 4), kThreads, 0, st>>>(x64, xhi, xlo, n);
+  return cudaGetLastError();
 }
 
 cudaError_t gram_init() {

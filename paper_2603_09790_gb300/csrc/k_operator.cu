@@ -28,7 +28,8 @@ struct EpiNV<EP_RESID> { static constexpr int v = 2; };
 
 template <int EPI>
 __device__ __forceinline__ constexpr bool epi_reduces() {
-  return EPI == EP_RESID || EPI == EP_POWER || EPI == EP_PCG_AP || EPI == EP_TRUERES;
+  return EPI == EP_RESID || EPI == EP_POWER || EPI == EP_PCG_AP || EPI == EP_TRUERES ||
+         EPI == EP_RR;
 }
 
 // y: (A u)_i where u is the (possibly M^{-1}-scaled) operator input; uc: that input at i.
@@ -48,12 +49,17 @@ __device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t i, double y, 
       if (e.zprev) t = e.c3 == 1.0 ? -__ldg(e.zprev + i) : -e.c3 * __ldg(e.zprev + i);
       e.znext[i] = fma(a, y, fma(-e.c2, uc, t));
     }
-  } else if constexpr (EPI == EP_RESID) {
+  } else if constexpr (EPI == EP_RESID || EPI == EP_RR) {
     const double bi = __ldg(e.b + i);
     const double ri = bi - y;
-    e.y[i] = ri;
+    if (e.y) e.y[i] = ri;
+    if (e.rhi) {  // mixed path: r = rhi + rlo with rhi the FP32 value nearest r
+      const float hi = __double2float_rn(ri);
+      e.rhi[i] = hi;
+      e.rlo[i] = __double2float_rn(ri - (double)hi);
+    }
     red[0] = fma(ri, ri, red[0]);
-    red[1] = fma(bi, bi, red[1]);
+    if constexpr (EPI == EP_RESID) red[1] = fma(bi, bi, red[1]);
   } else if constexpr (EPI == EP_POWER) {
     // v_{l-1} = y_{l-1} / lambda_{l-1} is normalised on the fly: scale by 1/lambda_{l-1}
     const double yi = e.ctrl->inv_scale * prec_d(e.M, i) * y;
@@ -112,6 +118,16 @@ __device__ void finish(const EpiArgs& e, const double* tot) {
     }
   } else if constexpr (EPI == EP_TRUERES) {
     c->sums[0] = tot[0];
+  } else if constexpr (EPI == EP_RR) {
+    // the replaced residual is the true one: the stop test of line 9 applies to it too
+    c->rr = tot[0];
+    if (!(tot[0] == tot[0]) || tot[0] > 1.79e308) {
+      c->status = SSTEP_ERR_NONFINITE;
+      c->done = 1;
+    } else if (tot[0] <= c->tol2) {
+      c->status = SSTEP_OK;
+      c->done = 1;
+    }
   }
 }
 
@@ -377,6 +393,141 @@ __global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
   reduce_and_finish<EPI>(e, red);
 }
 
+// ---------------------------------------------------------------- FP32 MPK step (mixed path)
+
+__device__ __forceinline__ void mpk_f32_epilogue(const MpkF32Args& e, int64_t i, float y,
+                                                 float uc, bool first) {
+  if (first) e.z1[i] = uc;  // z_1 = M^{-1} r
+  e.y[i] = y;               // A z_q
+  if (e.znext) {
+    const float a = e.dinv ? e.c1 * __ldg(e.dinv + i) : e.c1 * e.dinv_u;
+    const float t = e.zprev ? -__ldg(e.zprev + i) : 0.0f;
+    e.znext[i] = fmaf(a, y, fmaf(-e.c2, uc, t));
+  }
+}
+
+template <int PTS, bool POISSON>
+__device__ __forceinline__ float stencil7_point_f(const MpkF32Args& e, const float (*p)[TX + 2],
+                                                  int tx, int ty, float ub, float uc, float ua) {
+  if constexpr (POISSON) {
+    float s = (p[ty + 1][tx] + p[ty + 1][tx + 2]) + (p[ty][tx + 1] + p[ty + 2][tx + 1]);
+    if constexpr (PTS == 7) s += ub + ua;
+    return fmaf(e.wc, uc, -s);
+  } else if constexpr (PTS == 7) {
+    float a = e.w[0] * ub;
+    a = fmaf(e.w[1], p[ty][tx + 1], a);
+    a = fmaf(e.w[2], p[ty + 1][tx], a);
+    a = fmaf(e.w[3], uc, a);
+    a = fmaf(e.w[4], p[ty + 1][tx + 2], a);
+    a = fmaf(e.w[5], p[ty + 2][tx + 1], a);
+    return fmaf(e.w[6], ua, a);
+  } else {
+    float a = e.w[0] * p[ty][tx + 1];
+    a = fmaf(e.w[1], p[ty + 1][tx], a);
+    a = fmaf(e.w[2], uc, a);
+    a = fmaf(e.w[3], p[ty + 1][tx + 2], a);
+    return fmaf(e.w[4], p[ty + 2][tx + 1], a);
+  }
+}
+
+// The 2.5D body of k_stencil7 with FP32 values: half the bytes per point, and the FP32 pipe
+// (64x the FP64 one on this part) does the arithmetic, so the step is bound by HBM.
+template <int PTS, bool POISSON, bool FIRST, bool SCALE>
+__global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args e, int zc) {
+  if (e.ctrl && e.ctrl->done) return;
+  __shared__ float t[2][2][TY + 2][TX + 2];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int nx = op.nx, ny = op.ny, nz = op.nz;
+  const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int64_t pxy = (int64_t)nx * ny;
+  const bool in = x < nx && y < ny;
+  const int64_t col = (int64_t)y * nx + x;
+  const int hx = tx == 0 ? -1 : (tx == TX - 1 ? 1 : 0);
+  const int hy = ty == 0 ? -1 : (ty == TY - 1 ? 1 : 0);
+  const bool hxok = hx != 0 && x + hx >= 0 && x + hx < nx && y < ny;
+  const bool hyok = hy != 0 && y + hy >= 0 && y + hy < ny && x < nx;
+  const int64_t hxoff = col + hx, hyoff = col + (int64_t)hy * nx;
+  auto ld = [&](int64_t off, int zz, bool ok) -> float {
+    if (!ok || zz < 0 || zz >= nz) return 0.0f;
+    const int64_t idx = off + (int64_t)zz * pxy;
+    float v = __ldg(e.u + idx);
+    if constexpr (SCALE) v *= __ldg(e.dinv + idx);
+    return v;
+  };
+  float ub = ld(col, z0 - 1, in), uc = ld(col, z0, in);
+  float ua = ld(col, z0 + 1, in), ua2 = ld(col, z0 + 2, in);
+  float hx0 = ld(hxoff, z0, hxok), hx1 = ld(hxoff, z0 + 1, hxok);
+  float hy0 = ld(hyoff, z0, hyok), hy1 = ld(hyoff, z0 + 1, hyok);
+  int set = 0;
+  for (int z = z0; z < z1; z += 2) {
+    float (*P0)[TX + 2] = t[set][0];
+    float (*P1)[TX + 2] = t[set][1];
+    P0[ty + 1][tx + 1] = uc;
+    P1[ty + 1][tx + 1] = ua;
+    if (hx) {
+      P0[ty + 1][tx + 1 + hx] = hx0;
+      P1[ty + 1][tx + 1 + hx] = hx1;
+    }
+    if (hy) {
+      P0[ty + 1 + hy][tx + 1] = hy0;
+      P1[ty + 1 + hy][tx + 1] = hy1;
+    }
+    const float n3 = ld(col, z + 3, in), n4 = ld(col, z + 4, in);
+    const float nhx0 = ld(hxoff, z + 2, hxok), nhx1 = ld(hxoff, z + 3, hxok);
+    const float nhy0 = ld(hyoff, z + 2, hyok), nhy1 = ld(hyoff, z + 3, hyok);
+    __syncthreads();
+    if (in) {
+      float a0 = stencil7_point_f<PTS, POISSON>(e, P0, tx, ty, ub, uc, ua), c0 = uc;
+      if constexpr (FIRST && !SCALE) {
+        a0 *= e.dinv_u;
+        c0 *= e.dinv_u;
+      }
+      mpk_f32_epilogue(e, (int64_t)z * pxy + col, a0, c0, FIRST);
+      if (z + 1 < z1) {
+        float a1 = stencil7_point_f<PTS, POISSON>(e, P1, tx, ty, uc, ua, ua2), c1 = ua;
+        if constexpr (FIRST && !SCALE) {
+          a1 *= e.dinv_u;
+          c1 *= e.dinv_u;
+        }
+        mpk_f32_epilogue(e, (int64_t)(z + 1) * pxy + col, a1, c1, FIRST);
+      }
+    }
+    ub = ua;
+    uc = ua2;
+    ua = n3;
+    ua2 = n4;
+    hx0 = nhx0;
+    hx1 = nhx1;
+    hy0 = nhy0;
+    hy1 = nhy1;
+    set ^= 1;
+  }
+}
+
+template <bool FIRST, bool SCALE>
+__global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
+  if (e.ctrl && e.ctrl->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+    float a = 0.0f;
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      float v = __ldg(e.u + c);
+      if constexpr (SCALE) v *= __ldg(e.dinv + c);
+      a = fmaf(__ldg(e.valsf + k), v, a);
+    }
+    float uc = __ldg(e.u + i);
+    if constexpr (SCALE) uc *= __ldg(e.dinv + i);
+    if constexpr (FIRST && !SCALE) {
+      a *= e.dinv_u;
+      uc *= e.dinv_u;
+    }
+    mpk_f32_epilogue(e, i, a, uc, FIRST);
+  }
+}
+
 int num_sms() {
   static int sms = 0;
   if (!sms) {
@@ -464,8 +615,45 @@ cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st) 
     case EP_POWER: return dispatch<EP_POWER>(A, e, st);
     case EP_PCG_AP: return dispatch<EP_PCG_AP>(A, e, st);
     case EP_TRUERES: return dispatch<EP_TRUERES>(A, e, st);
+    case EP_RR: return dispatch<EP_RR>(A, e, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st) {
+  const bool scale = e.first && e.dinv != nullptr;
+  if (A.kind == SSTEP_MATRIX_STENCIL) {
+    const StencilOp& op = A.st;
+    if (op.points == 27) return cudaErrorNotSupported;  // the mixed path takes 27 points as CSR
+    StencilGrid g = stencil_grid(op);
+    const int threads = TX * TY;
+#define L7(P, POI)                                                                           \
+  do {                                                                                       \
+    if (e.first) {                                                                           \
+      if (scale) k_stencil7f<P, POI, true, true><<<g.grid, threads, 0, st>>>(op, e, g.zc);    \
+      else k_stencil7f<P, POI, true, false><<<g.grid, threads, 0, st>>>(op, e, g.zc);         \
+    } else {                                                                                 \
+      k_stencil7f<P, POI, false, false><<<g.grid, threads, 0, st>>>(op, e, g.zc);             \
+    }                                                                                        \
+  } while (0)
+    if (op.points == 7) {
+      if (op.poisson) L7(7, true);
+      else L7(7, false);
+    } else {
+      if (op.poisson) L7(5, true);
+      else L7(5, false);
+    }
+#undef L7
+    return cudaGetLastError();
+  }
+  const int grid = csr_ctas(A.csr.n);
+  if (e.first) {
+    if (scale) k_csrf<true, true><<<grid, kThreads, 0, st>>>(A.csr, e);
+    else k_csrf<true, false><<<grid, kThreads, 0, st>>>(A.csr, e);
+  } else {
+    k_csrf<false, false><<<grid, kThreads, 0, st>>>(A.csr, e);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace sstep

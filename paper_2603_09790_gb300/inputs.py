@@ -133,3 +133,107 @@ def poisson_problem(dims, points: int, seed: int = 0):
 def power_start(n: int, seed: int = 1) -> np.ndarray:
     """Start vector of the power method: U[-1,1) with seed 1."""
     return uniform_pm1(seed, n)
+
+
+# ---------------------------------------------------------------- variable-coefficient diffusion
+
+def normal_pm(seed: int, n: int) -> np.ndarray:
+    """Standard normal variates by Box-Muller from SplitMix64 outputs 2k, 2k+1 (k < n)."""
+    u = (splitmix64(seed, 2 * n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    u1 = 1.0 - u[0::2]  # in (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def lognormal_conductivity(cells, sigma: float = 1.0, corr: float = 8.0, seed: int = 0):
+    """Per-cell conductivity kappa = exp(sigma g): g is white noise (seed) convolved with a
+    separable Gaussian of standard deviation corr / sqrt(2) cells (covariance
+    exp(-d^2 / (2 corr^2))), renormalised to zero mean and unit variance.  Shape (cz, cy, cx)."""
+    from scipy.ndimage import gaussian_filter
+
+    cx, cy, cz = (int(c) for c in cells)
+    g = normal_pm(seed, cx * cy * cz).reshape(cz, cy, cx)
+    if corr > 0:
+        g = gaussian_filter(g, sigma=corr / np.sqrt(2.0), mode="wrap")
+    g = (g - g.mean()) / g.std()
+    return np.exp(sigma * g)
+
+
+def q1_reference_stiffness() -> np.ndarray:
+    """8 x 8 stiffness of the trilinear (Q1) element on the unit cube, vertex (i, j, k) of the
+    cell at local index i + 2 j + 4 k: K = K1 x M1 x M1 + M1 x K1 x M1 + M1 x M1 x K1 with the
+    1D stiffness K1 = [[1, -1], [-1, 1]] and mass M1 = [[1/3, 1/6], [1/6, 1/3]]."""
+    K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    M1 = np.array([[1.0, 0.5], [0.5, 1.0]]) / 3.0
+    # index order of np.kron(a, b) is (a index) * 2 + b index: build z, y, x major -> i + 2j + 4k
+    return (np.kron(np.kron(M1, M1), K1) + np.kron(np.kron(M1, K1), M1) +
+            np.kron(np.kron(K1, M1), M1))
+
+
+def q1_csr(dims, kappa):
+    """CSR of the Q1 finite-element diffusion operator on the nx x ny x nz interior vertices of a
+    grid of (nx+1)(ny+1)(nz+1) unit cells with conductivity kappa (shape (nz+1, ny+1, nx+1)),
+    Dirichlet boundary vertices eliminated.  27-point pattern; the face-neighbour couplings
+    of Q1 vanish identically and are not stored (21 entries on an interior row)."""
+    nx, ny, nz = (int(d) for d in dims)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    assert kappa.shape == (nz + 1, ny + 1, nx + 1)
+    Kr = q1_reference_stiffness()
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy, iz = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+            if (dx != 0) + (dy != 0) + (dz != 0) != 1]
+    coef = {}
+    for d in offs:
+        c = np.zeros(n)
+        # cells around vertex v (grid coords v+1): lower corner v+1+o, o in {-1, 0}^3
+        for ox in (-1, 0):
+            for oy in (-1, 0):
+                for oz in (-1, 0):
+                    lv = (-ox, -oy, -oz)  # local coordinates of v in that cell
+                    lw = (lv[0] + d[0], lv[1] + d[1], lv[2] + d[2])
+                    if min(lw) < 0 or max(lw) > 1:
+                        continue
+                    kv = Kr[lv[0] + 2 * lv[1] + 4 * lv[2], lw[0] + 2 * lw[1] + 4 * lw[2]]
+                    c += kv * kappa[iz + 1 + oz, iy + 1 + oy, ix + 1 + ox]
+        coef[d] = c
+    masks = []
+    for dx, dy, dz in offs:
+        m = (ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny) & \
+            (iz + dz >= 0) & (iz + dz < nz)
+        masks.append(m)
+    counts = np.zeros(n, dtype=np.int64)
+    for m in masks:
+        counts += m
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    colind = np.empty(nnz, dtype=np.int32)
+    vals = np.empty(nnz, dtype=np.float64)
+    fill = rowptr[:-1].copy()
+    for d, m in zip(offs, masks):
+        rows = idx[m]
+        pos = fill[m]
+        colind[pos] = (rows + d[0] + nx * (d[1] + ny * d[2])).astype(np.int32)
+        vals[pos] = coef[d][m]
+        fill[m] += 1
+    return rowptr, colind, vals
+
+
+def csr_matvec(rowptr, colind, vals, x):
+    """y = A x for CSR arrays (used to form b = A x_true of a synthetic problem)."""
+    prod = vals * np.asarray(x)[colind]
+    y = np.add.reduceat(prod, rowptr[:-1]) if prod.size else np.zeros(rowptr.size - 1)
+    y[rowptr[1:] == rowptr[:-1]] = 0.0
+    return y
+
+
+def q1_lognormal_problem(dims, sigma: float = 1.0, corr: float = 8.0, seed: int = 0):
+    """Operator (CSR), conductivity, x_true ~ U[-1,1) (seed) and b = A x_true."""
+    nx, ny, nz = (int(d) for d in dims)
+    kappa = lognormal_conductivity((nx + 1, ny + 1, nz + 1), sigma, corr, seed)
+    rp, ci, v = q1_csr((nx, ny, nz), kappa)
+    x_true = uniform_pm1(seed, nx * ny * nz)
+    b = csr_matvec(rp, ci, v, x_true)
+    return (rp, ci, v), kappa, x_true, b

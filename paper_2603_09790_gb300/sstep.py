@@ -47,7 +47,8 @@ class _Opts(C.Structure):
     _fields_ = [("s", C.c_int), ("sweeps", C.c_int), ("rtol", C.c_double), ("max_outer", C.c_int),
                 ("algo", C.c_int), ("gram_solver", C.c_int), ("power_iters", C.c_int),
                 ("power_tol", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
-                ("power_v0", C.c_void_p), ("check_every", C.c_int), ("gram_blocks", C.c_int)]
+                ("power_v0", C.c_void_p), ("check_every", C.c_int), ("gram_blocks", C.c_int),
+                ("precision", C.c_int), ("rr_period", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -182,7 +183,8 @@ class Solver:
 
     def __init__(self, A, *, precond="jacobi", s=4, sweeps=2, rtol=1e-8, max_outer=10000,
                  algo="literal", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
-                 lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", stream=None):
+                 lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", precision="fp64",
+                 rr_period=0, stream=None):
         lib = load()
         m = _Matrix()
         self._weights = None
@@ -210,6 +212,8 @@ class Solver:
         o.power_v0 = _ptr(power_v0)
         o.check_every = int(check_every)
         o.gram_blocks = {"full": 0, "sym": 1}[gram_blocks]
+        o.precision = {"fp64": 0, "fp32_rr": 1}[precision]
+        o.rr_period = int(rr_period)
         self.s = int(s)
         self.max_outer = int(max_outer)
         pc = _Precond(PREC[precond])

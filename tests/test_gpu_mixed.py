@@ -1,0 +1,97 @@
+"""The FP32-basis path (precision = fp32_rr) against the FP64 oracle and the FP64 CUDA path.
+
+Tolerance.  The basis Z, AZ, Q, AQ and the MPK SpMV are FP32 (unit roundoff 6e-8); Gram sums
+and the x, r increments are double-float (about 48 bits); r = b - A x is recomputed in FP64
+every rr_period outer iterations.  So the solve reaches the same FP64 true residual as the FP64
+path (checked at <= 2e-8 for rtol 1e-8), and its solution differs from the FP64 oracle's by at
+most what two solutions at rtol 1e-8 can differ: about rtol * kappa(A).  Iterates at a fixed
+outer count differ from the FP64 path by the FP32 rounding of the basis, amplified by the
+iteration: a few 1e-6 on these problems (checked at 1e-4).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2603_09790_gb300 import inputs as I
+from paper_2603_09790_gb300 import sstep
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def solve(A, b, **kw):
+    with sstep.Solver(A, **kw) as S:
+        x = dev(np.zeros_like(b))
+        info = S.solve(dev(b), x)
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), info, S.get_basis_info()
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("form,dims,points,s,nu", [
+    ("stencil", (40, 36, 28), 7, 4, 30), ("stencil", (40, 36, 28), 7, 4, 3),
+    ("csr", (64, 64), 5, 4, 30), ("stencil", (64, 64), 5, 2, 3), ("csr", (30, 26, 22), 27, 8, 30)])
+def test_mixed_reaches_fp64_true_residual(form, dims, points, s, nu):
+    csr = O.CSR(*I.poisson_csr(dims, points))
+    nx, ny, nz = (tuple(dims) + (1,))[:3]
+    A = sstep.Stencil(nx, ny, nz, points) if form == "stencil" else \
+        sstep.CSR(dev(csr.rowptr), dev(csr.colind), dev(csr.vals))
+    xt, b = I.poisson_problem(dims, points)
+    x, info, bi = solve(A, b, s=s, sweeps=nu, rtol=1e-8, precision="fp32_rr",
+                        power_v0=dev(I.power_start(csr.n)))
+    assert info.status == sstep.OK
+    assert info.relres_true <= 2e-8
+    ref = O.pcgs(csr, b, s=s, nu=nu, rtol=1e-8, algo="literal", lambda_max=bi["lambda_max"])
+    assert ref.status == O.OK
+    lam = np.linalg.eigvalsh(csr.dense()) if csr.n <= 5000 else None
+    kappa = lam[-1] / lam[0] if lam is not None else 1e4
+    assert relerr(x, ref.x) <= 2e-8 * kappa + 1e-10
+
+
+def test_mixed_q1_lognormal_s8():
+    """Variable-coefficient Q1 diffusion with log-normal conductivity (sigma 1, correlation
+    8 cells), s = 8, residual replacement every s outer iterations."""
+    dims = (24, 20, 16)
+    (rp, ci, v), kappa, xt, b = I.q1_lognormal_problem(dims)
+    csr = O.CSR(rp, ci, v)
+    A = sstep.CSR(dev(rp), dev(ci), dev(v))
+    x, info, bi = solve(A, b, s=8, sweeps=30, rtol=1e-8, precision="fp32_rr", rr_period=8,
+                        power_v0=dev(I.power_start(csr.n)))
+    assert info.status == sstep.OK and info.relres_true <= 2e-8
+    x64, info64, _ = solve(A, b, s=8, sweeps=30, rtol=1e-8, power_v0=dev(I.power_start(csr.n)))
+    ref = O.pcg(csr, b, rtol=1e-12)
+    lam = np.linalg.eigvalsh(csr.dense())
+    kappa_A = lam[-1] / lam[0]
+    assert relerr(x, ref.x) <= 2e-8 * kappa_A
+    assert relerr(x64, ref.x) <= 2e-8 * kappa_A
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 6, 8])
+def test_mixed_fixed_count_close_to_fp64(s):
+    dims = (30, 26, 22)
+    A = sstep.Stencil(*dims, points=7)
+    xt, b = I.poisson_problem(dims, 7)
+    K = 12
+    kw = dict(s=s, sweeps=30, rtol=0.0, max_outer=K, lambda_max=1.95)
+    xm, im, _ = solve(A, b, precision="fp32_rr", **kw)
+    xd, idd, _ = solve(A, b, **kw)
+    assert im.outer_iters == K and idd.outer_iters == K
+    assert relerr(xm, xd) <= 1e-4
+
+
+def test_mixed_rejects_unsupported():
+    A = sstep.Stencil(10, 10, 10, 7)
+    for kw in (dict(s=9), dict(algo="onesync"), dict(gram="cholesky")):
+        with pytest.raises(sstep.SstepError) as e:
+            sstep.Solver(A, precision="fp32_rr", lambda_max=2.0, **kw)
+        assert e.value.status == sstep.ERR_UNSUPPORTED
+    with pytest.raises(sstep.SstepError):
+        sstep.Solver(sstep.Stencil(10, 10, 10, 27), precision="fp32_rr", lambda_max=2.0)
