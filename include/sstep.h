@@ -221,6 +221,20 @@ SSTEP_API sstep_status sstep_get_basis_info(sstep_handle h, double* lambda_min, 
                                   double* c_alpha, double* c_sigma, double* c_gamma,
                                   int* power_iters_run);
 
+/* Gradient of a loss L(x(A)) with respect to the stored entries of a CSR matrix A, given the
+ * adjoint lambda = A^{-T} dL/dx (for SPD A, a second solve with the same handle):
+ * dL/dA_ij = -lambda_i x_j, written for each stored (i, j) in CSR order:
+ * grad_vals[k] = (accumulate ? grad_vals[k] : 0) - scale * lambda[row(k)] * x[colind[k]].
+ * Device pointers (rowptr n+1, colind nnz, lambda and x n, grad_vals nnz).  The paper has no
+ * counterpart; it makes the solver differentiable with respect to A's values. */
+SSTEP_API sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                          const double* lam, const double* x, double* grad_vals,
+                                          double scale, int accumulate, void* stream);
+
+/* Replace the values of the handle's CSR operator (same pattern), device or host vals[nnz];
+ * M^{-1} (Jacobi) and the FP32 copies are refreshed.  The Chebyshev interval is kept. */
+SSTEP_API sstep_status sstep_update_values(sstep_handle h, const double* vals);
+
 /* Residual history of the last solve: relres[k] = ||r^(k)|| / ||b|| for k = 0..iters
  * (recursively updated residual after each outer iteration).  relres: host array of maxlen
  * doubles; *count receives the number written. */

@@ -63,7 +63,7 @@ struct sstep_ctx {
   int64_t nlaunch = 0;         // kernel launches issued (graph replays count their nodes)
   int64_t graph_nodes[4] = {0, 0, 0, 0};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int64_t n = 0, ld = 0;
+  int64_t n = 0, ld = 0, nnz = 0;
   int s = 4;
   // device memory
   int64_t* rowptr = nullptr;
@@ -590,6 +590,7 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
     CK(cudaMemcpyAsync(h->colind, A->colind, sizeof(int32_t) * A->nnz, cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(h->vals, A->vals, sizeof(double) * A->nnz, cudaMemcpyDefault, h->st));
     h->op.csr = CsrOp{A->n, h->rowptr, h->colind, h->vals};
+    h->nnz = A->nnz;
     {
       int* bad = nullptr;
       CK(cudaMalloc(&bad, sizeof(int)));
@@ -1163,6 +1164,40 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
     sum += ms[p];
   }
   ms[kPh] = sum;
+  return SSTEP_OK;
+}
+
+sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                const double* lam, const double* x, double* grad_vals,
+                                double scale, int accumulate, void* stream) {
+  g_err.clear();
+  if (n < 1 || !rowptr || !colind || !lam || !x || !grad_vals)
+    return fail(SSTEP_ERR_INVALID, "bad pattern_grad arguments");
+  CsrOp A{n, rowptr, colind, nullptr};
+  CK(launch_pattern_grad(A, lam, x, grad_vals, scale, accumulate, (cudaStream_t)stream));
+  return SSTEP_OK;
+}
+
+sstep_status sstep_update_values(sstep_handle h, const double* vals) {
+  g_err.clear();
+  if (!h || !vals) return fail(SSTEP_ERR_INVALID, "null argument");
+  if (h->op.kind != SSTEP_MATRIX_CSR) return fail(SSTEP_ERR_INVALID, "the handle's operator is not CSR");
+  const int64_t nnz = h->nnz;
+  CK(cudaMemcpyAsync(h->vals, vals, sizeof(double) * nnz, cudaMemcpyDefault, h->st));
+  if (h->dinv) {
+    int* bad = nullptr;
+    CK(cudaMallocAsync((void**)&bad, sizeof(int), h->st));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
+    CK(launch_jacobi_csr(h->op.csr, h->dinv, bad, h->st));
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaFreeAsync(bad, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (hbad) return fail(SSTEP_ERR_INVALID, "Jacobi needs a positive diagonal entry in every row");
+  }
+  if (h->valsf) CK(launch_d2f(h->vals, h->valsf, nnz, h->st));
+  if (h->dinvf) CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
+  CK(cudaStreamSynchronize(h->st));
   return SSTEP_OK;
 }
 

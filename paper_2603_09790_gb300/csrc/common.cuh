@@ -270,6 +270,9 @@ cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st);
 cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st);
 cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st);
 cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
+// g[k] (+)= -scale * lam[row(k)] * x[col(k)] over the CSR pattern
+cudaError_t launch_pattern_grad(const CsrOp& A, const double* lam, const double* x, double* g,
+                                double scale, int accumulate, cudaStream_t st);
 // x64 += xhi + xlo; xhi = xlo = 0 (before a residual replacement and at the end)
 cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl, cudaStream_t st);
 

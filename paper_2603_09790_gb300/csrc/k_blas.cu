@@ -1459,6 +1459,27 @@ cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st) {
 }
 
 namespace {
+// dL/dA_ij = -lambda_i x_j on the stored pattern (row-per-thread over the CSR rows).
+__global__ void k_pattern_grad(CsrOp A, const double* lam, const double* x, double* g,
+                               double scale, int accumulate) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double li = -scale * __ldg(lam + i);
+    for (int64_t k = __ldg(A.rowptr + i); k < __ldg(A.rowptr + i + 1); ++k) {
+      const double v = li * __ldg(x + __ldg(A.colind + k));
+      g[k] = accumulate ? g[k] + v : v;
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_pattern_grad(const CsrOp& A, const double* lam, const double* x, double* g,
+                                double scale, int accumulate, cudaStream_t st) {
+  k_pattern_grad<<<stream_ctas(A.n, 8), kThreads, 0, st>>>(A, lam, x, g, scale, accumulate);
+  return cudaGetLastError();
+}
+
+namespace {
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)

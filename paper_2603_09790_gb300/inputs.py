@@ -237,3 +237,34 @@ def q1_lognormal_problem(dims, sigma: float = 1.0, corr: float = 8.0, seed: int 
     x_true = uniform_pm1(seed, nx * ny * nz)
     b = csr_matvec(rp, ci, v, x_true)
     return (rp, ci, v), kappa, x_true, b
+
+
+def q1_assembly(dims):
+    """The linear map from cell conductivities to the CSR values of q1_csr: vals[k] =
+    sum_t S_vals[t] * kappa.flat[S_cells[t]] over the triplets t with S_rows[t] = k.
+    Returns (rowptr, colind, S_rows, S_cells, S_vals); same pattern as q1_csr."""
+    nx, ny, nz = (int(d) for d in dims)
+    ones = np.ones((nz + 1, ny + 1, nx + 1))
+    rowptr, colind, _ = q1_csr((nx, ny, nz), ones)
+    Kr = q1_reference_stiffness()
+    n = nx * ny * nz
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    ix, iy, iz = rows % nx, (rows // nx) % ny, rows // (nx * ny)
+    jx, jy, jz = colind % nx, (colind // nx) % ny, colind // (nx * ny)
+    dx, dy, dz = jx - ix, jy - iy, jz - iz
+    tr, tc, tv = [], [], []
+    k_all = np.arange(colind.size, dtype=np.int64)
+    for ox in (-1, 0):
+        for oy in (-1, 0):
+            for oz in (-1, 0):
+                lvx, lvy, lvz = -ox, -oy, -oz
+                lwx, lwy, lwz = lvx + dx, lvy + dy, lvz + dz
+                ok = (lwx >= 0) & (lwx <= 1) & (lwy >= 0) & (lwy <= 1) & (lwz >= 0) & (lwz <= 1)
+                kv = Kr[lvx + 2 * lvy + 4 * lvz, (lwx + 2 * lwy + 4 * lwz)[ok]]
+                cell = ((iz[ok] + 1 + oz) * (ny + 1) + (iy[ok] + 1 + oy)) * (nx + 1) + (ix[ok] + 1 + ox)
+                tr.append(k_all[ok])
+                tc.append(cell)
+                tv.append(kv)
+    S_rows, S_cells, S_vals = np.concatenate(tr), np.concatenate(tc), np.concatenate(tv)
+    keep = S_vals != 0.0
+    return rowptr, colind, S_rows[keep], S_cells[keep], S_vals[keep]

@@ -89,6 +89,8 @@ def load():
         "sstep_get_history": (I, [P, P, I, P]),
         "sstep_profile": (I, [P, P, I, P]),
         "sstep_block_gram_noalloc": (I, [I64, I, P, I, P, I, P, P, P]),
+        "sstep_pattern_grad": (I, [I64, P, P, P, P, P, D, I, P]),
+        "sstep_update_values": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -283,6 +285,11 @@ class Solver:
         _check(load().sstep_profile(self._h, _ptr(b), int(iters), ms))
         return list(ms)
 
+    def update_values(self, vals):
+        """sstep_update_values: new values for the handle's CSR operator (same pattern); the
+        Jacobi diagonal is recomputed, the Chebyshev interval is kept."""
+        _check(load().sstep_update_values(self._h, _ptr(vals)))
+
     def get_history(self):
         buf = np.zeros(self.max_outer + 2)
         cnt = C.c_int()
@@ -310,6 +317,14 @@ def block_gram_noalloc(L, R, pairs, out, stream=None):
     pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
     _check(load().sstep_block_gram_noalloc(n, len(L), Lp, len(R), Rp, pr.size // 2, pr.ctypes.data,
                                            _ptr(out), _stream_ptr(stream)))
+
+
+def pattern_grad(rowptr, colind, lam, x, grad_vals, scale=1.0, accumulate=False, stream=None):
+    """sstep_pattern_grad: grad_vals[k] (+)= -scale * lam[i] * x[colind[k]] for every stored
+    entry k of row i (device tensors; rowptr int64, colind int32)."""
+    n = int(rowptr.numel()) - 1
+    _check(load().sstep_pattern_grad(n, _ptr(rowptr), _ptr(colind), _ptr(lam), _ptr(x), _ptr(grad_vals),
+                                     float(scale), int(bool(accumulate)), _stream_ptr(stream)))
 
 
 def fgs(W, B, nu, X, solver="fgs", status=None, stream=None):

@@ -67,3 +67,30 @@ def test_lognormal_field_statistics():
     assert c > 0.9
     z = I.normal_pm(0, 200000)
     assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+
+
+def test_assembly_map_reproduces_csr():
+    """The linear map kappa -> vals (used to differentiate through assembly) reproduces q1_csr
+    exactly, and is linear: a cell's unit conductivity gives that cell's 8x8 element matrix."""
+    dims = (6, 5, 4)
+    nx, ny, nz = dims
+    kappa = I.lognormal_conductivity((nx + 1, ny + 1, nz + 1), 1.0, 2.0, seed=1)
+    rp, ci, v = I.q1_csr(dims, kappa)
+    rp2, ci2, sr, sc, sv = I.q1_assembly(dims)
+    assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2)
+    vals = np.zeros(ci.size)
+    np.add.at(vals, sr, sv * kappa.reshape(-1)[sc])
+    assert np.abs(vals - v).max() <= 1e-15 * np.abs(v).max()
+    # one interior cell switched on: its 8 vertices couple through K_ref and nothing else does
+    cx, cy, cz = 2, 2, 2
+    e = np.zeros_like(kappa)
+    e[cz, cy, cx] = 1.0
+    _, _, ve = I.q1_csr(dims, e)
+    A = O.CSR(rp, ci, ve).dense()
+    K = I.q1_reference_stiffness()
+    verts = [((cz - 1 + (q >> 2)) * ny + (cy - 1 + ((q >> 1) & 1))) * nx + (cx - 1 + (q & 1)) for q in range(8)]
+    B = np.zeros_like(A)
+    for a in range(8):
+        for b in range(8):
+            B[verts[a], verts[b]] += K[a, b]
+    assert np.abs(A - B).max() < 1e-15
