@@ -112,6 +112,13 @@ typedef struct {
                          every rr_period outer iterations x is folded and r = b - A x is
                          recomputed in FP64 (residual replacement).  Literal form, s <= 8. */
   int rr_period;      /* outer iterations between residual replacements (<= 0: s) */
+  /* Batched persistent solver (implied when nsys > 1; see sstep_setup).  s = 0 lets the
+   * autotuner pick s from {2, 4, 8}; cluster = 0 / block_threads = 0 let it pick the CTAs per
+   * thread-block cluster (one cluster works on one system and right-hand side at a time) from
+   * {2, 4, 8, 16} and the threads per CTA from {256, 512}. */
+  int persistent;     /* 1: use the batched persistent solver even for nsys = 1 */
+  int cluster;        /* CTAs per cluster: 0 (autotune), 1, 2, 4, 8 or 16 */
+  int block_threads;  /* threads per CTA: 0 (autotune), 256 or 512 (512 only for s <= 4) */
 } sstep_opts;
 enum { SSTEP_PRECISION_FP64 = 0, SSTEP_PRECISION_FP32_RR = 1 };
 enum { SSTEP_GRAM_BLOCKS_FULL = 0, SSTEP_GRAM_BLOCKS_SYM = 1 };
@@ -138,7 +145,14 @@ SSTEP_API void sstep_default_opts(sstep_opts* o);
  * device, forms M^{-1}, runs the power method on M^{-1}A when o->lambda_max <= 0, derives the
  * Chebyshev scalars c_alpha = 2/(lmax-lmin), c_sigma = (lmax+lmin)/(lmax-lmin), c_gamma = 1, and
  * allocates the basis blocks Z, AZ, Q, AQ (4 s vectors) and x, r, b buffers.
- * nsys must be 1.  stream: cudaStream_t passed as void*.  On error *out is NULL. */
+ * nsys = 1 (and persistent = 0): one operator A[0], any kind.
+ * nsys > 1 (or persistent = 1): the batched persistent solver for the nsys systems A[0..nsys-1],
+ * each a 7-point STENCIL with constant weights whose six neighbour weights are equal (NULL:
+ * Poisson), with M = NONE or JACOBI, the literal form, FGS, precision FP64 or FP32_RR and
+ * s in {2, 4, 8} (0: autotuned).  Each system gets its own power-method lambda_max (unless
+ * o->lambda_max > 0 is given for all) and its Gershgorin lambda_min when o->lambda_min < 0.
+ * The paper solves one system at a time; batching is this library's extension.
+ * stream: cudaStream_t passed as void*.  On error *out is NULL. */
 SSTEP_API sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,
                          const sstep_opts* o, void* stream, sstep_handle* out);
 
@@ -148,10 +162,26 @@ SSTEP_API sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_
  * info may be NULL.  Returns the solve status (also in info->status). */
 SSTEP_API sstep_status sstep_solve(sstep_handle h, const double* b, double* x, sstep_info* info);
 
-/* Solve nrhs systems with the same A one after another: b[i], x[i] as in sstep_solve;
- * infos may be NULL or hold nrhs entries.  Returns the first non-OK status, else SSTEP_OK. */
+/* Single-system handle: solve nrhs right-hand sides with the same A one after another;
+ * b[i], x[i] as in sstep_solve; infos may be NULL or hold nrhs entries.
+ * Batched handle (nsys systems): b and x hold nsys * nrhs DEVICE pointers, system-major
+ * (b[sys * nrhs + j] is right-hand side j of system sys, n_sys doubles; x likewise, x^(0) on
+ * entry); infos may be NULL or hold nsys * nrhs entries in the same order.  All problems are
+ * solved by one persistent kernel launch (replayed from a CUDA graph): each thread-block
+ * cluster takes the next (system, right-hand side) problem from a device work queue, largest
+ * systems first, and runs Algorithm 1 on it to convergence with cluster barriers and
+ * distributed-shared-memory reductions.  Results equal those of independent solves up to
+ * rounding order.  Returns the first non-OK status, else SSTEP_OK. */
 SSTEP_API sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const double* const* b,
                                  double* const* x, sstep_info* infos);
+
+/* Batched handle: the configuration in use (chosen by the autotuner where the options left
+ * it open): step size s, CTAs per cluster, threads per CTA, number of clusters resident at
+ * once (= workspace slots), and the wall time the autotuner spent at set-up (0 when the
+ * choice came from its in-process cache or from the options).  Any output may be NULL.
+ * SSTEP_ERR_INVALID for a single-system handle. */
+SSTEP_API sstep_status sstep_get_batch_config(sstep_handle h, int* s, int* cluster, int* threads,
+                                              int* slots, double* tune_ms);
 
 /* Release everything the handle owns (NULL is accepted). */
 SSTEP_API sstep_status sstep_free(sstep_handle h);

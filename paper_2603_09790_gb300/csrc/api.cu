@@ -94,6 +94,8 @@ struct sstep_ctx {
   // host polling of the stop flag
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   int* poll_flags = nullptr;  // pinned, 4 ints
+  // batched persistent solver (nsys > 1 or opts.persistent): everything lives in here
+  BatchCtx* batch = nullptr;
 };
 
 namespace {
@@ -504,6 +506,7 @@ sstep_status validate_opts(const sstep_opts* o) {
 
 void destroy(sstep_ctx* h) {
   if (!h) return;
+  if (h->batch) batch_free(h->batch);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
@@ -884,6 +887,9 @@ void sstep_default_opts(sstep_opts* o) {
   o->gram_blocks = SSTEP_GRAM_BLOCKS_FULL;
   o->precision = SSTEP_PRECISION_FP64;
   o->rr_period = 0;
+  o->persistent = 0;
+  o->cluster = 0;
+  o->block_threads = 0;
 }
 
 sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,
@@ -893,6 +899,16 @@ sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M
   *out = nullptr;
   sstep_ctx* h = new (std::nothrow) sstep_ctx();
   if (!h) return fail(SSTEP_ERR_OOM, "host allocation failed");
+  if (o && (nsys > 1 || o->persistent)) {
+    g_err.clear();
+    sstep_status st = batch_setup(A, nsys, M, o, (cudaStream_t)stream, &h->batch);
+    if (st != SSTEP_OK) {
+      delete h;
+      return st;
+    }
+    *out = h;
+    return SSTEP_OK;
+  }
   sstep_status st = setup_impl(A, nsys, M, o, stream, h);
   if (st != SSTEP_OK) {
     std::string keep = g_err;
@@ -908,6 +924,7 @@ sstep_status sstep_setup(const sstep_matrix* A, int nsys, const sstep_precond* M
 sstep_status sstep_solve(sstep_handle h, const double* b, double* x, sstep_info* info) {
   g_err.clear();
   if (!h || !b || !x) return fail(SSTEP_ERR_INVALID, "null handle, b or x");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "a batched handle solves through sstep_solve_batched");
   return solve_impl(h, b, x, info);
 }
 
@@ -915,6 +932,7 @@ sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const double* const* 
                                  double* const* x, sstep_info* infos) {
   g_err.clear();
   if (!h || nrhs < 0 || (nrhs > 0 && (!b || !x))) return fail(SSTEP_ERR_INVALID, "bad arguments");
+  if (h->batch) return batch_solve(h->batch, nrhs, b, x, infos);
   sstep_status first = SSTEP_OK;
   for (int i = 0; i < nrhs; ++i) {
     sstep_status st = sstep_solve(h, b[i], x[i], infos ? infos + i : nullptr);
@@ -924,6 +942,14 @@ sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const double* const* 
       return st;
   }
   return first;
+}
+
+sstep_status sstep_get_batch_config(sstep_handle h, int* s, int* cluster, int* threads,
+                                    int* slots, double* tune_ms) {
+  g_err.clear();
+  if (!h || !h->batch) return fail(SSTEP_ERR_INVALID, "not a batched handle");
+  batch_config(h->batch, s, cluster, threads, slots, tune_ms);
+  return SSTEP_OK;
 }
 
 sstep_status sstep_free(sstep_handle h) {
@@ -950,6 +976,7 @@ const char* sstep_last_error(void) { return g_err.c_str(); }
 sstep_status sstep_mpk(sstep_handle h, const double* r, double* Z, double* AZ, int s_override) {
   g_err.clear();
   if (!h || !r || !Z || !AZ) return fail(SSTEP_ERR_INVALID, "null argument");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   const int s = s_override ? s_override : h->s;
   if (s < 1 || s > kMaxS) return fail(SSTEP_ERR_INVALID, "s out of range");
   // Z and AZ given by the caller use leading dimension n.
@@ -1012,6 +1039,7 @@ sstep_status sstep_block_update(sstep_handle h, const double* Z, const double* A
                                 double* AQ, const double* alpha, const double* beta, double* x,
                                 double* r, double* rr_out, int s_override) {
   g_err.clear();
+  if (h && h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   if (!h || !Z || !AZ || !Q || !AQ || !alpha || !x || !r || !rr_out)
     return fail(SSTEP_ERR_INVALID, "null argument");
   const int s = s_override ? s_override : h->s;
@@ -1041,6 +1069,7 @@ sstep_status sstep_block_update(sstep_handle h, const double* Z, const double* A
 sstep_status sstep_spmv(sstep_handle h, const double* x, double* y) {
   g_err.clear();
   if (!h || !x || !y) return fail(SSTEP_ERR_INVALID, "null argument");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   EpiArgs e = epi_base(h, EP_SPMV);
   e.ctrl = nullptr;
   e.u = x;
@@ -1054,6 +1083,7 @@ sstep_status sstep_get_basis_info(sstep_handle h, double* lambda_min, double* la
                                   double* c_alpha, double* c_sigma, double* c_gamma,
                                   int* power_iters_run) {
   if (!h) return fail(SSTEP_ERR_INVALID, "null handle");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   if (lambda_min) *lambda_min = h->lmin;
   if (lambda_max) *lambda_max = h->lmax;
   if (c_alpha) *c_alpha = h->c_alpha;
@@ -1066,6 +1096,7 @@ sstep_status sstep_get_basis_info(sstep_handle h, double* lambda_min, double* la
 sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* ms) {
   g_err.clear();
   if (!h || !b || !ms || iters < 1) return fail(SSTEP_ERR_INVALID, "bad profile arguments");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   const int algo = h->mixed ? kAlgoMixed : h->o.algo;
   CK(cudaMemcpyAsync(h->b, b, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
   CK(cudaMemsetAsync(h->x, 0, sizeof(double) * h->n, h->st));
@@ -1181,6 +1212,7 @@ sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, const int32_t*
 sstep_status sstep_update_values(sstep_handle h, const double* vals) {
   g_err.clear();
   if (!h || !vals) return fail(SSTEP_ERR_INVALID, "null argument");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   if (h->op.kind != SSTEP_MATRIX_CSR) return fail(SSTEP_ERR_INVALID, "the handle's operator is not CSR");
   const int64_t nnz = h->nnz;
   CK(cudaMemcpyAsync(h->vals, vals, sizeof(double) * nnz, cudaMemcpyDefault, h->st));
@@ -1203,6 +1235,7 @@ sstep_status sstep_update_values(sstep_handle h, const double* vals) {
 
 sstep_status sstep_get_history(sstep_handle h, double* relres, int maxlen, int* count) {
   if (!h || !relres || maxlen < 1) return fail(SSTEP_ERR_INVALID, "bad arguments");
+  if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
   CK(cudaStreamSynchronize(h->st));
   const int n = std::min(maxlen, h->hctrl->iters + 1);
   CK(cudaMemcpy(relres, h->hist, sizeof(double) * n, cudaMemcpyDeviceToHost));

@@ -96,6 +96,42 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Element i (0-based) of the SplitMix64 stream with the given seed (Steele, Lea, Flood 2014),
+// mapped to U[-1, 1): the (i+1)-th state is seed + (i+1) * golden gamma, so every element is
+// computed independently.  Used for seeded input vectors (power-method start, test inputs).
+__host__ __device__ __forceinline__ double splitmix_pm1(uint64_t seed, int64_t i) {
+  uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// Error-free transformations on the FP32 pipe: TwoProd via FMA (a*b = p + e exactly) and
+// Knuth's TwoSum.  A (hi, lo) pair accumulates products of FP32 numbers with about 48 bits,
+// so Gram sums of FP32 vectors carry FP64-class accuracy while the narrow FP64 pipe of this
+// part stays idle.  Intrinsics keep the compiler from contracting the sequences.
+__device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// (ah, al) += (bh, bl), renormalised.
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float lo = __fadd_rn(err, __fadd_rn(al, bl));
+  const float h = __fadd_rn(s, lo);
+  ah = h;
+  al = __fsub_rn(lo, __fsub_rn(h, s));
+}
+
 // Block-wide sum of NV values per thread; result valid in thread 0.  Fixed order.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* NV * 32 */) {
@@ -373,5 +409,15 @@ int operator_grid_ctas(const OpDesc& A);  // CTAs of one operator launch (partia
 
 // Sets the calling thread's message returned by sstep_last_error() (defined in api.cu).
 void set_last_error(const char* msg);
+
+// Batched persistent solver (batch.cu): many 7-point stencil systems x right-hand sides.
+struct BatchCtx;
+sstep_status batch_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,
+                         const sstep_opts* o, cudaStream_t st, BatchCtx** out);
+sstep_status batch_solve(BatchCtx* b, int nrhs, const double* const* bv, double* const* xv,
+                         sstep_info* infos);
+void batch_config(const BatchCtx* b, int* s, int* cluster, int* threads, int* slots,
+                  double* tune_ms);
+void batch_free(BatchCtx* b);
 
 }  // namespace sstep

@@ -507,31 +507,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
 
 // ---------------------------------------------------------------- mixed path (FP32 basis)
 
-// Error-free transformations on the FP32 pipe: TwoProd via FMA (a*b = p + e exactly) and
-// Knuth's TwoSum.  A (hi, lo) pair accumulates products of FP32 numbers with about 48 bits,
-// so Gram sums of FP32 vectors carry FP64-class accuracy while the narrow FP64 pipe of this
-// part stays idle.  Intrinsics keep the compiler from contracting the sequences.
-__device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);
-  const float s = __fadd_rn(hi, p);
-  const float bb = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, e));
-}
-
-// (ah, al) += (bh, bl), renormalised.
-__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
-  const float s = __fadd_rn(ah, bh);
-  const float bb = __fsub_rn(s, ah);
-  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-  const float lo = __fadd_rn(err, __fadd_rn(al, bl));
-  const float h = __fadd_rn(s, lo);
-  ah = h;
-  al = __fsub_rn(lo, __fsub_rn(h, s));
-}
-
 // Per-thread (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the last CTA.
 // Returns true in the last CTA, with the K sums in buf[0..K).
 template <int K>
@@ -993,11 +968,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(PcgArgs a) {
 __global__ void k_fill_splitmix(double* v, int64_t n, uint64_t seed) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z = z ^ (z >> 31);
-    v[i] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    v[i] = splitmix_pm1(seed, i);
   }
 }
 

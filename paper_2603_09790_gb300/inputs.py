@@ -268,3 +268,18 @@ def q1_assembly(dims):
     S_rows, S_cells, S_vals = np.concatenate(tr), np.concatenate(tc), np.concatenate(tv)
     keep = S_vals != 0.0
     return rowptr, colind, S_rows[keep], S_cells[keep], S_vals[keep]
+
+
+def batch_grids(nsys: int = 64, lo: int = 32, hi: int = 96, seed: int = 0):
+    """Grid edges of a batch of 3D systems: each of nx, ny, nz drawn independently and
+    uniformly from {lo, ..., hi} with SplitMix64 (seed), in the order sys0 (nx, ny, nz),
+    sys1 (nx, ny, nz), ...  Returns a list of (nx, ny, nz)."""
+    u = (uniform_pm1(seed, 3 * nsys) + 1.0) * 0.5  # exact: U[0, 1) on the 2^-53 grid
+    e = lo + np.minimum(np.floor(u * (hi - lo + 1)).astype(np.int64), hi - lo)
+    return [tuple(int(v) for v in e[3 * i:3 * i + 3]) for i in range(nsys)]
+
+
+def batch_rhs(sys: int, n: int, nrhs: int) -> np.ndarray:
+    """Right-hand sides of system `sys` of a batch: U[-1, 1) from SplitMix64 seed 1 + sys,
+    right-hand side j taking elements j*n .. (j+1)*n - 1 of the stream.  Shape (nrhs, n)."""
+    return uniform_pm1(1 + sys, nrhs * n).reshape(nrhs, n)

@@ -48,7 +48,8 @@ class _Opts(C.Structure):
                 ("algo", C.c_int), ("gram_solver", C.c_int), ("power_iters", C.c_int),
                 ("power_tol", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
                 ("power_v0", C.c_void_p), ("check_every", C.c_int), ("gram_blocks", C.c_int),
-                ("precision", C.c_int), ("rr_period", C.c_int)]
+                ("precision", C.c_int), ("rr_period", C.c_int), ("persistent", C.c_int),
+                ("cluster", C.c_int), ("block_threads", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -91,6 +92,7 @@ def load():
         "sstep_block_gram_noalloc": (I, [I64, I, P, I, P, I, P, P, P]),
         "sstep_pattern_grad": (I, [I64, P, P, P, P, P, D, I, P]),
         "sstep_update_values": (I, [P, P]),
+        "sstep_get_batch_config": (I, [P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,25 +188,35 @@ class Solver:
     def __init__(self, A, *, precond="jacobi", s=4, sweeps=2, rtol=1e-8, max_outer=10000,
                  algo="literal", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
                  lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", precision="fp64",
-                 rr_period=0, stream=None):
+                 rr_period=0, persistent=False, cluster=0, block_threads=0, stream=None):
+        """A: a Stencil or CSR (one system), or a list of 7-point Stencils (the batched
+        persistent solver; also used for a single Stencil when persistent=True)."""
         lib = load()
-        m = _Matrix()
-        self._weights = None
-        if isinstance(A, Stencil):
-            m.kind = MATRIX_STENCIL
-            m.n = A.n
-            m.nx, m.ny, m.nz, m.points = A.nx, A.ny, A.nz, A.points
-            if A.weights is not None:
-                self._weights = np.ascontiguousarray(A.weights, dtype=np.float64)
-                m.weights = self._weights.ctypes.data
-        elif isinstance(A, CSR):
-            m.kind = MATRIX_CSR
-            m.n = A.n
-            m.nnz = A.nnz
-            m.rowptr, m.colind, m.vals = _ptr(A.rowptr), _ptr(A.colind), _ptr(A.vals)
-        else:
-            raise TypeError("A must be a Stencil or a CSR")
-        self.n = int(m.n)
+        mats = list(A) if isinstance(A, (list, tuple)) else [A]
+        if not mats:
+            raise ValueError("no system given")
+        marr = (_Matrix * len(mats))()
+        self._weights = []
+        for m, a in zip(marr, mats):
+            if isinstance(a, Stencil):
+                m.kind = MATRIX_STENCIL
+                m.n = a.n
+                m.nx, m.ny, m.nz, m.points = a.nx, a.ny, a.nz, a.points
+                if a.weights is not None:
+                    w = np.ascontiguousarray(a.weights, dtype=np.float64)
+                    self._weights.append(w)
+                    m.weights = w.ctypes.data
+            elif isinstance(a, CSR):
+                m.kind = MATRIX_CSR
+                m.n = a.n
+                m.nnz = a.nnz
+                m.rowptr, m.colind, m.vals = _ptr(a.rowptr), _ptr(a.colind), _ptr(a.vals)
+            else:
+                raise TypeError("A must be a Stencil or a CSR, or a list of Stencils")
+        self.nsys = len(mats)
+        self.sizes = [int(m.n) for m in marr]
+        self.batched = self.nsys > 1 or bool(persistent)
+        self.n = int(marr[0].n)
         o = _Opts()
         lib.sstep_default_opts(C.byref(o))
         o.s, o.sweeps, o.rtol, o.max_outer = int(s), int(sweeps), float(rtol), int(max_outer)
@@ -216,11 +228,13 @@ class Solver:
         o.gram_blocks = {"full": 0, "sym": 1}[gram_blocks]
         o.precision = {"fp64": 0, "fp32_rr": 1}[precision]
         o.rr_period = int(rr_period)
+        o.persistent = int(bool(persistent))
+        o.cluster, o.block_threads = int(cluster), int(block_threads)
         self.s = int(s)
         self.max_outer = int(max_outer)
         pc = _Precond(PREC[precond])
         h = C.c_void_p()
-        _check(lib.sstep_setup(C.byref(m), 1, C.byref(pc), C.byref(o), _stream_ptr(stream), C.byref(h)))
+        _check(lib.sstep_setup(C.cast(marr, C.c_void_p), self.nsys, C.byref(pc), C.byref(o), _stream_ptr(stream), C.byref(h)))
         self._h = h
 
     # -- lifecycle
@@ -251,11 +265,20 @@ class Solver:
         return _info(info)
 
     def solve_batched(self, bs, xs, check=True):
+        """Single-system handle: one right-hand side after another.  Batched handle: bs and xs
+        hold nsys * nrhs device tensors, system-major (bs[sys * nrhs + j]); one launch."""
         n = len(bs)
+        if len(xs) != n:
+            raise ValueError("bs and xs differ in length")
+        nrhs = n
+        if self.batched:
+            if n % self.nsys:
+                raise ValueError("a batched handle takes nsys * nrhs right-hand sides")
+            nrhs = n // self.nsys
         B = (C.c_void_p * n)(*[_ptr(b) for b in bs])
         X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
         infos = (_Info * n)()
-        st = load().sstep_solve_batched(self._h, n, B, X, infos)
+        st = load().sstep_solve_batched(self._h, nrhs, B, X, infos)
         if check and st not in (OK, NOT_CONVERGED):
             _check(st)
         return [_info(i) for i in infos]
@@ -270,6 +293,14 @@ class Solver:
 
     def spmv(self, x, y):
         _check(load().sstep_spmv(self._h, _ptr(x), _ptr(y)))
+
+    def get_batch_config(self):
+        """Batched handle: the configuration in use (autotuned where it was left open)."""
+        v = [C.c_int() for _ in range(4)]
+        t = C.c_double()
+        _check(load().sstep_get_batch_config(self._h, *[C.byref(x) for x in v], C.byref(t)))
+        return dict(s=v[0].value, cluster=v[1].value, threads=v[2].value, slots=v[3].value,
+                    tune_ms=t.value)
 
     def get_basis_info(self):
         v = [C.c_double() for _ in range(5)]
