@@ -248,7 +248,7 @@ __device__ void mpk(cg::cluster_group& cl, const BSys& sy, const double* r, T* Z
     }
     const double c1 = q == 1 ? sy.ca : 2.0 * sy.ca;
     const T a1 = (T)(c1 * sy.d), c2 = (T)(q == 1 ? sy.cs : 2.0 * sy.cs);
-    const T* u = q > 1 ? Z + (q - 2) * ld : Z;  // z_{q-1} (q >= 2)
+    const T* u = Z + (q - 1) * ld;  // z_q (q >= 2; column q-1)
     for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
       int ix, iy, iz;
       coords(p, sy.nx, sy.ny, ix, iy, iz);
