@@ -50,6 +50,11 @@ def parse():
     p.add_argument("--extra", default="4:30,4:3:fp32_rr,4:30:fp32_rr",
                    help="extra s-step configs 's:nu[:precision]' to time once each, e.g. "
                         "'4:30,4:3:fp32_rr' (precision fp64 or fp32_rr)")
+    p.add_argument("--batch", default="64:16",
+                   help="batched workload 'nsys:nrhs' (7-point systems, edges uniform in 32..96); "
+                        "empty to skip")
+    p.add_argument("--q1", type=int, default=192,
+                   help="edge of the Q1 log-normal diffusion workload (FP32 basis, s = 8); 0 skips")
     return p.parse_args()
 
 
@@ -253,6 +258,113 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
+def run_batch(spec, dev, sstep, I, torch):
+    """Batched workload: nsys 7-point Poisson systems with edges drawn uniformly in 32..96
+    (seed 0), nrhs right-hand sides each (U[-1,1), seed 1 + system), Jacobi, nu = 3, rtol 1e-8,
+    solved by one persistent launch per call; against the plain FP64 form (one single-system
+    handle per system, right-hand sides one after another)."""
+    nsys, nrhs = (int(v) for v in spec.split(":"))
+    grids = I.batch_grids(nsys, 32, 96, seed=0)
+    n = [int(np.prod(g)) for g in grids]
+    A = [sstep.Stencil(*g, points=7) for g in grids]
+    bd, xd = [], []
+    for i in range(nsys):
+        rhs = torch.from_numpy(I.batch_rhs(i, n[i], nrhs)).to(dev)
+        for j in range(nrhs):
+            bd.append(rhs[j].contiguous())
+            xd.append(torch.zeros(n[i], dtype=torch.float64, device=dev))
+    out = {"workload": f"batch_{nsys}x{nrhs}_poisson7_edges32-96_jacobi_nu30",
+           "unknowns_per_rhs": int(sum(n)), "problems": nsys * nrhs,
+           "sweeps": "30 (the paper's own FGS sweep count; the batched configuration names none)"}
+    common = dict(sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0, cluster=0, block_threads=0)
+
+    def zero():
+        for x in xd:
+            x.zero_()
+        torch.cuda.synchronize()
+
+    for label, kw in (("fp64_s4", dict(s=4)), ("fp64_autotuned", dict(s=0)),
+                      ("fp32_rr_s4", dict(s=4, precision="fp32_rr")),
+                      ("fp32_rr_autotuned", dict(s=0, precision="fp32_rr")),
+                      ("fp64_autotuned_nu3", dict(s=0, sweeps=3))):
+        kw = dict(common, **kw)
+        t0 = time.perf_counter()
+        S = sstep.Solver(A, **kw)
+        t_setup = time.perf_counter() - t0
+        zero()
+        S.solve_batched(bd, xd)  # warm-up (graph instantiation)
+        zero()
+        t0 = time.perf_counter()
+        infos = S.solve_batched(bd, xd)
+        t = time.perf_counter() - t0
+        cfg = S.get_batch_config()
+        S.free()
+        its = [i.outer_iters for i in infos]
+        out[label] = {"s": t, "setup_s": t_setup, "config": cfg,
+                      "outer_iters_mean": float(np.mean(its)), "outer_iters_max": int(max(its)),
+                      "all_converged": all(i.status == sstep.OK for i in infos),
+                      "max_relres_true": float(max(i.relres_true for i in infos)),
+                      "launches_per_solve": int(infos[0].launches)}
+    # the plain FP64 form on a sample of the right-hand sides, scaled to all of them
+    sample = min(2, nrhs)
+    t_plain = 0.0
+    for i in range(nsys):
+        S = sstep.Solver(A[i], s=4, **{k: v for k, v in common.items() if k not in ("cluster", "block_threads")})
+        xs = [torch.zeros(n[i], dtype=torch.float64, device=dev) for _ in range(sample)]
+        S.solve(bd[i * nrhs], xs[0])  # graph instantiation
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve_batched(bd[i * nrhs:i * nrhs + sample], xs)
+        t_plain += time.perf_counter() - t0
+        S.free()
+    out["plain_fp64_s4_sequential_s"] = t_plain * nrhs / sample
+    out["plain_sample"] = f"{sample} of {nrhs} right-hand sides of every system, time scaled by {nrhs / sample:g}"
+    out["fp64_s4_speedup_vs_plain"] = out["plain_fp64_s4_sequential_s"] / out["fp64_s4"]["s"]
+    out["timing"] = "host wall time of one synchronous sstep_solve_batched call, after a warm-up call"
+    return out
+
+
+def run_q1(N, dev, sstep, I, torch):
+    """Q1 trilinear diffusion with log-normal conductivity (sigma 1, correlation 8 cells) on an
+    N^3 grid of interior vertices, CSR, Jacobi, s = 8, rtol 1e-8: the FP32-basis form against
+    the FP64 form and FP64 classical PCG of the same library."""
+    dims = (N, N, N)
+    t0 = time.perf_counter()
+    (rp, ci, v), kappa, xt, b = I.q1_lognormal_problem(dims)
+    t_gen = time.perf_counter() - t0
+    n = N ** 3
+    A = sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                  torch.from_numpy(v).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    xtd = torch.from_numpy(xt).to(dev)
+    out = {"workload": f"q1_lognormal_{N}^3_csr_jacobi_literal_s8", "n": n, "nnz": int(rp[-1]),
+           "generation_s": t_gen}
+    sol = {}
+    for label, kw in (("fp64_s8_nu30", dict(s=8, sweeps=30)),
+                      ("fp32_rr_s8_nu30", dict(s=8, sweeps=30, precision="fp32_rr", rr_period=8)),
+                      ("fp32_rr_s8_nu3", dict(s=8, sweeps=3, precision="fp32_rr", rr_period=8)),
+                      ("fp64_pcg", dict(algo="pcg"))):
+        S = sstep.Solver(A, rtol=1e-8, power_iters=20, power_tol=0.0, lambda_min=-1.0, **kw)
+        x = torch.zeros_like(bd)
+        S.solve(bd, x)  # warm-up (graph instantiation)
+        x.zero_()
+        torch.cuda.synchronize()
+        info = S.solve(bd, x)
+        S.free()
+        sol[label] = x
+        out[label] = {"s": info.ms_solve / 1e3, "status": info.status, "outer_iters": info.outer_iters,
+                      "relres_true": info.relres_true,
+                      "rel_error_vs_x_true": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
+    ref = sol["fp64_s8_nu30"]
+    for label in ("fp32_rr_s8_nu30", "fp32_rr_s8_nu3", "fp64_pcg"):
+        out[label]["rel_diff_vs_fp64_s8"] = float(torch.linalg.norm(sol[label] - ref) / torch.linalg.norm(ref))
+        out[label]["time_over_fp64_s8"] = out[label]["s"] / out["fp64_s8_nu30"]["s"]
+    out["timing"] = "host wall time of one sstep_solve (device buffers) after a warm-up solve"
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -378,6 +490,9 @@ def main():
             "time_over_fp64_pcg": ems[0] / float(np.mean(pms))}
         E.free()
 
+    batch = run_batch(args.batch, dev, sstep, I, torch) if args.batch else None
+    q1 = run_q1(args.q1, dev, sstep, I, torch) if args.q1 > 0 else None
+
     # ---- roofline of each kernel from the phase times
     work = kernel_work(args.s, n)
     hbm, hbm_src = hbm_peak()
@@ -433,6 +548,8 @@ def main():
                 "relres_true": pinfos[-1].relres_true},
         "sstep_over_pcg_time": ms_step / float(np.mean(pms)),
         "extra_configs": extra,
+        "batched": batch,
+        "q1_diffusion": q1,
         "e2e": {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(info.launches),

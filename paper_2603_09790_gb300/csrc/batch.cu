@@ -776,14 +776,15 @@ std::vector<int> sys_order(const BatchCtx* b) {
   return ord;
 }
 
-// Time one configuration on a trial batch (nrhs_trial seeded right-hand sides per system).
+// Time one configuration to convergence on a trial batch: one seeded right-hand side per
+// system, x0 = 0, the handle's own rtol, sweeps and iteration cap.
 sstep_status trial(BatchCtx* b, int s, int C, int NT, double* ms_out) {
   *ms_out = -1.0;
   KernelFn fn = pick_kernel(s, b->mixed, NT);
   if (!fn) return SSTEP_OK;
   const int nc = max_clusters(fn, C, NT);
   if (nc < 1) return SSTEP_OK;
-  const int nrhs = 2;
+  const int nrhs = 1;  // one seeded right-hand side per system
   int64_t total = 0;
   for (const BSys& y : b->hsys) total += y.n;
   const int nprob = b->nsys * nrhs;
@@ -892,22 +893,40 @@ sstep_status autotune(BatchCtx* b, int s_fixed, int c_fixed, int t_fixed) {
     }
   }
   const double t0 = wall_ms();
-  std::vector<int> ss = s_fixed ? std::vector<int>{s_fixed} : std::vector<int>{2, 4, 8};
-  std::vector<int> cs = c_fixed ? std::vector<int>{c_fixed} : std::vector<int>{2, 4, 8, 16};
-  std::vector<int> ts = t_fixed ? std::vector<int>{t_fixed} : std::vector<int>{256, 512};
+  // Two stages: the step size at one launch shape (it decides the iteration counts), then the
+  // launch shape (CTAs per cluster, threads per CTA) at that step size.
   double best = -1.0;
   Choice ch;
-  for (int s : ss)
+  auto run = [&](int s, int c, int t) -> sstep_status {
+    double ms;
+    sstep_status st = trial(b, s, c, t, &ms);
+    if (st == SSTEP_OK && ms > 0.0 && (best < 0.0 || ms < best)) {
+      best = ms;
+      ch = Choice{s, c, t};
+    }
+    return st;
+  };
+  const int c0 = c_fixed ? c_fixed : 4, t0s = t_fixed ? t_fixed : 256;
+  if (!s_fixed) {
+    for (int s : {2, 4, 8}) {
+      sstep_status st = run(s, c0, t0s);
+      if (st != SSTEP_OK) return st;
+    }
+  } else {
+    sstep_status st = run(s_fixed, c0, t0s);
+    if (st != SSTEP_OK) return st;
+  }
+  if (best > 0.0) {
+    const int s1 = ch.s;
+    std::vector<int> cs = c_fixed ? std::vector<int>{c_fixed} : std::vector<int>{2, 4, 8, 16};
+    std::vector<int> ts = t_fixed ? std::vector<int>{t_fixed} : std::vector<int>{256, 512};
     for (int c : cs)
       for (int t : ts) {
-        double ms;
-        sstep_status st = trial(b, s, c, t, &ms);
+        if (c == c0 && t == t0s) continue;
+        sstep_status st = run(s1, c, t);
         if (st != SSTEP_OK) return st;
-        if (ms > 0.0 && (best < 0.0 || ms < best)) {
-          best = ms;
-          ch = Choice{s, c, t};
-        }
       }
+  }
   if (best < 0.0) return bfail(SSTEP_ERR_UNSUPPORTED, "no launchable batched configuration");
   b->s = ch.s;
   b->cluster = ch.cluster;

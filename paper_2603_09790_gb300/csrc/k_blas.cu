@@ -513,10 +513,17 @@ template <int K>
 __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
                              double* partials, unsigned int* ticket) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // warp stage in double-float on the FP32 pipe; one FP64 conversion per warp and value
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const double v = warp_sum((double)hi[k] + (double)lo[k]);
-    if (lane == 0) buf[wid * K + k] = v;
+    float h = hi[k], l = lo[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+      df_add(h, l, oh, ol);
+    }
+    if (lane == 0) buf[wid * K + k] = (double)h + (double)l;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -648,26 +655,46 @@ __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   __syncthreads();
   float rrh[1] = {0.0f}, rrl[1] = {0.0f};
   const int64_t ld = a.ld;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // two points per trip, every load issued before the arithmetic (memory-level parallelism)
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < a.n; p0 += 2 * stride) {
+    const int64_t pp[2] = {p0, p0 + stride};
+    const bool has[2] = {true, p0 + stride < a.n};
+    float q[2][S], aq[2][S], xh[2], xl[2], rh[2], rl[2];
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const float q = __ldg(a.Q + j * ld + p), aq = __ldg(a.AQ + j * ld + p);
-      df_acc_prod(dxh, dxl, q, ah[j]);
-      dxl = fmaf(q, al[j], dxl);
-      df_acc_prod(drh, drl, aq, ah[j]);
-      drl = fmaf(aq, al[j], drl);
+    for (int u = 0; u < 2; ++u) {
+      const int64_t p = has[u] ? pp[u] : p0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q[u][j] = __ldg(a.Q + j * ld + p);
+        aq[u][j] = __ldg(a.AQ + j * ld + p);
+      }
+      xh[u] = a.xhi[p];
+      xl[u] = a.xlo[p];
+      rh[u] = a.rhi[p];
+      rl[u] = a.rlo[p];
     }
-    float xh = a.xhi[p], xl = a.xlo[p], rh = a.rhi[p], rl = a.rlo[p];
-    df_add(xh, xl, dxh, dxl);
-    df_add(rh, rl, -drh, -drl);
-    a.xhi[p] = xh;
-    a.xlo[p] = xl;
-    a.rhi[p] = rh;
-    a.rlo[p] = rl;
-    df_acc_prod(rrh[0], rrl[0], rh, rh);
-    rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!has[u]) continue;
+      const int64_t p = pp[u];
+      float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        df_acc_prod(dxh, dxl, q[u][j], ah[j]);
+        dxl = fmaf(q[u][j], al[j], dxl);
+        df_acc_prod(drh, drl, aq[u][j], ah[j]);
+        drl = fmaf(aq[u][j], al[j], drl);
+      }
+      df_add(xh[u], xl[u], dxh, dxl);
+      df_add(rh[u], rl[u], -drh, -drl);
+      a.xhi[p] = xh[u];
+      a.xlo[p] = xl[u];
+      a.rhi[p] = rh[u];
+      a.rlo[p] = rl[u];
+      df_acc_prod(rrh[0], rrl[0], rh[u], rh[u]);
+      rrl[0] = fmaf(2.0f * rh[u], rl[u], rrl[0]);
+    }
   }
   if (!df_grid_sums<1>(rrh, rrl, buf, a.partials, &a.ctrl->ticket[TK_UPDATE])) return;
   if (threadIdx.x == 0) {
@@ -1419,7 +1446,7 @@ cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStrea
 }
 
 cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st) {
-  const int grid = update_ctas(a.n);
+  const int grid = stream_ctas(a.n, 8);  // 2048 threads per SM: latency-bound otherwise
   switch (s) {
 #define CASE(S) \
   case S: k_update_xrf<S><<<grid, kThreads, 0, st>>>(a); return cudaGetLastError();
