@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--batch", default="64:16",
                    help="batched workload 'nsys:nrhs' (7-point systems, edges uniform in 32..96); "
                         "empty to skip")
+    p.add_argument("--adjoint", type=int, default=128,
+                   help="edge of the differentiated Q1 workload (theta ~ N(0, 0.5^2) per cell, unit "
+                        "right-hand side); 0 skips")
     p.add_argument("--q1", type=int, default=192,
                    help="edge of the Q1 log-normal diffusion workload (FP32 basis, s = 8); 0 skips")
     return p.parse_args()
@@ -365,6 +368,73 @@ def run_q1(N, dev, sstep, I, torch):
     return out
 
 
+def run_adjoint(N, dev, sstep, I, torch):
+    """Differentiated solve: Q1 diffusion on N^3 interior vertices with kappa = exp(theta),
+    theta ~ N(0, 0.5^2) iid per cell (seed 0), b = 1, loss = ||x - x_target||^2 with x_target
+    the solution for theta = 0.  Forward + backward (x recomputed, adjoint s-step solve, pattern
+    gradient, assembly transpose) against one plain FP64 solve of the same system; the gradient
+    is checked by central differences on 4 random cells."""
+    from paper_2603_09790_gb300 import autograd as AG
+    dims = (N, N, N)
+    t0 = time.perf_counter()
+    asm = AG.Q1Assembly(dims, dev)
+    t_asm = time.perf_counter() - t0
+    ncell = (N + 1) ** 3
+    theta0 = torch.from_numpy(0.5 * I.normal_pm(0, ncell)).to(dev)
+    b = torch.ones(N ** 3, dtype=torch.float64, device=dev)
+    opts = dict(s=4, sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0)
+    with torch.no_grad():
+        x_target = AG.solve(asm.values(torch.ones_like(theta0)), b, asm.pattern, **opts)
+
+    def loss_of(th, o):
+        x = AG.solve(asm.values(torch.exp(th)), b, asm.pattern, **o)
+        return torch.sum((x - x_target) ** 2)
+
+    th = theta0.clone().requires_grad_(True)
+    loss_of(th, opts).backward()  # warm-up
+    th = theta0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = loss_of(th, opts)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    loss.backward()
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    g = th.grad
+    # the plain FP64 form: set-up and solve of the same system, no gradient
+    vals = asm.values(torch.exp(theta0)).contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A = sstep.CSR(asm.pattern.rowptr, asm.pattern.colind, vals)
+    with sstep.Solver(A, **opts) as S:
+        x = torch.zeros_like(b)
+        info = S.solve(b, x)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # central differences on 4 random cells, solves at rtol 1e-12
+    o12 = dict(opts, rtol=1e-12)
+    rng = np.random.default_rng(2)
+    cells = rng.choice(ncell, 4, replace=False)
+    h = 1e-3
+    fd_err = []
+    with torch.no_grad():
+        for c in cells:
+            tp, tm = theta0.clone(), theta0.clone()
+            tp[c] += h
+            tm[c] -= h
+            fd = (loss_of(tp, o12).item() - loss_of(tm, o12).item()) / (2 * h)
+            fd_err.append(abs(fd - g[c].item()) / max(abs(g).max().item(), 1e-300))
+    return {"workload": f"q1_theta_{N}^3_csr_jacobi_literal_s4_nu30_adjoint", "n": N ** 3,
+            "cells": ncell, "assembly_map_s": t_asm, "loss": float(loss.item()),
+            "forward_s": t_fwd, "forward_backward_s": t_all, "plain_fp64_setup_solve_s": t_plain,
+            "plain_outer_iters": info.outer_iters,
+            "forward_backward_over_plain": t_all / t_plain,
+            "fd_cells": [int(c) for c in cells], "fd_step": h,
+            "fd_max_err_rel_to_max_grad": float(max(fd_err)),
+            "timing": "host wall time (synchronised), set-up of every solver handle included"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -492,6 +562,7 @@ def main():
 
     batch = run_batch(args.batch, dev, sstep, I, torch) if args.batch else None
     q1 = run_q1(args.q1, dev, sstep, I, torch) if args.q1 > 0 else None
+    adjoint = run_adjoint(args.adjoint, dev, sstep, I, torch) if args.adjoint > 0 else None
 
     # ---- roofline of each kernel from the phase times
     work = kernel_work(args.s, n)
@@ -550,6 +621,7 @@ def main():
         "extra_configs": extra,
         "batched": batch,
         "q1_diffusion": q1,
+        "differentiated": adjoint,
         "e2e": {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(info.launches),

@@ -11,6 +11,8 @@ sequential loops, FP64), written from the paper:
 * ``pcg``      -- classical Hestenes-Stiefel PCG (Section 1)
 * ``power``    -- power method for lambda_max, Section 2
 * ``cheb``     -- Chebyshev scalars alpha, sigma, gamma, Section 2
+* ``AMG``      -- the aggregation AMG preconditioner ``amg.c`` defines (the paper's own AMG
+                  is external; Section 5 treats M^{-1} as a black box)
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
@@ -24,7 +26,7 @@ import numpy as np
 from . import build as _build
 
 OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE = 0, 1, 2, 3, 4
-PREC = {"none": 0, "jacobi": 1}
+PREC = {"none": 0, "jacobi": 1, "amg": 2}
 ALGO = {"literal": 0, "onesync": 1}
 GRAM = {"fgs": 0, "cholesky": 1}
 
@@ -69,6 +71,20 @@ def _load():
         lib.or_pcgs.restype = C.c_int
         lib.or_pcg.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, P, P]
         lib.or_pcg.restype = C.c_int
+        I64 = C.c_int64
+        lib.or_amg_match.argtypes = [P, P, P]
+        lib.or_amg_match.restype = C.c_int
+        lib.or_amg_galerkin.argtypes = [P, P, I64, P, P, P, P]
+        lib.or_amg_galerkin.restype = C.c_int
+        lib.or_amg_setup.argtypes = [P, I64, C.c_int, P]
+        lib.or_amg_setup.restype = C.c_int
+        lib.or_amg_free.argtypes = [P]
+        lib.or_amg_apply.argtypes = [P, P, P]
+        lib.or_amg_nlevels.argtypes = [P]
+        lib.or_amg_nlevels.restype = C.c_int
+        lib.or_amg_level.argtypes = [P, C.c_int, P, P, P, P, P, P]
+        lib.or_amg_level.restype = C.c_int
+        lib.or_use_amg.argtypes = [P]
         _lib = lib
     return _lib
 
@@ -126,12 +142,20 @@ def prec_apply(prec: str, dinv, x) -> np.ndarray:
     return y
 
 
+def _use(prec, amg):
+    if prec == "amg":
+        if amg is None:
+            raise ValueError("prec='amg' needs amg=AMG(A)")
+        _load().or_use_amg(amg._h)
+
+
 def gershgorin_lower(A: CSR, prec: str = "jacobi") -> float:
     return float(_load().or_gershgorin_lower(A.ref, PREC[prec]))
 
 
-def power(A: CSR, prec: str, v0, max_iters: int = 50, tol: float = 1e-3):
+def power(A: CSR, prec: str, v0, max_iters: int = 50, tol: float = 1e-3, amg=None):
     """Power-method estimate of lambda_max(M^{-1}A) (Section 2); returns (lambda, iterations)."""
+    _use(prec, amg)
     d = jacobi_dinv(A) if prec == "jacobi" else np.ones(A.n)
     v0 = _f64(v0)
     it = C.c_int(0)
@@ -147,8 +171,10 @@ def cheb(lmin: float, lmax: float):
     return a.value, s.value, g.value
 
 
-def mpk(A: CSR, prec: str, r, s: int, c_alpha: float, c_sigma: float, c_gamma: float = 1.0):
+def mpk(A: CSR, prec: str, r, s: int, c_alpha: float, c_sigma: float, c_gamma: float = 1.0,
+        amg=None):
     """Algorithm 2: returns Z (n x s) and P (n x (s+1)) as column arrays (shape (s, n), (s+1, n))."""
+    _use(prec, amg)
     d = jacobi_dinv(A) if prec == "jacobi" else np.ones(A.n)
     r = _f64(r)
     Z = np.empty((s, A.n))
@@ -209,8 +235,9 @@ class Result:
 
 def pcgs(A: CSR, b, x0=None, *, s=4, nu=2, rtol=1e-8, max_outer=10000, algo="literal",
          gram="fgs", prec="jacobi", lambda_min=0.0, lambda_max=0.0, power_v0=None,
-         power_iters=50, power_tol=1e-3, history=False) -> Result:
-    """Algorithm 1 (PCG-S) on the CPU in FP64."""
+         power_iters=50, power_tol=1e-3, history=False, amg=None) -> Result:
+    """Algorithm 1 (PCG-S) on the CPU in FP64 (prec 'amg' applies the hierarchy amg)."""
+    _use(prec, amg)
     b = _f64(b)
     x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
     v0 = _f64(power_v0) if power_v0 is not None else np.ones(A.n)
@@ -225,8 +252,10 @@ def pcgs(A: CSR, b, x0=None, *, s=4, nu=2, rtol=1e-8, max_outer=10000, algo="lit
     return Result(x, info, hist, ea, eb)
 
 
-def pcg(A: CSR, b, x0=None, *, rtol=1e-8, max_iters=100000, prec="jacobi", history=False) -> Result:
+def pcg(A: CSR, b, x0=None, *, rtol=1e-8, max_iters=100000, prec="jacobi", history=False,
+        amg=None) -> Result:
     """Classical Hestenes-Stiefel PCG on the CPU in FP64."""
+    _use(prec, amg)
     b = _f64(b)
     x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
     info = _Info()
@@ -234,6 +263,81 @@ def pcg(A: CSR, b, x0=None, *, rtol=1e-8, max_iters=100000, prec="jacobi", histo
     _load().or_pcg(A.ref, PREC[prec], _ptr(b), _ptr(x), float(rtol), int(max_iters),
                    C.byref(info), _ptr(hist))
     return Result(x, info, hist)
+
+
+def _csr_from(n, nnz, rp, ci, v):
+    rowptr = np.ctypeslib.as_array(C.cast(rp, C.POINTER(C.c_int64)), shape=(n + 1,)).copy()
+    colind = np.ctypeslib.as_array(C.cast(ci, C.POINTER(C.c_int32)), shape=(max(nnz, 1),))[:nnz].copy()
+    vals = np.ctypeslib.as_array(C.cast(v, C.POINTER(C.c_double)), shape=(max(nnz, 1),))[:nnz].copy()
+    return CSR(rowptr, colind, vals)
+
+
+def amg_match(A: CSR):
+    """One greedy pairwise matching (amg.c): returns (agg, number of aggregates)."""
+    agg = np.empty(A.n, dtype=np.int32)
+    nc = C.c_int64(0)
+    if _load().or_amg_match(A.ref, _ptr(agg), C.byref(nc)) != OK:
+        raise ValueError("matching needs a positive diagonal")
+    return agg, int(nc.value)
+
+
+def amg_galerkin(A: CSR, agg, nc: int) -> CSR:
+    """P^T A P for the piecewise-constant aggregation agg (amg.c's fixed summation order)."""
+    agg = np.ascontiguousarray(agg, dtype=np.int32)
+    rp, ci, v = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    nnz = C.c_int64(0)
+    lib = _load()
+    if lib.or_amg_galerkin(A.ref, _ptr(agg), int(nc), C.byref(rp), C.byref(ci), C.byref(v),
+                           C.byref(nnz)) != OK:
+        raise ValueError("galerkin product failed")
+    out = _csr_from(int(nc), int(nnz.value), rp, ci, v)
+    libc = C.CDLL(None)
+    libc.free.argtypes = [C.c_void_p]
+    for ptr in (rp, ci, v):
+        libc.free(ptr)
+    return out
+
+
+class AMG:
+    """Aggregation AMG hierarchy of amg.c for A: levels until n <= coarse_max."""
+
+    def __init__(self, A: CSR, coarse_max: int = 2048, max_levels: int = 25):
+        self._lib = _load()
+        h = C.c_void_p()
+        st = self._lib.or_amg_setup(A.ref, int(coarse_max), int(max_levels), C.byref(h))
+        if st != OK:
+            raise ValueError(f"AMG set-up failed with status {st}")
+        self._h = h
+        self.nlevels = int(self._lib.or_amg_nlevels(h))
+
+    def level(self, l: int):
+        """(CSR of level l, its aggregation map or None on the coarsest level)."""
+        n, nnz = C.c_int64(), C.c_int64()
+        rp, ci, v, agg = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        if self._lib.or_amg_level(self._h, int(l), C.byref(n), C.byref(nnz), C.byref(rp), C.byref(ci),
+                                  C.byref(v), C.byref(agg)) != OK:
+            raise IndexError(l)
+        A = _csr_from(int(n.value), int(nnz.value), rp, ci, v)
+        a = None
+        if agg.value:
+            a = np.ctypeslib.as_array(C.cast(agg, C.POINTER(C.c_int32)), shape=(int(n.value),)).copy()
+        return A, a
+
+    def apply(self, b) -> np.ndarray:
+        """One V-cycle: M^{-1} b."""
+        b = _f64(b)
+        x = np.empty_like(b)
+        self._lib.or_amg_apply(self._h, _ptr(b), _ptr(x))
+        return x
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._lib.or_use_amg(None)
+                self._lib.or_amg_free(self._h)
+                self._h = None
+        except Exception:
+            pass
 
 
 class _swapped_library:

@@ -8,7 +8,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, "oracle.c")]
+SRC = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "amg.c")]
 
 
 def build(force: bool = False) -> str:

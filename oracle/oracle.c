@@ -50,6 +50,10 @@ int or_jacobi_dinv(const or_csr* A, double* dinv) {
 
 /* y = M^{-1} x. */
 void or_prec_apply(int prec, int64_t n, const double* dinv, const double* x, double* y) {
+  if (prec == OR_PREC_AMG) {
+    or_amg_apply(or_current_amg(), x, y);
+    return;
+  }
   if (prec == OR_PREC_JACOBI) {
     for (int64_t i = 0; i < n; ++i) y[i] = dinv[i] * x[i];
   } else {
@@ -60,6 +64,7 @@ void or_prec_apply(int prec, int64_t n, const double* dinv, const double* x, dou
 /* Gershgorin lower bound of spec(M^{-1}A), clamped at 0 (Section 2 sets lambda_min = 0;
  * for the Poisson matrices used here both readings give 0). */
 double or_gershgorin_lower(const or_csr* A, int prec) {
+  if (prec == OR_PREC_AMG) return 0.0;  /* no cheap bound for a V-cycle: Section 2's 0 */
   double lo = INFINITY;
   for (int64_t i = 0; i < A->n; ++i) {
     double d = 0.0, off = 0.0;

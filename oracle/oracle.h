@@ -37,7 +37,7 @@ enum {
   OR_ERR_NONFINITE = 4    /* non-finite residual norm */
 };
 
-enum { OR_PREC_NONE = 0, OR_PREC_JACOBI = 1 };
+enum { OR_PREC_NONE = 0, OR_PREC_JACOBI = 1, OR_PREC_AMG = 2 };
 enum { OR_ALGO_LITERAL = 0, OR_ALGO_ONESYNC = 1 };
 enum { OR_GRAM_FGS = 0, OR_GRAM_CHOLESKY = 1 };
 
@@ -98,6 +98,32 @@ int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
 /* Classical preconditioned CG (Hestenes-Stiefel).  hist optional, length max_iters+1. */
 int or_pcg(const or_csr* A, int prec, const double* b, double* x, double rtol, int max_iters,
            or_info* info, double* hist);
+
+/* ---- aggregation AMG (amg.c): the preconditioner OR_PREC_AMG.  The paper uses an external
+ * AMG as a black box M (Section 5); amg.c states the concrete one: double pairwise greedy
+ * matching on w_ij = -a_ij / sqrt(a_ii a_jj), unsmoothed aggregation, Galerkin coarse
+ * operators, l1-Jacobi pre/post smoothing, dense Cholesky on the coarsest level, V-cycle. */
+#define OR_AMG_MAX_LEVELS 32
+typedef struct or_amg or_amg;
+/* One pairwise matching of A's rows: agg[i] = aggregate of row i (aggregates of 1 or 2 rows,
+ * numbered by their lowest row); *nc = number of aggregates. */
+int or_amg_match(const or_csr* A, int32_t* agg, int64_t* nc);
+/* A_c = P^T A P for the aggregation agg (nc aggregates); allocates *rowptr, *colind, *vals
+ * (free with free()). */
+int or_amg_galerkin(const or_csr* A, const int32_t* agg, int64_t nc, int64_t** rowptr,
+                    int32_t** colind, double** vals, int64_t* nnz);
+/* Hierarchy for A: levels until n <= coarse_max or max_levels. */
+int or_amg_setup(const or_csr* A, int64_t coarse_max, int max_levels, or_amg** out);
+void or_amg_free(or_amg* M);
+/* x = M^{-1} b: one V-cycle. */
+void or_amg_apply(const or_amg* M, const double* b, double* x);
+int or_amg_nlevels(const or_amg* M);
+/* Level l's matrix and aggregation map (agg is NULL on the coarsest level); pointers owned by M. */
+int or_amg_level(const or_amg* M, int l, int64_t* n, int64_t* nnz, const int64_t** rowptr,
+                 const int32_t** colind, const double** vals, const int32_t** agg);
+/* The hierarchy that OR_PREC_AMG applies in or_prec_apply, or_pcgs and or_pcg. */
+void or_use_amg(const or_amg* M);
+const or_amg* or_current_amg(void);
 
 #ifdef __cplusplus
 }

@@ -12,8 +12,23 @@ import pytest
 import oracle as O
 
 from . import oracle_pins as P
+from . import test_oracle_amg as AMG_PINS
 
 SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+AMG_SRC = os.path.join(os.path.dirname(O.__file__), "amg.c")
+
+# Slips in amg.c, caught by the AMG pins (tests/test_oracle_amg.py).
+AMG_MUTATIONS = {
+    "amg_match_takes_weakest": ("if (w > wbest || (w == wbest && best >= 0 && j < best)) {",
+                                "if (best < 0 || w < wbest) {"),
+    "amg_galerkin_drops_repeat": ("          acc[pos[Jc]] += A->vals[k];", "          acc[pos[Jc]] += 0.0;"),
+    "amg_no_post_smoothing": ("  for (int64_t i = 0; i < n; ++i) x[i] += r[i] / L->dl1[i];\n}",
+                              "  for (int64_t i = 0; i < n; ++i) x[i] += 0.0 * r[i];\n}"),
+    "amg_restriction_sign": ("C->b[L->agg[i]] += r[i];", "C->b[L->agg[i]] -= r[i];"),
+    "amg_l1_uses_diagonal_only": ("for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k) s += fabs(L->vals[k]);",
+                                  "for (int64_t k = L->rowptr[i]; k < L->rowptr[i + 1]; ++k) s += (L->colind[k] == i) ? L->vals[k] : 0.0;"),
+    "amg_prolongation_missing": ("x[i] += C->x[L->agg[i]];", "x[i] += 0.0 * C->x[L->agg[i]];"),
+}
 
 MUTATIONS = {
     "spmv_reads_own_row": ("s += A->vals[k] * x[A->colind[k]];", "s += A->vals[k] * x[i];"),
@@ -41,25 +56,51 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
-    old, new = MUTATIONS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, "mutation anchor must occur exactly once"
-    mutated = tmp_path / "oracle.c"
-    mutated.write_text(src.replace(old, new))
+def build_mutant(tmp_path, target, old, new):
+    """Compile oracle.c + amg.c with one replacement in `target` (a source path)."""
+    srcs = []
+    for path in (SRC, AMG_SRC):
+        text = open(path).read()
+        if path == target:
+            assert text.count(old) == 1, "mutation anchor must occur exactly once"
+            text = text.replace(old, new)
+        out = tmp_path / os.path.basename(path)
+        out.write_text(text)
+        srcs.append(str(out))
     (tmp_path / "oracle.h").write_text(open(SRC[:-1] + "h").read())
     lib = tmp_path / "libmut.so"
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-o", str(lib), str(mutated), "-lm"])
+                           "-o", str(lib)] + srcs + ["-lm"])
+    return lib
+
+
+def run_pins(lib, pins):
     failed = []
     with O.use_library(str(lib)):
-        for pin in P.ALL_PINS:
+        for pin in pins:
             try:
                 pin()
-            except (AssertionError, FloatingPointError, ValueError, np_linalg_error()):
+            except (AssertionError, FloatingPointError, ValueError, IndexError, np_linalg_error()):
                 failed.append(pin.__name__)
-    assert failed, f"no pin caught mutation {name}"
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    lib = build_mutant(tmp_path, SRC, old, new)
+    assert run_pins(lib, P.ALL_PINS), f"no pin caught mutation {name}"
+
+
+AMG_PIN_FUNCS = [getattr(AMG_PINS, k) for k in sorted(dir(AMG_PINS))
+                 if k.startswith("test_") and k != "test_amg_rejects_bad_input"]
+
+
+@pytest.mark.parametrize("name", sorted(AMG_MUTATIONS))
+def test_planted_amg_mistake_is_caught(name, tmp_path):
+    old, new = AMG_MUTATIONS[name]
+    lib = build_mutant(tmp_path, AMG_SRC, old, new)
+    assert run_pins(lib, AMG_PIN_FUNCS), f"no AMG pin caught mutation {name}"
 
 
 def np_linalg_error():
