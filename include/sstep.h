@@ -71,10 +71,20 @@ typedef struct {
 
 /* ------------------------------------------------------------------ preconditioner M */
 /* The paper treats M^{-1} as a black box (Section 4): NONE is M = I (the CG-S runs of
- * Section 6.1), JACOBI is M = diag(A). */
-enum { SSTEP_PREC_NONE = 0, SSTEP_PREC_JACOBI = 1 };
+ * Section 6.1), JACOBI is M = diag(A).  AMG (CSR operators, FP64 s-step forms) is one V-cycle
+ * of this library's aggregation AMG; the paper's own AMG is external (Section 5), so the
+ * library defines it: coupling w_ij = -a_ij / sqrt(a_ii a_jj); greedy pairwise matching of the
+ * rows in increasing order (largest w_ij > 0, ties to the lower index), applied twice per
+ * level; unsmoothed piecewise-constant prolongation P; Galerkin A_c = P^T A P summed in a fixed
+ * order (reproducible bit for bit); one l1-Jacobi sweep (D = diag(sum_j |a_ij|)) before and
+ * after the coarse correction; a dense solve (from the Cholesky factor, set up on the host)
+ * once n <= amg_coarse_max.  The V-cycle is symmetric positive definite.  Set-up runs on the
+ * host; every application runs on the device. */
+enum { SSTEP_PREC_NONE = 0, SSTEP_PREC_JACOBI = 1, SSTEP_PREC_AMG = 2 };
 typedef struct {
   int kind;
+  int amg_coarse_max;  /* AMG: largest directly solved level, 1..4096 (0: 512) */
+  int amg_max_levels;  /* AMG: at most this many levels, 1..32 (0: 25) */
 } sstep_precond;
 
 /* ------------------------------------------------------------------ options */
@@ -182,6 +192,18 @@ SSTEP_API sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const doubl
  * SSTEP_ERR_INVALID for a single-system handle. */
 SSTEP_API sstep_status sstep_get_batch_config(sstep_handle h, int* s, int* cluster, int* threads,
                                               int* slots, double* tune_ms);
+
+/* AMG handle (precond kind SSTEP_PREC_AMG): the hierarchy, for inspection.  *nlevels receives
+ * the number of levels.  sstep_amg_level copies level l's matrix (CSR: rowptr n+1, colind nnz,
+ * vals nnz) and its aggregation map agg (n entries; the coarsest level has none and agg is left
+ * untouched) into HOST arrays; any pointer may be NULL (n and nnz first, to size the arrays). */
+SSTEP_API sstep_status sstep_amg_levels(sstep_handle h, int* nlevels);
+SSTEP_API sstep_status sstep_amg_level(sstep_handle h, int l, int64_t* n, int64_t* nnz,
+                                       int64_t* rowptr, int32_t* colind, double* vals,
+                                       int32_t* agg);
+/* x = M^{-1} b: one V-cycle of the handle's AMG on device vectors b and x (n doubles each,
+ * distinct), ordered on the handle's stream and finished on return. */
+SSTEP_API sstep_status sstep_amg_apply(sstep_handle h, const double* b, double* x);
 
 /* Release everything the handle owns (NULL is accepted). */
 SSTEP_API sstep_status sstep_free(sstep_handle h);

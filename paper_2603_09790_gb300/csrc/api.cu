@@ -96,6 +96,10 @@ struct sstep_ctx {
   int* poll_flags = nullptr;  // pinned, 4 ints
   // batched persistent solver (nsys > 1 or opts.persistent): everything lives in here
   BatchCtx* batch = nullptr;
+  // aggregation AMG preconditioner (kind SSTEP_PREC_AMG) and its MPK work vector
+  AmgHier* amg = nullptr;
+  double* t = nullptr;
+  int amg_coarse_max = 512, amg_max_levels = 25;
 };
 
 namespace {
@@ -124,7 +128,33 @@ EpiArgs epi_base(sstep_ctx* h, int epi) {
 }
 
 // Algorithm 2 on residual r: Z = [z_1..z_s], AZ = [A z_1 .. A z_s].
+// AMG: M^{-1} is a V-cycle, so SpMV, M^{-1} and the recurrence run as separate launches:
+// z_1 = M^{-1} r; A z_q; t = M^{-1}(A z_q); z_{q+1} = c1 t - c2 z_q - c3 z_{q-1}.
+sstep_status run_mpk_amg(sstep_ctx* h, const double* r, double* Z, double* AZ, int s) {
+  const int64_t ld = h->ld, n = h->n;
+  const int per = amg_kernels_per_apply(h->amg);
+  CK(amg_apply(h->amg, r, Z, h->st));
+  h->nlaunch += per;
+  for (int q = 1; q <= s; ++q) {
+    EpiArgs e = epi_base(h, EP_SPMV);
+    e.u = Z + (q - 1) * ld;
+    e.y = AZ + (q - 1) * ld;
+    CK(launch_operator(h->op, e, h->st));
+    ++h->nlaunch;
+    if (q == s) break;
+    CK(amg_apply(h->amg, AZ + (q - 1) * ld, h->t, h->st));
+    h->nlaunch += per;
+    const double c1 = q == 1 ? h->c_alpha : 2.0 * h->c_alpha;
+    const double c2 = q == 1 ? h->c_sigma : 2.0 * h->c_sigma;
+    CK(launch_cheb_combine(n, h->t, Z + (q - 1) * ld, q == 1 ? nullptr : Z + (q - 2) * ld, c1, c2,
+                           h->c_gamma, Z + q * ld, h->st));
+    ++h->nlaunch;
+  }
+  return SSTEP_OK;
+}
+
 sstep_status run_mpk(sstep_ctx* h, const double* r, double* Z, double* AZ, int s, Ctrl* ctrl) {
+  if (h->amg) return run_mpk_amg(h, r, Z, AZ, s);
   const int64_t ld = h->ld;
   for (int q = 1; q <= s; ++q) {
     EpiArgs e = epi_base(h, q == 1 ? EP_MPK_FIRST : EP_MPK);
@@ -424,6 +454,25 @@ sstep_status power_method(sstep_ctx* h) {
     CK(launch_fill_splitmix(h->x, h->n, 1ull, h->st));
   }
   CK(launch_norm2(h->x, h->n, h->ctrl, h->partials, 0, h->st));
+  if (h->amg) {  // t = M^{-1} A v by a V-cycle, then the scaling and the stop rule
+    double* v = h->x;
+    double* t = h->b;
+    for (int it = 0; it < h->o.power_iters; ++it) {
+      EpiArgs e = epi_base(h, EP_SPMV);
+      e.u = v;
+      e.y = h->r;
+      CK(launch_operator(h->op, e, h->st));
+      CK(amg_apply(h->amg, h->r, t, h->st));
+      CK(launch_power_scale(h->n, t, h->ctrl, h->partials, h->st));
+      std::swap(v, t);
+    }
+    CKS(read_ctrl(h));
+    h->lmax = h->hctrl->lam;
+    h->power_run = h->hctrl->power_iters;
+    if (!(h->lmax > 0.0) || h->lmax != h->lmax)
+      return fail(SSTEP_ERR_INVALID, "power method produced no positive estimate of lambda_max");
+    return SSTEP_OK;
+  }
   double* buf[2] = {h->x, h->r};
   for (int it = 0; it < h->o.power_iters; ++it) {
     EpiArgs e = epi_base(h, EP_POWER);
@@ -507,6 +556,8 @@ sstep_status validate_opts(const sstep_opts* o) {
 void destroy(sstep_ctx* h) {
   if (!h) return;
   if (h->batch) batch_free(h->batch);
+  if (h->amg) amg_free(h->amg);
+  if (h->t) cudaFree(h->t);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
@@ -537,8 +588,17 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   h->s = o->s;
   if (o->check_every <= 0) h->o.check_every = 0;
   h->prec_kind = M ? M->kind : SSTEP_PREC_JACOBI;
-  if (h->prec_kind != SSTEP_PREC_NONE && h->prec_kind != SSTEP_PREC_JACOBI)
-    return fail(SSTEP_ERR_UNSUPPORTED, "preconditioner kind not implemented");
+  if (h->prec_kind != SSTEP_PREC_NONE && h->prec_kind != SSTEP_PREC_JACOBI &&
+      h->prec_kind != SSTEP_PREC_AMG)
+    return fail(SSTEP_ERR_INVALID, "unknown preconditioner kind");
+  if (h->prec_kind == SSTEP_PREC_AMG) {
+    if (A->kind != SSTEP_MATRIX_CSR)
+      return fail(SSTEP_ERR_UNSUPPORTED, "the AMG preconditioner takes CSR operators");
+    if (o->algo == SSTEP_ALGO_PCG || o->precision != SSTEP_PRECISION_FP64)
+      return fail(SSTEP_ERR_UNSUPPORTED, "the AMG preconditioner serves the FP64 s-step forms");
+    if (M->amg_coarse_max) h->amg_coarse_max = M->amg_coarse_max;
+    if (M->amg_max_levels) h->amg_max_levels = M->amg_max_levels;
+  }
   h->user_stream = (cudaStream_t)stream;
   // Work runs on the caller's stream when one is given (so the caller's CUDA events bracket
   // the kernels); the legacy default stream cannot be captured, so NULL gets a private stream.
@@ -644,7 +704,13 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
 
   // ---- Jacobi M^{-1} for CSR
   if (A->kind == SSTEP_MATRIX_CSR) {
-    if (h->prec_kind == SSTEP_PREC_JACOBI) {
+    if (h->prec_kind == SSTEP_PREC_AMG) {
+      CKS(amg_build(h->rowptr, h->colind, h->vals, h->n, h->nnz, h->amg_coarse_max,
+                    h->amg_max_levels, h->st, &h->amg));
+      CKS(alloc(&h->t, ld));
+      h->M.dinv = nullptr;
+      h->M.dinv_u = 1.0;
+    } else if (h->prec_kind == SSTEP_PREC_JACOBI) {
       CKS(alloc(&h->dinv, ld));
       int* bad = nullptr;
       CK(cudaMalloc(&bad, sizeof(int)));
@@ -665,7 +731,9 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
 
   // ---- Chebyshev interval (Section 2)
   const int jac = h->prec_kind == SSTEP_PREC_JACOBI;
-  if (o->lambda_min < 0.0) {
+  if (o->lambda_min < 0.0 && h->amg) {
+    h->lmin = 0.0;  // no cheap bound for a V-cycle: Section 2's 0
+  } else if (o->lambda_min < 0.0) {
     if (A->kind == SSTEP_MATRIX_STENCIL) {
       h->lmin = stencil_gershgorin(h->op.st, jac);
     } else {
@@ -942,6 +1010,30 @@ sstep_status sstep_solve_batched(sstep_handle h, int nrhs, const double* const* 
       return st;
   }
   return first;
+}
+
+sstep_status sstep_amg_levels(sstep_handle h, int* nlevels) {
+  g_err.clear();
+  if (!h || !h->amg || !nlevels) return fail(SSTEP_ERR_INVALID, "not an AMG handle");
+  *nlevels = amg_nlevels(h->amg);
+  return SSTEP_OK;
+}
+
+sstep_status sstep_amg_level(sstep_handle h, int l, int64_t* n, int64_t* nnz, int64_t* rowptr,
+                             int32_t* colind, double* vals, int32_t* agg) {
+  g_err.clear();
+  if (!h || !h->amg) return fail(SSTEP_ERR_INVALID, "not an AMG handle");
+  sstep_status st = amg_level_copy(h->amg, l, n, nnz, rowptr, colind, vals, agg);
+  if (st != SSTEP_OK) return fail(st, "level out of range");
+  return SSTEP_OK;
+}
+
+sstep_status sstep_amg_apply(sstep_handle h, const double* b, double* x) {
+  g_err.clear();
+  if (!h || !h->amg || !b || !x || b == x) return fail(SSTEP_ERR_INVALID, "bad AMG apply arguments");
+  CK(amg_apply(h->amg, b, x, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return SSTEP_OK;
 }
 
 sstep_status sstep_get_batch_config(sstep_handle h, int* s, int* cluster, int* threads,
@@ -1226,6 +1318,18 @@ sstep_status sstep_update_values(sstep_handle h, const double* vals) {
     CK(cudaFreeAsync(bad, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (hbad) return fail(SSTEP_ERR_INVALID, "Jacobi needs a positive diagonal entry in every row");
+  }
+  if (h->amg) {  // the hierarchy depends on the values: rebuild it, re-capture the graphs
+    CK(cudaStreamSynchronize(h->st));
+    amg_free(h->amg);
+    h->amg = nullptr;
+    CKS(amg_build(h->rowptr, h->colind, h->vals, h->n, h->nnz, h->amg_coarse_max,
+                  h->amg_max_levels, h->st, &h->amg));
+    for (auto& g : h->gexec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
   }
   if (h->valsf) CK(launch_d2f(h->vals, h->valsf, nnz, h->st));
   if (h->dinvf) CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));

@@ -410,6 +410,21 @@ int operator_grid_ctas(const OpDesc& A);  // CTAs of one operator launch (partia
 // Sets the calling thread's message returned by sstep_last_error() (defined in api.cu).
 void set_last_error(const char* msg);
 
+// Aggregation AMG preconditioner (amg.cu): host set-up, device V-cycle.
+struct AmgHier;
+sstep_status amg_build(const int64_t* rowptr_dev, const int32_t* colind_dev, const double* vals_dev,
+                       int64_t n, int64_t nnz, int64_t coarse_max, int max_levels,
+                       cudaStream_t st, AmgHier** out);
+cudaError_t amg_apply(const AmgHier* H, const double* b, double* x, cudaStream_t st);  // b != x
+int amg_kernels_per_apply(const AmgHier* H);
+int amg_nlevels(const AmgHier* H);
+sstep_status amg_level_copy(const AmgHier* H, int l, int64_t* n, int64_t* nnz, int64_t* rowptr,
+                            int32_t* colind, double* vals, int32_t* agg);
+void amg_free(AmgHier* H);
+cudaError_t launch_cheb_combine(int64_t n, const double* t, const double* zq, const double* zprev,
+                                double c1, double c2, double c3, double* znext, cudaStream_t st);
+cudaError_t launch_power_scale(int64_t n, double* t, Ctrl* c, double* partials, cudaStream_t st);
+
 // Batched persistent solver (batch.cu): many 7-point stencil systems x right-hand sides.
 struct BatchCtx;
 sstep_status batch_setup(const sstep_matrix* A, int nsys, const sstep_precond* M,

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsstep.so")
 
 OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED = range(8)
 MATRIX_CSR, MATRIX_STENCIL = 0, 1
-PREC = {"none": 0, "jacobi": 1}
+PREC = {"none": 0, "jacobi": 1, "amg": 2}
 ALGO = {"onesync": 0, "literal": 1, "pcg": 2}
 GRAM = {"fgs": 0, "cholesky": 1}
 
@@ -40,7 +40,7 @@ class _Matrix(C.Structure):
 
 
 class _Precond(C.Structure):
-    _fields_ = [("kind", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("amg_coarse_max", C.c_int), ("amg_max_levels", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -93,6 +93,9 @@ def load():
         "sstep_pattern_grad": (I, [I64, P, P, P, P, P, D, I, P]),
         "sstep_update_values": (I, [P, P]),
         "sstep_get_batch_config": (I, [P, P, P, P, P, P]),
+        "sstep_amg_levels": (I, [P, P]),
+        "sstep_amg_level": (I, [P, I, P, P, P, P, P, P]),
+        "sstep_amg_apply": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,7 +191,8 @@ class Solver:
     def __init__(self, A, *, precond="jacobi", s=4, sweeps=2, rtol=1e-8, max_outer=10000,
                  algo="literal", gram="fgs", power_iters=50, power_tol=1e-3, lambda_min=0.0,
                  lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", precision="fp64",
-                 rr_period=0, persistent=False, cluster=0, block_threads=0, stream=None):
+                 rr_period=0, persistent=False, cluster=0, block_threads=0, amg_coarse_max=0,
+                 amg_max_levels=0, stream=None):
         """A: a Stencil or CSR (one system), or a list of 7-point Stencils (the batched
         persistent solver; also used for a single Stencil when persistent=True)."""
         lib = load()
@@ -232,7 +236,7 @@ class Solver:
         o.cluster, o.block_threads = int(cluster), int(block_threads)
         self.s = int(s)
         self.max_outer = int(max_outer)
-        pc = _Precond(PREC[precond])
+        pc = _Precond(PREC[precond], int(amg_coarse_max), int(amg_max_levels))
         h = C.c_void_p()
         _check(lib.sstep_setup(C.cast(marr, C.c_void_p), self.nsys, C.byref(pc), C.byref(o), _stream_ptr(stream), C.byref(h)))
         self._h = h
@@ -293,6 +297,28 @@ class Solver:
 
     def spmv(self, x, y):
         _check(load().sstep_spmv(self._h, _ptr(x), _ptr(y)))
+
+    def amg_levels(self):
+        """AMG handle: the hierarchy, one (CSR arrays, aggregation map or None) per level."""
+        lib = load()
+        nl = C.c_int()
+        _check(lib.sstep_amg_levels(self._h, C.byref(nl)))
+        out = []
+        for l in range(nl.value):
+            n, nnz = C.c_int64(), C.c_int64()
+            _check(lib.sstep_amg_level(self._h, l, C.byref(n), C.byref(nnz), None, None, None, None))
+            rp = np.empty(n.value + 1, dtype=np.int64)
+            ci = np.empty(nnz.value, dtype=np.int32)
+            v = np.empty(nnz.value)
+            agg = np.full(n.value, -1, dtype=np.int32)
+            _check(lib.sstep_amg_level(self._h, l, None, None, rp.ctypes.data, ci.ctypes.data,
+                                       v.ctypes.data, agg.ctypes.data))
+            out.append(((rp, ci, v), agg if l + 1 < nl.value else None))
+        return out
+
+    def amg_apply(self, b, x):
+        """x = M^{-1} b (one V-cycle) on device tensors."""
+        _check(load().sstep_amg_apply(self._h, _ptr(b), _ptr(x)))
 
     def get_batch_config(self):
         """Batched handle: the configuration in use (autotuned where it was left open)."""

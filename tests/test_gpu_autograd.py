@@ -53,11 +53,13 @@ def _loss_fn(asm, b, target, opts):
     return f
 
 
-def test_q1_theta_gradient():
+@pytest.mark.parametrize("precond", ["jacobi", "amg"])
+def test_q1_theta_gradient(precond):
     dims = (12, 10, 9)
     theta0, b0, t0 = _problem(dims, 5)
     asm = AG.Q1Assembly(dims, DEV)
-    opts = dict(s=4, sweeps=30, rtol=1e-12)
+    pk = dict(precond=precond, amg_coarse_max=64) if precond == "amg" else {}
+    opts = dict(s=4, sweeps=30, rtol=1e-12, **pk)
     b, target = torch.from_numpy(b0).to(DEV), torch.from_numpy(t0).to(DEV)
     theta = torch.from_numpy(theta0).to(DEV).requires_grad_(True)
     f = _loss_fn(asm, b, target, opts)
@@ -86,7 +88,7 @@ def test_q1_theta_gradient():
     # (b) central differences through the CUDA solver on 32 random cells
     rng = np.random.default_rng(9)
     cells = rng.choice(np.flatnonzero(np.abs(gd) > 1e-3 * np.abs(gd).max()), 32, replace=False)
-    fo = _loss_fn(asm, b, target, dict(s=4, sweeps=30, rtol=1e-13))
+    fo = _loss_fn(asm, b, target, dict(s=4, sweeps=30, rtol=1e-13, **pk))
     h = 1e-4
     for c in cells:
         tp = torch.from_numpy(theta0).to(DEV)
