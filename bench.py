@@ -382,7 +382,8 @@ def run_adjoint(N, dev, sstep, I, torch):
     ncell = (N + 1) ** 3
     theta0 = torch.from_numpy(0.5 * I.normal_pm(0, ncell)).to(dev)
     b = torch.ones(N ** 3, dtype=torch.float64, device=dev)
-    opts = dict(s=4, sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0)
+    opts = dict(s=4, sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0, precond="amg",
+                amg_coarse_max=512)
     with torch.no_grad():
         x_target = AG.solve(asm.values(torch.ones_like(theta0)), b, asm.pattern, **opts)
 
@@ -425,7 +426,16 @@ def run_adjoint(N, dev, sstep, I, torch):
             tm[c] -= h
             fd = (loss_of(tp, o12).item() - loss_of(tm, o12).item()) / (2 * h)
             fd_err.append(abs(fd - g[c].item()) / max(abs(g).max().item(), 1e-300))
-    return {"workload": f"q1_theta_{N}^3_csr_jacobi_literal_s4_nu30_adjoint", "n": N ** 3,
+    # the same solve with Jacobi instead of the V-cycle
+    t0 = time.perf_counter()
+    with sstep.Solver(A, **dict(opts, precond="jacobi")) as S:
+        xj = torch.zeros_like(b)
+        info_j = S.solve(b, xj)
+    torch.cuda.synchronize()
+    t_jac = time.perf_counter() - t0
+    return {"workload": f"q1_theta_{N}^3_csr_amg_literal_s4_nu30_adjoint", "n": N ** 3,
+            "amg": "double pairwise aggregation, l1-Jacobi V-cycle, dense coarse solve at <= 512",
+            "plain_fp64_jacobi_setup_solve_s": t_jac, "plain_jacobi_outer_iters": info_j.outer_iters,
             "cells": ncell, "assembly_map_s": t_asm, "loss": float(loss.item()),
             "forward_s": t_fwd, "forward_backward_s": t_all, "plain_fp64_setup_solve_s": t_plain,
             "plain_outer_iters": info.outer_iters,
