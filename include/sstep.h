@@ -13,8 +13,10 @@
  *    library's own device buffers, with the copies ordered on the handle's stream.
  *  - Every entry point returns an sstep_status and never aborts, throws or traps.  A
  *    description of the last failure on the calling thread is returned by sstep_last_error().
- *  - Work is ordered on the CUDA stream given at set-up (passed as void*; NULL = the legacy
- *    default stream).  sstep_solve* return after the solve has finished on that stream.
+ *  - Work is ordered on the CUDA stream given at set-up (passed as void*).  NULL: a private
+ *    blocking stream of the handle, which is ordered with the caller's work on the legacy
+ *    default stream (a capturable stand-in for it).  sstep_solve* return after the solve has
+ *    finished on that stream.
  *  - Not thread-safe per handle: one handle must not be used from two threads at once.
  */
 #ifndef SSTEP_H

@@ -54,13 +54,17 @@ class _SStepSolve(torch.autograd.Function):
         gvals = None
         if ctx.needs_input_grad[0]:
             gvals = torch.empty_like(vals)
-            sstep.pattern_grad(pattern.rowptr, pattern.colind, lam, x, gvals)
+            sstep.pattern_grad(pattern.rowptr, pattern.colind, lam, x, gvals,
+                               stream=ctx.opts.get("stream"))
         return gvals, (lam if ctx.needs_input_grad[1] else None), None, None
 
 
 def solve(vals, b, pattern: CSRPattern, **opts):
     """x = A^{-1} b with A = CSR(pattern, vals), differentiable in vals and b; opts are
-    sstep.Solver keywords (s, sweeps, rtol, ...)."""
+    sstep.Solver keywords (s, sweeps, rtol, precond, ...).  The solves are ordered on torch's
+    current stream unless opts names another."""
+    if "stream" not in opts:
+        opts = dict(opts, stream=torch.cuda.current_stream(b.device).cuda_stream or None)
     return _SStepSolve.apply(vals, b, pattern, opts)
 
 

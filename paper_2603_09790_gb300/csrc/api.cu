@@ -601,12 +601,14 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   }
   h->user_stream = (cudaStream_t)stream;
   // Work runs on the caller's stream when one is given (so the caller's CUDA events bracket
-  // the kernels); the legacy default stream cannot be captured, so NULL gets a private stream.
+  // the kernels).  The legacy default stream cannot be captured, so NULL gets a private
+  // *blocking* stream: it stays ordered with the caller's work on the legacy default stream
+  // (for example the kernels that produced b or the CSR values).
   if (h->user_stream) {
     h->st = h->user_stream;
     h->own_stream = false;
   } else {
-    CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->st, cudaStreamDefault));
     h->own_stream = true;
   }
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));

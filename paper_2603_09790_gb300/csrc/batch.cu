@@ -1157,7 +1157,8 @@ sstep_status batch_setup(const sstep_matrix* A, int nsys, const sstep_precond* M
   if (st) {
     b->st = st;
   } else {
-    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    // blocking: ordered with the caller's work on the legacy default stream
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamDefault) != cudaSuccess) {
       delete b;
       return bfail(SSTEP_ERR_CUDA, "stream creation failed");
     }
