@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--adjoint", type=int, default=128,
                    help="edge of the differentiated Q1 workload (theta ~ N(0, 0.5^2) per cell, unit "
                         "right-hand side); 0 skips")
+    p.add_argument("--hpcg", type=int, default=200,
+                   help="edge of the 27-point Poisson benchmark with unit right-hand side "
+                        "(s in 4..10, eta diagnostics); 0 skips")
     p.add_argument("--q1", type=int, default=192,
                    help="edge of the Q1 log-normal diffusion workload (FP32 basis, s = 8); 0 skips")
     return p.parse_args()
@@ -368,6 +371,51 @@ def run_q1(N, dev, sstep, I, torch):
     return out
 
 
+def run_hpcg27(N, dev, sstep, torch):
+    """The paper's own benchmark problem on one GPU: 27-point Poisson on N^3 interior points
+    (N = 200 is one GPU's share of its 64-GPU run), unit right-hand side, Jacobi, rtol 1e-8,
+    s in {4, 6, 8, 10} at nu = 30, FP64; outer counts, times, the reduced-solve residuals
+    eta_alpha / eta_beta of every outer iteration, and the diagonally normalised Gram pattern
+    for s = 10 at outer iterations 5..8 (mean |W_ij| / sqrt(W_ii W_jj) by distance |i - j|)."""
+    A = sstep.Stencil(N, N, N, 27)
+    b = torch.ones(N ** 3, dtype=torch.float64, device=dev)
+    out = {"workload": f"poisson27_{N}^3_stencil_jacobi_unit_rhs_literal_nu30", "n": N ** 3}
+    common = dict(rtol=1e-8, power_iters=20, power_tol=0.0, lambda_min=-1.0)
+    for s_ in (4, 6, 8, 10):
+        S = sstep.Solver(A, s=s_, sweeps=30, **common)
+        x = torch.zeros_like(b)
+        S.solve(b, x)  # warm-up (graph instantiation)
+        x.zero_()
+        info = S.solve(b, x)
+        d = S.get_diagnostics()
+        S.free()
+        ea, eb = d["eta_a"], d["eta_b"]
+        e = {"s": info.ms_solve / 1e3, "outer_iters": info.outer_iters,
+             "inner_equiv": info.inner_equiv, "relres_true": info.relres_true,
+             "eta_alpha_max": float(ea.max()) if ea.size else None,
+             "eta_alpha_median": float(np.median(ea)) if ea.size else None,
+             "eta_beta_max": float(eb.max()) if eb.size else None,
+             "eta_beta_median": float(np.median(eb)) if eb.size else None}
+        if s_ == 10 and d["W"].shape[0] >= 9:
+            pat = []
+            for k in range(5, 9):
+                W = d["W"][k]
+                dg = np.sqrt(np.diag(W))
+                Wn = np.abs(W) / np.outer(dg, dg)
+                pat.append([float(np.mean(np.diag(Wn, off))) for off in range(s_)])
+            e["gram_pattern_k5_8_by_offset"] = pat
+        out[f"s{s_}_nu30"] = e
+    P = sstep.Solver(A, algo="pcg", **common)
+    x = torch.zeros_like(b)
+    P.solve(b, x)
+    x.zero_()
+    info = P.solve(b, x)
+    P.free()
+    out["pcg"] = {"s": info.ms_solve / 1e3, "iters": info.outer_iters, "relres_true": info.relres_true}
+    out["timing"] = "sstep_info.ms_solve (host wall time of one solve, device buffers) after a warm-up"
+    return out
+
+
 def run_adjoint(N, dev, sstep, I, torch):
     """Differentiated solve: Q1 diffusion on N^3 interior vertices with kappa = exp(theta),
     theta ~ N(0, 0.5^2) iid per cell (seed 0), b = 1, loss = ||x - x_target||^2 with x_target
@@ -573,6 +621,7 @@ def main():
     batch = run_batch(args.batch, dev, sstep, I, torch) if args.batch else None
     q1 = run_q1(args.q1, dev, sstep, I, torch) if args.q1 > 0 else None
     adjoint = run_adjoint(args.adjoint, dev, sstep, I, torch) if args.adjoint > 0 else None
+    hpcg = run_hpcg27(args.hpcg, dev, sstep, torch) if args.hpcg > 0 else None
 
     # ---- roofline of each kernel from the phase times
     work = kernel_work(args.s, n)
@@ -632,6 +681,7 @@ def main():
         "batched": batch,
         "q1_diffusion": q1,
         "differentiated": adjoint,
+        "poisson27_unit_rhs": hpcg,
         "e2e": {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(info.launches),

@@ -207,6 +207,17 @@ SSTEP_API sstep_status sstep_amg_level(sstep_handle h, int l, int64_t* n, int64_
  * distinct), ordered on the handle's stream and finished on return. */
 SSTEP_API sstep_status sstep_amg_apply(sstep_handle h, const double* b, double* x);
 
+/* Reduced-solve diagnostics of the last solve (Section 3.3 experiments): for every outer
+ * iteration k < *count, eta_a[k] = ||Q_k^T r^(k) - W_k alpha_k||_2 / ||Q_k^T r^(k)||_2 and, for
+ * k < *count - 1, eta_b[k] = ||-Q_k^T AZ_{k+1} - W_k beta_k||_F / ||Q_k^T AZ_{k+1}||_F; W receives
+ * W_k (s x s column-major, one after another) for k < *countw <= min(maxw, 64).  HOST arrays
+ * of maxlen (eta_a, eta_b) and maxw * s * s (W) doubles; any output may be NULL.  Recorded on
+ * the device by the reduced-solve step at no extra pass over the vectors.  *count = 0 for
+ * classical PCG. */
+SSTEP_API sstep_status sstep_get_diagnostics(sstep_handle h, double* eta_a, double* eta_b,
+                                             int maxlen, int* count, double* W, int maxw,
+                                             int* countw);
+
 /* Release everything the handle owns (NULL is accepted). */
 SSTEP_API sstep_status sstep_free(sstep_handle h);
 

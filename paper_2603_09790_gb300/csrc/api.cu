@@ -74,6 +74,7 @@ struct sstep_ctx {
   double *x = nullptr, *r = nullptr, *b = nullptr, *p = nullptr, *Ap = nullptr;
   double* partials = nullptr;
   double* hist = nullptr;
+  double *eta_a = nullptr, *eta_b = nullptr, *whist = nullptr;  // reduced-solve diagnostics
   Ctrl* ctrl = nullptr;
   Ctrl* hctrl = nullptr;  // pinned host mirror
   // basis info
@@ -435,6 +436,10 @@ sstep_status reset_ctrl(sstep_ctx* h) {
   c->full_gram = full_blocks(h);
   c->power_tol = h->o.power_tol;
   c->power_max = h->o.power_iters;
+  c->eta_a = h->eta_a;
+  c->eta_b = h->eta_b;
+  c->whist = h->whist;
+  c->whist_max = h->whist ? kDiagW : 0;
   CK(cudaMemcpyAsync(h->ctrl, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->st));
   return SSTEP_OK;
 }
@@ -565,7 +570,8 @@ void destroy(sstep_ctx* h) {
   for (void* p : fbufs)
     if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
-                  h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl};
+                  h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl, h->eta_a, h->eta_b,
+                  h->whist};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -695,6 +701,9 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
        (int64_t)4096});
   CKS(alloc(&h->partials, part));
   CKS(alloc(&h->hist, (int64_t)h->o.max_outer + 2));
+  CKS(alloc(&h->eta_a, (int64_t)h->o.max_outer + 2));
+  CKS(alloc(&h->eta_b, (int64_t)h->o.max_outer + 2));
+  CKS(alloc(&h->whist, (int64_t)kDiagW * s * s));
   CK(cudaMalloc(&h->ctrl, sizeof(Ctrl)));
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
   CK(cudaMallocHost(&h->hctrl, sizeof(Ctrl)));
@@ -1035,6 +1044,23 @@ sstep_status sstep_amg_apply(sstep_handle h, const double* b, double* x) {
   if (!h || !h->amg || !b || !x || b == x) return fail(SSTEP_ERR_INVALID, "bad AMG apply arguments");
   CK(amg_apply(h->amg, b, x, h->st));
   CK(cudaStreamSynchronize(h->st));
+  return SSTEP_OK;
+}
+
+sstep_status sstep_get_diagnostics(sstep_handle h, double* eta_a, double* eta_b, int maxlen,
+                                   int* count, double* W, int maxw, int* countw) {
+  g_err.clear();
+  if (!h || h->batch) return fail(SSTEP_ERR_INVALID, "not a single-system handle");
+  CK(cudaStreamSynchronize(h->st));
+  const int iters = h->o.algo == SSTEP_ALGO_PCG && !h->mixed ? 0 : h->hctrl->iters;
+  const int na = std::max(0, std::min(maxlen, iters));
+  if (na > 0 && eta_a) CK(cudaMemcpy(eta_a, h->eta_a, sizeof(double) * na, cudaMemcpyDeviceToHost));
+  if (na > 1 && eta_b) CK(cudaMemcpy(eta_b, h->eta_b, sizeof(double) * (na - 1), cudaMemcpyDeviceToHost));
+  if (count) *count = na;
+  const int nw = std::max(0, std::min({maxw, iters, kDiagW}));
+  if (nw > 0 && W)
+    CK(cudaMemcpy(W, h->whist, sizeof(double) * (size_t)nw * h->s * h->s, cudaMemcpyDeviceToHost));
+  if (countw) *countw = nw;
   return SSTEP_OK;
 }
 

@@ -60,7 +60,15 @@ struct Ctrl {
   double W[kMaxS * kMaxS];       // W_k used for alpha_k (and for beta_k)
   double sums[kMaxEntries];      // reduced Gram sums of the last reduction
   unsigned int ticket[kNumTickets];
+  // diagnostics of the reduced solves (Section 3.3 experiments), written by the Gram tails:
+  // eta_a[k] = ||b1 - W_k alpha_k|| / ||b1||, eta_b[k] = ||B2 - W_k beta_k||_F / ||B2||_F,
+  // whist[k] = W_k for k < whist_max (s x s column-major each)
+  double* eta_a;
+  double* eta_b;
+  double* whist;
+  int whist_max;
 };
+constexpr int kDiagW = 64;  // outer iterations whose W_k is kept
 
 // ---------------------------------------------------------------- operator descriptors
 

@@ -144,6 +144,34 @@ struct OneSyncIdx {
   __host__ __device__ int count() const { return g6(L.s); }
 };
 
+// Relative residual of a reduced solve, ||B - W X|| / ||B|| (Frobenius over nrhs columns),
+// one thread (Section 3.3: eta_alpha, eta_beta).
+__device__ double reduced_relres(int s, const double* W, const double* B, const double* X, int nrhs) {
+  double num = 0.0, den = 0.0;
+  for (int c = 0; c < nrhs; ++c)
+    for (int i = 0; i < s; ++i) {
+      double v = B[i + c * s];
+      for (int j = 0; j < s; ++j) v = fma(-W[i + j * s], X[j + c * s], v);
+      num = fma(v, v, num);
+      den = fma(B[i + c * s], B[i + c * s], den);
+    }
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+// Records eta_alpha for alpha_k (k = updates so far) and W_k.
+__device__ void record_alpha(Ctrl* c, int s, const double* W, const double* b1, const double* a) {
+  const int k = c->iters;
+  if (c->eta_a && k <= c->max_iters) c->eta_a[k] = reduced_relres(s, W, b1, a, 1);
+  if (c->whist && k < c->whist_max)
+    for (int e = 0; e < s * s; ++e) c->whist[(size_t)k * s * s + e] = W[e];
+}
+
+// Records eta_beta for beta_k, computed after update k + 1.
+__device__ void record_beta(Ctrl* c, int s, const double* W, const double* B, const double* X) {
+  const int k = c->iters - 1;
+  if (c->eta_b && k >= 0 && k <= c->max_iters) c->eta_b[k] = reduced_relres(s, W, B, X, s);
+}
+
 // The tail: executed by the last CTA after the reduction, with the sums in shared memory.
 __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
   const int s = c->s, nu = c->nu, solver = c->solver;
@@ -171,6 +199,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
     if (ok) {
       for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = X[i];
       for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
+      if (tid == 0) record_alpha(c, s, W, b1, X);
     }
   } else if (mode == GM_LITERAL_B2) {
     // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (lines 12-13)
@@ -180,8 +209,10 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
     }
     __syncthreads();
     ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
-    if (ok)
+    if (ok) {
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
+      if (tid == 0) record_beta(c, s, W, Bm, X);
+    }
   } else if (mode == GM_ONESYNC) {
     const OneSyncIdx I{L};
     for (int e = tid; e < s * s; e += blockDim.x) {
@@ -197,6 +228,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
     ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
     if (ok) {
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
+      if (tid == 0) record_beta(c, s, W, Bm, X);
       // T = G1 beta
       for (int e = tid; e < s * s; e += blockDim.x) {
         const int i = e % s, j = e / s;
@@ -230,6 +262,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
       if (ok) {
         for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = T[i];
         for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
+        if (tid == 0) record_alpha(c, s, W, b1, T);
       }
     }
   }

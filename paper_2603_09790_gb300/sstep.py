@@ -96,6 +96,7 @@ def load():
         "sstep_amg_levels": (I, [P, P]),
         "sstep_amg_level": (I, [P, I, P, P, P, P, P, P]),
         "sstep_amg_apply": (I, [P, P, P]),
+        "sstep_get_diagnostics": (I, [P, P, P, I, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -319,6 +320,19 @@ class Solver:
     def amg_apply(self, b, x):
         """x = M^{-1} b (one V-cycle) on device tensors."""
         _check(load().sstep_amg_apply(self._h, _ptr(b), _ptr(x)))
+
+    def get_diagnostics(self):
+        """eta_alpha, eta_beta per outer iteration and the first W_k of the last solve."""
+        m = self.max_outer + 2
+        ea, eb = np.zeros(m), np.zeros(m)
+        W = np.zeros((64, self.s, self.s))
+        cnt, cw = C.c_int(), C.c_int()
+        _check(load().sstep_get_diagnostics(self._h, ea.ctypes.data, eb.ctypes.data, m, C.byref(cnt),
+                                            W.ctypes.data, 64, C.byref(cw)))
+        n = cnt.value
+        # W_k is column-major: W[k][j, i] holds entry (i, j)
+        return dict(eta_a=ea[:n].copy(), eta_b=eb[:max(n - 1, 0)].copy(),
+                    W=np.transpose(W[:cw.value], (0, 2, 1)).copy())
 
     def get_batch_config(self):
         """Batched handle: the configuration in use (autotuned where it was left open)."""
