@@ -249,23 +249,37 @@ __device__ void mpk(cg::cluster_group& cl, const BSys& sy, const double* r, T* Z
     const double c1 = q == 1 ? sy.ca : 2.0 * sy.ca;
     const T a1 = (T)(c1 * sy.d), c2 = (T)(q == 1 ? sy.cs : 2.0 * sy.cs);
     const T* u = Z + (q - 1) * ld;  // z_q (q >= 2; column q-1)
-    for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
-      int ix, iy, iz;
-      coords(p, sy.nx, sy.ny, ix, iy, iz);
-      T y, uc;
-      if (q == 1) {  // uniform M^{-1}: A (d r) = d (A r)
-        uc = (T)r[p];
-        y = stencil7<T>(r, p, ix, iy, iz, sy, wc, wo, uc) * d;
-        uc *= d;
-        Z[p] = uc;
-      } else {
-        uc = u[p];
-        y = stencil7<T>(u, p, ix, iy, iz, sy, wc, wo, uc);
+    // kU points per thread and trip, every load of the trip issued before the first store,
+    // so that a thread keeps several L2 round trips in flight
+    constexpr int kU = 4;
+    const int bd = blockDim.x;
+    for (int p0 = rg.lo + threadIdx.x; p0 < rg.hi; p0 += kU * bd) {
+      T y[kU], uc[kU], zp[kU];
+#pragma unroll
+      for (int k = 0; k < kU; ++k) {
+        const int p = p0 + k * bd;
+        y[k] = uc[k] = zp[k] = T(0);
+        if (p < rg.hi) {
+          int ix, iy, iz;
+          coords(p, sy.nx, sy.ny, ix, iy, iz);
+          if (q == 1) {  // uniform M^{-1}: A (d r) = d (A r)
+            uc[k] = (T)r[p];
+            y[k] = stencil7<T>(r, p, ix, iy, iz, sy, wc, wo, uc[k]) * d;
+            uc[k] *= d;
+          } else {
+            uc[k] = u[p];
+            y[k] = stencil7<T>(u, p, ix, iy, iz, sy, wc, wo, uc[k]);
+            if (q < S) zp[k] = Z[(q - 2) * ld + p];
+          }
+        }
       }
-      AZ[(q - 1) * ld + p] = y;
-      if (q < S) {
-        const T t = q > 1 ? -Z[(q - 2) * ld + p] : T(0);
-        Z[q * ld + p] = fmat<T>(a1, y, fmat<T>(-c2, uc, t));
+#pragma unroll
+      for (int k = 0; k < kU; ++k) {
+        const int p = p0 + k * bd;
+        if (p >= rg.hi) break;
+        if (q == 1) Z[p] = uc[k];
+        AZ[(q - 1) * ld + p] = y[k];
+        if (q < S) Z[q * ld + p] = fmat<T>(a1, y[k], fmat<T>(-c2, uc[k], -zp[k]));
       }
     }
   }
