@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--adjoint", type=int, default=128,
                    help="edge of the differentiated Q1 workload (theta ~ N(0, 0.5^2) per cell, unit "
                         "right-hand side); 0 skips")
+    p.add_argument("--batch-shape", default="0:0",
+                   help="'cluster:threads' of the batched launches (0: autotuned)")
     p.add_argument("--hpcg", type=int, default=200,
                    help="edge of the 27-point Poisson benchmark with unit right-hand side "
                         "(s in 4..10, eta diagnostics); 0 skips")
@@ -264,7 +266,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
-def run_batch(spec, dev, sstep, I, torch):
+def run_batch(spec, dev, sstep, I, torch, shape="0:0"):
     """Batched workload: nsys 7-point Poisson systems with edges drawn uniformly in 32..96
     (seed 0), nrhs right-hand sides each (U[-1,1), seed 1 + system), Jacobi, nu = 3, rtol 1e-8,
     solved by one persistent launch per call; against the plain FP64 form (one single-system
@@ -282,7 +284,8 @@ def run_batch(spec, dev, sstep, I, torch):
     out = {"workload": f"batch_{nsys}x{nrhs}_poisson7_edges32-96_jacobi_nu30",
            "unknowns_per_rhs": int(sum(n)), "problems": nsys * nrhs,
            "sweeps": "30 (the paper's own FGS sweep count; the batched configuration names none)"}
-    common = dict(sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0, cluster=0, block_threads=0)
+    cl, nt = (int(v) for v in shape.split(":"))
+    common = dict(sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0, cluster=cl, block_threads=nt)
 
     def zero():
         for x in xd:
@@ -628,7 +631,7 @@ def main():
             "time_over_fp64_pcg": ems[0] / float(np.mean(pms))}
         E.free()
 
-    batch = run_batch(args.batch, dev, sstep, I, torch) if args.batch else None
+    batch = run_batch(args.batch, dev, sstep, I, torch, args.batch_shape) if args.batch else None
     q1 = run_q1(args.q1, dev, sstep, I, torch) if args.q1 > 0 else None
     adjoint = run_adjoint(args.adjoint, dev, sstep, I, torch) if args.adjoint > 0 else None
     hpcg = run_hpcg27(args.hpcg, dev, sstep, torch) if args.hpcg > 0 else None

@@ -790,15 +790,15 @@ std::vector<int> sys_order(const BatchCtx* b) {
   return ord;
 }
 
-// Time one configuration to convergence on a trial batch: one seeded right-hand side per
-// system, x0 = 0, the handle's own rtol, sweeps and iteration cap.
-sstep_status trial(BatchCtx* b, int s, int C, int NT, double* ms_out) {
+// Time one configuration on a trial batch of nrhs seeded right-hand sides per system, x0 = 0:
+// to convergence with the handle's own rtol and cap (fixed_outer = 0), or for exactly
+// fixed_outer outer iterations (rtol 0).
+sstep_status trial(BatchCtx* b, int s, int C, int NT, int nrhs, int fixed_outer, double* ms_out) {
   *ms_out = -1.0;
   KernelFn fn = pick_kernel(s, b->mixed, NT);
   if (!fn) return SSTEP_OK;
   const int nc = max_clusters(fn, C, NT);
   if (nc < 1) return SSTEP_OK;
-  const int nrhs = 1;  // one seeded right-hand side per system
   int64_t total = 0;
   for (const BSys& y : b->hsys) total += y.n;
   const int nprob = b->nsys * nrhs;
@@ -854,6 +854,10 @@ sstep_status trial(BatchCtx* b, int s, int C, int NT, double* ms_out) {
     }
     BArgs a = base_args(b);
     a.rr_period = b->rr_opt > 0 ? b->rr_opt : s;
+    if (fixed_outer > 0) {
+      a.rtol = 0.0;
+      a.max_outer = fixed_outer;
+    }
     a.prob = dp;
     a.res = dr;
     a.nprob = nprob;
@@ -907,38 +911,47 @@ sstep_status autotune(BatchCtx* b, int s_fixed, int c_fixed, int t_fixed) {
     }
   }
   const double t0 = wall_ms();
-  // Two stages: the step size at one launch shape (it decides the iteration counts), then the
-  // launch shape (CTAs per cluster, threads per CTA) at that step size.
+  // Two stages.  (1) The step size, at one launch shape, timed to convergence on one
+  // right-hand side per system (s decides the iteration counts).  (2) The launch shape (CTAs
+  // per cluster, threads per CTA) at that step size, timed over a fixed number of outer
+  // iterations on enough problems to fill every candidate's resident clusters a few times
+  // (the shape decides how the problems spread over the SMs, not the iteration counts).
   double best = -1.0;
   Choice ch;
-  auto run = [&](int s, int c, int t) -> sstep_status {
-    double ms;
-    sstep_status st = trial(b, s, c, t, &ms);
-    if (st == SSTEP_OK && ms > 0.0 && (best < 0.0 || ms < best)) {
-      best = ms;
-      ch = Choice{s, c, t};
-    }
-    return st;
-  };
   const int c0 = c_fixed ? c_fixed : 4, t0s = t_fixed ? t_fixed : 256;
+  int s1 = s_fixed;
   if (!s_fixed) {
+    double b1 = -1.0;
     for (int s : {2, 4, 8}) {
-      sstep_status st = run(s, c0, t0s);
+      double ms;
+      sstep_status st = trial(b, s, c0, t0s, 1, 0, &ms);
       if (st != SSTEP_OK) return st;
+      if (ms > 0.0 && (b1 < 0.0 || ms < b1)) {
+        b1 = ms;
+        s1 = s;
+      }
     }
-  } else {
-    sstep_status st = run(s_fixed, c0, t0s);
-    if (st != SSTEP_OK) return st;
+    if (b1 < 0.0) return bfail(SSTEP_ERR_UNSUPPORTED, "no launchable batched configuration");
   }
-  if (best > 0.0) {
-    const int s1 = ch.s;
-    std::vector<int> cs = c_fixed ? std::vector<int>{c_fixed} : std::vector<int>{2, 4, 8, 16};
-    std::vector<int> ts = t_fixed ? std::vector<int>{t_fixed} : std::vector<int>{256, 512};
+  std::vector<int> cs = c_fixed ? std::vector<int>{c_fixed} : std::vector<int>{2, 4, 8, 16};
+  std::vector<int> ts = t_fixed ? std::vector<int>{t_fixed} : std::vector<int>{256, 512};
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
+  const int want = std::max(b->nsys, 2 * std::max(nsm, 1));  // ~4x the resident clusters of C = 2
+  const int nrhs2 = std::min(8, (want + b->nsys - 1) / b->nsys);
+  if (cs.size() * ts.size() == 1) {
+    ch = Choice{s1, cs[0], ts[0]};
+    best = 1.0;
+  } else {
     for (int c : cs)
       for (int t : ts) {
-        if (c == c0 && t == t0s) continue;
-        sstep_status st = run(s1, c, t);
+        double ms;
+        sstep_status st = trial(b, s1, c, t, nrhs2, 8, &ms);
         if (st != SSTEP_OK) return st;
+        if (ms > 0.0 && (best < 0.0 || ms < best)) {
+          best = ms;
+          ch = Choice{s1, c, t};
+        }
       }
   }
   if (best < 0.0) return bfail(SSTEP_ERR_UNSUPPORTED, "no launchable batched configuration");
