@@ -13,9 +13,10 @@
 // another CTA owns are read through L2 (ld.global.cg) after the barrier that follows their
 // writes.
 //
-// The basis is FP64 or FP32 (FP32_RR): with FP32 the Gram sums are accumulated in double-float
-// on the FP32 pipe, x and r stay FP64, and r = b - A x is recomputed in FP64 every rr_period
-// outer iterations (residual replacement), as in the single-system FP32 path.
+// The basis is FP64 or FP32 (FP32_RR): with FP32 the Gram sums and the x, r increments are
+// double-float on the FP32 pipe (x = x_fp64 + (xh + xl), r = rh + rl), and every rr_period outer
+// iterations x is folded and r = b - A x recomputed in FP64 (residual replacement), as in the
+// single-system FP32 path.
 //
 // The paper solves one system at a time (Section 5); batching and the autotuner over (s,
 // cluster size, threads per CTA) are this library's additions.
@@ -214,11 +215,11 @@ __device__ __forceinline__ Range my_range(int n, int C, int rank) {
   return Range{lo, min(n, lo + chunk)};
 }
 
-// sum_p (b - A x)_p^2 over this CTA's points; writes r when r != nullptr (FP64 throughout).
-// Also sum b_p^2 into v[1] when NV == 2.
+// sum_p (b - A x)_p^2 over this CTA's points in FP64; stores r (FP64) when r != nullptr, or
+// r split into FP32 (hi, lo) when rh != nullptr.  Also sum b_p^2 into v[1] when NV == 2.
 template <int NV>
 __device__ __forceinline__ void residual(const BSys& sy, const double* b, const double* x, double* r,
-                                        Range rg, double (&v)[NV]) {
+                                        float* rh, float* rl, Range rg, double (&v)[NV]) {
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = 0.0;
   for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
@@ -228,16 +229,31 @@ __device__ __forceinline__ void residual(const BSys& sy, const double* b, const 
     const double bi = __ldg(b + p);
     const double ri = bi - y;
     if (r) r[p] = ri;
+    if (rh) {
+      const float h = __double2float_rn(ri);
+      rh[p] = h;
+      rl[p] = __double2float_rn(ri - (double)h);
+    }
     v[0] = fma(ri, ri, v[0]);
     if constexpr (NV == 2) v[1] = fma(bi, bi, v[1]);
   }
 }
 
+// FP32 form: x += xh + xl in FP64 and the increments restart from 0 (own points).
+__device__ __forceinline__ void fold_x(double* x, float* xh, float* xl, Range rg) {
+  for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
+    x[p] += (double)xh[p] + (double)xl[p];
+    xh[p] = 0.0f;
+    xl[p] = 0.0f;
+  }
+}
+
 // Algorithm 2: Z = [z_1 .. z_S], AZ = [A z_1 .. A z_S] from r, with z_1 = M^{-1} r and
 // z_{q+1} = 2 c_alpha M^{-1} A z_q - 2 c_sigma z_q - z_{q-1} (first step c_alpha, c_sigma).
-// A cluster barrier precedes every step after the first (neighbours of z_q).
-template <int S, typename T>
-__device__ void mpk(cg::cluster_group& cl, const BSys& sy, const double* r, T* Z, T* AZ,
+// A cluster barrier precedes every step after the first (neighbours of z_q).  R: the storage
+// type of r (FP64, or the FP32 high part of r in the FP32 form).
+template <int S, typename T, typename R>
+__device__ void mpk(cg::cluster_group& cl, const BSys& sy, const R* r, T* Z, T* AZ,
                     int64_t ld, Range rg) {
   const T d = (T)sy.d, wc = (T)sy.wc, wo = (T)sy.wo;
 #pragma unroll 1
@@ -285,12 +301,20 @@ __device__ void mpk(cg::cluster_group& cl, const BSys& sy, const double* r, T* Z
   }
 }
 
+// x and r of one problem: FP64 x and r, or (FP32 form) x = x_fp64 + (xh + xl) with the
+// increments in FP32 (hi, lo) pairs and r = rh + rl, between residual replacements.
+struct XR {
+  double* x;
+  double* r;
+  float *rh, *rl, *xh, *xl;
+};
+
 // Lines 7-9: x += Q alpha, r -= AQ alpha, returns ||r||^2 (cluster sum).
 template <int S, typename T>
 __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q, const T* AQ,
-                            double* x, double* r, int64_t ld, Range rg) {
-  double v[1] = {0.0};
+                            const XR& v, int64_t ld, Range rg) {
   if constexpr (std::is_same<T, double>::value) {
+    double acc[1] = {0.0};
     double al[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) al[j] = sh.alpha[j];
@@ -301,35 +325,47 @@ __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T
         dx = fma(Q[j * ld + p], al[j], dx);
         dr = fma(AQ[j * ld + p], al[j], dr);
       }
-      x[p] += dx;
-      const double ri = r[p] - dr;
-      r[p] = ri;
-      v[0] = fma(ri, ri, v[0]);
+      v.x[p] += dx;
+      const double ri = v.r[p] - dr;
+      v.r[p] = ri;
+      acc[0] = fma(ri, ri, acc[0]);
     }
-  } else {
+    csum<S, 1>(cl, acc, sh, par);
+  } else {  // all on the FP32 pipe, double-float as in the single-system FP32 path
     float ah[S], al[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       ah[j] = __double2float_rn(sh.alpha[j]);
       al[j] = __double2float_rn(sh.alpha[j] - (double)ah[j]);
     }
+    float rrh[1] = {0.0f}, rrl[1] = {0.0f};
     for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
+      float q[S], aq[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q[j] = Q[j * ld + p];
+        aq[j] = AQ[j * ld + p];
+      }
+      float xh = v.xh[p], xl = v.xl[p], rh = v.rh[p], rl = v.rl[p];
       float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const float q = Q[j * ld + p], aq = AQ[j * ld + p];
-        df_acc_prod(dxh, dxl, q, ah[j]);
-        dxl = fmaf(q, al[j], dxl);
-        df_acc_prod(drh, drl, aq, ah[j]);
-        drl = fmaf(aq, al[j], drl);
+        df_acc_prod(dxh, dxl, q[j], ah[j]);
+        dxl = fmaf(q[j], al[j], dxl);
+        df_acc_prod(drh, drl, aq[j], ah[j]);
+        drl = fmaf(aq[j], al[j], drl);
       }
-      x[p] += (double)dxh + (double)dxl;
-      const double ri = r[p] - ((double)drh + (double)drl);
-      r[p] = ri;
-      v[0] = fma(ri, ri, v[0]);
+      df_add(xh, xl, dxh, dxl);
+      df_add(rh, rl, -drh, -drl);
+      v.xh[p] = xh;
+      v.xl[p] = xl;
+      v.rh[p] = rh;
+      v.rl[p] = rl;
+      df_acc_prod(rrh[0], rrl[0], rh, rh);
+      rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
     }
+    csum_df<S, 1>(cl, rrh, rrl, sh, par);
   }
-  csum<S, 1>(cl, v, sh, par);
   return sh.sums[0];
 }
 
@@ -383,7 +419,7 @@ __device__ bool b2_beta(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q,
 // with lines 5-6 (W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)).  False on breakdown.
 template <int S, typename T, bool FIRST>
 __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* AZn, const T* Qo,
-                         const T* AQo, const double* r, int nu, int64_t ld, Range rg) {
+                         const T* AQo, const XR& v, int nu, int64_t ld, Range rg) {
   constexpr int K = S * S + S;
   if constexpr (std::is_same<T, double>::value) {
     double acc[K];
@@ -418,7 +454,7 @@ __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* 
           AZn[j * ld + p] = va;
         }
       }
-      const double rp = r[p];
+      const double rp = v.r[p];
 #pragma unroll
       for (int i = 0; i < S; ++i) {
 #pragma unroll
@@ -460,8 +496,7 @@ __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* 
           AZn[j * ld + p] = va;
         }
       }
-      const double rp = r[p];
-      const float rh = __double2float_rn(rp), rl = __double2float_rn(rp - (double)rh);
+      const float rh = v.rh[p], rl = v.rl[p];
 #pragma unroll
       for (int i = 0; i < S; ++i) {
 #pragma unroll
@@ -488,19 +523,42 @@ __device__ __forceinline__ int stop_rule(double rr, double tol2, int iters, int 
 // One problem, start to finish, by the whole cluster.
 template <int S, typename T>
 __device__ void solve_one(const BArgs& a, cg::cluster_group& cl, BSh<S>& sh, int& par, int pi,
-                          double* r, T* blk) {
+                          char* slot) {
   const BProb pr = a.prob[pi];
   const BSys sy = a.sys[pr.sys];
   const Range rg = my_range(sy.n, (int)cl.num_blocks(), (int)cl.block_rank());
   const int64_t ld = a.ld;
   constexpr bool kMixed = std::is_same<T, float>::value;
+  // slot: FP64 form [r | blocks]; FP32 form [rh | rl | xh | xl | blocks]
+  XR v{pr.x, nullptr, nullptr, nullptr, nullptr, nullptr};
+  T* blk;
+  if constexpr (kMixed) {
+    v.rh = (float*)slot;
+    v.rl = v.rh + ld;
+    v.xh = v.rl + ld;
+    v.xl = v.xh + ld;
+    blk = (T*)(v.xl + ld);
+  } else {
+    v.r = (double*)slot;
+    blk = (T*)(v.r + ld);
+  }
   // pair k of blocks: Z = blk + 2kS ld, AZ = blk + (2k+1) S ld
   auto Zp = [&](int k) { return blk + (size_t)(2 * k) * S * ld; };
   auto AZp = [&](int k) { return blk + (size_t)(2 * k + 1) * S * ld; };
+  auto run_mpk = [&](T* Z, T* AZ) {
+    if constexpr (kMixed) mpk<S, T, float>(cl, sy, v.rh, Z, AZ, ld, rg);
+    else mpk<S, T, double>(cl, sy, v.r, Z, AZ, ld, rg);
+  };
+  auto barrier = [&]() {
+    __threadfence();
+    cl.sync();
+  };
 
   // ---- line 1: r = b - A x0; ||b||^2
   double v2[2];
-  residual<2>(sy, pr.b, pr.x, r, rg, v2);
+  residual<2>(sy, pr.b, pr.x, v.r, v.rh, v.rl, rg, v2);
+  if constexpr (kMixed)
+    for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) v.xh[p] = v.xl[p] = 0.0f;
   csum<S, 2>(cl, v2, sh, par);
   double rr = sh.sums[0];
   const double nb2 = sh.sums[1];
@@ -517,44 +575,51 @@ __device__ void solve_one(const BArgs& a, cg::cluster_group& cl, BSh<S>& sh, int
   }
   if (status < 0) {
     int qp = 0;  // the pair holding Q, AQ
-    mpk<S, T>(cl, sy, r, Zp(0), AZp(0), ld, rg);
+    run_mpk(Zp(0), AZp(0));
     // k = 0: Q_0 = Z_0 (line 3), W, b1, alpha (lines 5-6)
-    if (!upd_gram<S, T, true>(cl, sh, par, Zp(0), AZp(0), nullptr, nullptr, r, a.nu, ld, rg))
+    if (!upd_gram<S, T, true>(cl, sh, par, Zp(0), AZp(0), nullptr, nullptr, v, a.nu, ld, rg))
       status = SSTEP_ERR_BREAKDOWN;
     while (status < 0) {
-      rr = update_xr<S, T>(cl, sh, par, Zp(qp), AZp(qp), pr.x, r, ld, rg);  // lines 7-8
+      rr = update_xr<S, T>(cl, sh, par, Zp(qp), AZp(qp), v, ld, rg);  // lines 7-8
       ++iters;
-      status = stop_rule(rr, tol2, iters, a.max_outer);                     // line 9
-      if (kMixed && status < 0 && iters % a.rr_period == 0) {
-        // residual replacement: r = b - A x in FP64 (x's neighbours were written before the
-        // barrier of the last reduction)
-        double v1[1];
-        residual<1>(sy, pr.b, pr.x, r, rg, v1);
-        csum<S, 1>(cl, v1, sh, par);
-        rr = sh.sums[0];
-        if (!(rr == rr) || rr > 1.79e308) status = SSTEP_ERR_NONFINITE;
-        else if (rr <= tol2) status = SSTEP_OK;
+      status = stop_rule(rr, tol2, iters, a.max_outer);               // line 9
+      if constexpr (kMixed) {
+        if (status < 0 && iters % a.rr_period == 0) {
+          // residual replacement: x folded to FP64, then r = b - A x in FP64
+          fold_x(pr.x, v.xh, v.xl, rg);
+          barrier();
+          double v1[1];
+          residual<1>(sy, pr.b, pr.x, nullptr, v.rh, v.rl, rg, v1);
+          csum<S, 1>(cl, v1, sh, par);
+          rr = sh.sums[0];
+          if (!(rr == rr) || rr > 1.79e308) status = SSTEP_ERR_NONFINITE;
+          else if (rr <= tol2) status = SSTEP_OK;
+        }
       }
       if (status >= 0) break;
       const int zp = qp ^ 1;
-      mpk<S, T>(cl, sy, r, Zp(zp), AZp(zp), ld, rg);                     // line 10
-      if (!b2_beta<S, T>(cl, sh, par, Zp(qp), AZp(zp), a.nu, ld, rg)) {   // lines 12-13
+      run_mpk(Zp(zp), AZp(zp));                                         // line 10
+      if (!b2_beta<S, T>(cl, sh, par, Zp(qp), AZp(zp), a.nu, ld, rg)) {  // lines 12-13
         status = SSTEP_ERR_BREAKDOWN;
         break;
       }
       // line 15 then lines 5-6 of the next iteration
-      if (!upd_gram<S, T, false>(cl, sh, par, Zp(zp), AZp(zp), Zp(qp), AZp(qp), r, a.nu, ld, rg)) {
+      if (!upd_gram<S, T, false>(cl, sh, par, Zp(zp), AZp(zp), Zp(qp), AZp(qp), v, a.nu, ld, rg)) {
         status = SSTEP_ERR_BREAKDOWN;
         break;
       }
       qp = zp;
     }
   }
-  // true residual at exit (x's neighbours were written before the last reduction's barrier)
+  if constexpr (kMixed) {
+    fold_x(pr.x, v.xh, v.xl, rg);
+    barrier();
+  }
+  // true residual at exit (x's neighbours were written before the last barrier)
   double rt = rr;
   if (nb2 > 0.0 && status != SSTEP_ERR_NONFINITE) {
     double v1[1];
-    residual<1>(sy, pr.b, pr.x, nullptr, rg, v1);
+    residual<1>(sy, pr.b, pr.x, nullptr, nullptr, nullptr, rg, v1);
     csum<S, 1>(cl, v1, sh, par);
     rt = sh.sums[0];
   }
@@ -576,8 +641,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_solve(BArgs a) {
   __shared__ BSh<S> sh;
   const int C = (int)cl.num_blocks();
   const int slot = (int)(blockIdx.x / C);
-  double* r = (double*)(a.ws + (size_t)slot * a.slot_bytes);
-  T* blk = (T*)(r + a.ld);
+  char* ws = a.ws + (size_t)slot * a.slot_bytes;
   int par = 0;
   for (;;) {
     if (cl.block_rank() == 0 && threadIdx.x == 0) sh.prob = atomicAdd(a.queue, 1);
@@ -585,7 +649,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_solve(BArgs a) {
     const int pi = *cl.map_shared_rank(&sh.prob, 0);
     cl.sync();  // nobody leaves (or overwrites sh.prob) before every CTA has read it
     if (pi >= a.nprob) break;
-    solve_one<S, T>(a, cl, sh, par, pi, r, blk);
+    solve_one<S, T>(a, cl, sh, par, pi, ws);
   }
 }
 
@@ -724,8 +788,10 @@ sstep_status bfail(sstep_status st, const std::string& msg) {
   } while (0)
 
 size_t slot_bytes_for(int s, bool mixed, int64_t ld) {
+  // FP64 form: r and 4s basis vectors; FP32 form: rh, rl, xh, xl and 4s basis vectors
   const size_t el = mixed ? sizeof(float) : sizeof(double);
-  size_t b = sizeof(double) * (size_t)ld + el * (size_t)(4 * s) * (size_t)ld;
+  size_t b = (mixed ? 4 * sizeof(float) : sizeof(double)) * (size_t)ld +
+             el * (size_t)(4 * s) * (size_t)ld;
   b = std::max(b, sizeof(double) * 2 * (size_t)ld);  // power method: two FP64 vectors
   return (b + 255) / 256 * 256;
 }
