@@ -625,10 +625,25 @@ def main():
                          precision=prec, **common)
         ems, einfos = timed_solves(E, xe, 1, 1)
         err = float(torch.linalg.norm(xe - x_fp64) / torch.linalg.norm(x_fp64))
-        extra[f"s{s_}_nu{nu_}" + ("" if prec == "fp64" else "_" + prec)] = {
+        key = f"s{s_}_nu{nu_}" + ("" if prec == "fp64" else "_" + prec)
+        extra[key] = {
             "s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
             "relres_true": einfos[0].relres_true, "rel_diff_vs_fp64_solution": err,
             "time_over_fp64_pcg": ems[0] / float(np.mean(pms))}
+        if prec == "fp32_rr":  # the FP32 kernels are HBM-bound: GB/s per launch
+            E.profile(bd, iters=2)
+            fph = E.profile(bd, iters=5)
+            F = 4.0 * n
+            fb = {"mpk_step": (16 * (s_ - 1) + 8) * F / s_, "gram_b2": 2 * s_ * F,
+                  "update_w": (6 * s_ + 2) * F, "update_xr": (2 * s_ + 8) * F}
+            fms = {"mpk_step": fph[0] / s_, "gram_b2": fph[1], "update_w": fph[2], "update_xr": fph[3]}
+            hbm_, _ = hbm_peak()
+            extra[key]["per_kernel"] = {
+                k: {"ms_per_launch": fms[k], "GB_s": fb[k] / (fms[k] * 1e-3) / 1e9,
+                    "hbm_frac": fb[k] / (fms[k] * 1e-3) / 1e9 / hbm_} for k in fb}
+            extra[key]["ms_per_outer"] = float(sum(fph[:4]))
+            extra[key]["hbm_frac_whole_outer"] = sum(fb[k] * (s_ if k == "mpk_step" else 1)
+                                                     for k in fb) / (sum(fph[:4]) * 1e-3) / 1e9 / hbm_
         E.free()
 
     batch = run_batch(args.batch, dev, sstep, I, torch, args.batch_shape) if args.batch else None
