@@ -634,7 +634,7 @@ def main():
             E.profile(bd, iters=2)
             fph = E.profile(bd, iters=5)
             F = 4.0 * n
-            fb = {"mpk_step": (16 * (s_ - 1) + 8) * F / s_, "gram_b2": 2 * s_ * F,
+            fb = {"mpk_step": (4 * (s_ - 1) + 2) * F / s_, "gram_b2": 2 * s_ * F,
                   "update_w": (6 * s_ + 2) * F, "update_xr": (2 * s_ + 8) * F}
             fms = {"mpk_step": fph[0] / s_, "gram_b2": fph[1], "update_w": fph[2], "update_xr": fph[3]}
             hbm_, _ = hbm_peak()

@@ -592,9 +592,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_b2f(MixedArgs a) {
   float hi[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-  const int64_t ld = a.ld;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // four consecutive points per thread and trip (16-byte loads: more bytes in flight)
+  const int64_t n4 = a.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 q[S], z[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) q[i] = __ldg(reinterpret_cast<const float4*>(a.Q + i * ld) + v);
+#pragma unroll
+    for (int j = 0; j < S; ++j) z[j] = __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].x, z[j].x);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].y, z[j].y);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].z, z[j].z);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].w, z[j].w);
+      }
+  }
+  for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
     float q[S], z[S];
 #pragma unroll
     for (int i = 0; i < S; ++i) q[i] = __ldg(a.Q + i * ld + p);
