@@ -708,45 +708,65 @@ __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   float rrh[1] = {0.0f}, rrl[1] = {0.0f};
   const int64_t ld = a.ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // two points per trip, every load issued before the arithmetic (memory-level parallelism)
-  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < a.n; p0 += 2 * stride) {
-    const int64_t pp[2] = {p0, p0 + stride};
-    const bool has[2] = {true, p0 + stride < a.n};
-    float q[2][S], aq[2][S], xh[2], xl[2], rh[2], rl[2];
+  // one point: x += Q alpha, r -= AQ alpha in double-float, ||r||^2 accumulated
+  auto point = [&](const float (&q)[S], const float (&aq)[S], float& xh, float& xl, float& rh,
+                   float& rl) {
+    float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int64_t p = has[u] ? pp[u] : p0;
-#pragma unroll
-      for (int j = 0; j < S; ++j) {
-        q[u][j] = __ldg(a.Q + j * ld + p);
-        aq[u][j] = __ldg(a.AQ + j * ld + p);
-      }
-      xh[u] = a.xhi[p];
-      xl[u] = a.xlo[p];
-      rh[u] = a.rhi[p];
-      rl[u] = a.rlo[p];
+    for (int j = 0; j < S; ++j) {
+      df_acc_prod(dxh, dxl, q[j], ah[j]);
+      dxl = fmaf(q[j], al[j], dxl);
+      df_acc_prod(drh, drl, aq[j], ah[j]);
+      drl = fmaf(aq[j], al[j], drl);
     }
+    df_add(xh, xl, dxh, dxl);
+    df_add(rh, rl, -drh, -drl);
+    df_acc_prod(rrh[0], rrl[0], rh, rh);
+    rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
+  };
+  // four consecutive points per thread and trip with 16-byte loads and stores (ld and the
+  // vector lengths are multiples of 64, so every column is 16-byte aligned)
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n4 = a.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 q4[S], aq4[S];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      if (!has[u]) continue;
-      const int64_t p = pp[u];
-      float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
-#pragma unroll
-      for (int j = 0; j < S; ++j) {
-        df_acc_prod(dxh, dxl, q[u][j], ah[j]);
-        dxl = fmaf(q[u][j], al[j], dxl);
-        df_acc_prod(drh, drl, aq[u][j], ah[j]);
-        drl = fmaf(aq[u][j], al[j], drl);
-      }
-      df_add(xh[u], xl[u], dxh, dxl);
-      df_add(rh[u], rl[u], -drh, -drl);
-      a.xhi[p] = xh[u];
-      a.xlo[p] = xl[u];
-      a.rhi[p] = rh[u];
-      a.rlo[p] = rl[u];
-      df_acc_prod(rrh[0], rrl[0], rh[u], rh[u]);
-      rrl[0] = fmaf(2.0f * rh[u], rl[u], rrl[0]);
+    for (int j = 0; j < S; ++j) {
+      q4[j] = __ldg(reinterpret_cast<const float4*>(a.Q + j * ld) + v);
+      aq4[j] = __ldg(reinterpret_cast<const float4*>(a.AQ + j * ld) + v);
     }
+    float4 xh = reinterpret_cast<float4*>(a.xhi)[v], xl = reinterpret_cast<float4*>(a.xlo)[v];
+    float4 rh = reinterpret_cast<float4*>(a.rhi)[v], rl = reinterpret_cast<float4*>(a.rlo)[v];
+    float q[S], aq[S];
+#define SSTEP_XR_LANE(c)                    \
+    for (int j = 0; j < S; ++j) {           \
+      q[j] = q4[j].c;                       \
+      aq[j] = aq4[j].c;                     \
+    }                                       \
+    point(q, aq, xh.c, xl.c, rh.c, rl.c);
+    SSTEP_XR_LANE(x)
+    SSTEP_XR_LANE(y)
+    SSTEP_XR_LANE(z)
+    SSTEP_XR_LANE(w)
+#undef SSTEP_XR_LANE
+    reinterpret_cast<float4*>(a.xhi)[v] = xh;
+    reinterpret_cast<float4*>(a.xlo)[v] = xl;
+    reinterpret_cast<float4*>(a.rhi)[v] = rh;
+    reinterpret_cast<float4*>(a.rlo)[v] = rl;
+  }
+  for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
+    float q[S], aq[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      q[j] = __ldg(a.Q + j * ld + p);
+      aq[j] = __ldg(a.AQ + j * ld + p);
+    }
+    float xh = a.xhi[p], xl = a.xlo[p], rh = a.rhi[p], rl = a.rlo[p];
+    point(q, aq, xh, xl, rh, rl);
+    a.xhi[p] = xh;
+    a.xlo[p] = xl;
+    a.rhi[p] = rh;
+    a.rlo[p] = rl;
   }
   if (!df_grid_sums<1>(rrh, rrl, buf, a.partials, &a.ctrl->ticket[TK_UPDATE])) return;
   if (threadIdx.x == 0) {
