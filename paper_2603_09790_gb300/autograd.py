@@ -1,8 +1,8 @@
 """Differentiable PCG-S solves: x = A(vals)^{-1} b as a torch.autograd.Function.
 
 Forward solves with the CUDA library.  Backward recomputes x (no solution is kept between the
-two passes), solves the adjoint system A^T lambda = dL/dx with the same s-step kernels (A is
-SPD, so A^T = A and the forward handle's Chebyshev interval serves), and forms
+two passes; the solver handle is), solves the adjoint system A^T lambda = dL/dx with the same
+s-step kernels and handle (A is SPD, so A^T = A), and forms
 dL/dA_ij = -lambda_i x_j on A's stored pattern with sstep_pattern_grad; dL/db = lambda.
 The paper has no differentiated form; this is the standard adjoint of a linear solve.
 """
@@ -35,22 +35,34 @@ class _SStepSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vals, b, pattern, opts):
         A = sstep.CSR(pattern.rowptr, pattern.colind, vals.detach().contiguous())
-        with sstep.Solver(A, **opts) as S:
+        S = sstep.Solver(A, **opts)
+        try:
             x = _solve(S, b)
-            bi = S.get_basis_info()
+        except Exception:
+            S.free()
+            raise
         ctx.save_for_backward(vals, b)
         ctx.pattern = pattern
-        ctx.opts = dict(opts, lambda_min=bi["lambda_min"], lambda_max=bi["lambda_max"])
+        ctx.opts = opts
+        # the handle (operator copy, preconditioner set-up, Chebyshev interval) is kept for the
+        # backward pass; x itself is not kept and is recomputed there
+        ctx.solver = S
         return x
 
     @staticmethod
     def backward(ctx, gx):
         vals, b = ctx.saved_tensors
         pattern = ctx.pattern
-        A = sstep.CSR(pattern.rowptr, pattern.colind, vals.detach().contiguous())
-        with sstep.Solver(A, **ctx.opts) as S:
-            x = _solve(S, b)
-            lam = _solve(S, gx)
+        S = ctx.solver
+        ctx.solver = None
+        if S is None:  # a second backward through the same graph: set the handle up again
+            A = sstep.CSR(pattern.rowptr, pattern.colind, vals.detach().contiguous())
+            S = sstep.Solver(A, **ctx.opts)
+        try:
+            x = _solve(S, b)             # x recomputed
+            lam = _solve(S, gx)          # A^T lambda = dL/dx (A symmetric)
+        finally:
+            S.free()
         gvals = None
         if ctx.needs_input_grad[0]:
             gvals = torch.empty_like(vals)

@@ -137,3 +137,18 @@ def test_update_values_matches_fresh_setup():
         i2 = Su.solve(b, xu)
     assert i1.outer_iters == i2.outer_iters
     assert torch.equal(xf, xu)
+
+
+def test_second_backward_sets_the_handle_up_again():
+    dims = (8, 7, 6)
+    theta0, b0, t0 = _problem(dims, 6)
+    asm = AG.Q1Assembly(dims, DEV)
+    theta = torch.from_numpy(theta0).to(DEV).requires_grad_(True)
+    b = torch.from_numpy(b0).to(DEV)
+    x = AG.solve(asm.values(torch.exp(theta)), b, asm.pattern, s=4, sweeps=30, rtol=1e-12)
+    loss = torch.sum(x * x)
+    loss.backward(retain_graph=True)
+    g1 = theta.grad.clone()
+    theta.grad = None
+    loss.backward()
+    assert torch.allclose(theta.grad, g1, rtol=1e-9, atol=1e-14 * g1.abs().max().item())
