@@ -505,6 +505,112 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args 
   }
 }
 
+// FP32 MPK step for 7-point stencils with nx a multiple of 4 and a uniform M^{-1}: each thread
+// owns four consecutive x points (16-byte loads and stores), a CTA a 64 x 16 tile of a z
+// chunk, marching in z with the planes z-1, z, z+1 in registers and plane z staged in shared
+// memory (two buffers, one barrier per plane) for the y and cross-vector x neighbours.  Four
+// points share one set of index computations, which bounded the scalar kernel.
+constexpr int TX4 = 16, TY4 = 16;  // threads: 16 float4 columns x 16 rows
+constexpr int kRow4 = 4 * TX4 + 8;  // floats per staged row: 4 pad | 64 values | 4 pad
+
+template <bool POISSON, bool FIRST>
+__global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Args e, int zc) {
+  if (e.ctrl && e.ctrl->done) return;
+  __shared__ __align__(16) float sm[2][TY4 + 2][kRow4];
+  const int tx = threadIdx.x % TX4, ty = threadIdx.x / TX4;
+  const int nx = op.nx, ny = op.ny, nz = op.nz;
+  const int x0 = (blockIdx.x * TX4 + tx) * 4, y = blockIdx.y * TY4 + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int64_t pxy = (int64_t)nx * ny;
+  const bool in = x0 < nx && y < ny;          // nx % 4 == 0: the whole vector is inside
+  const int64_t col = (int64_t)y * nx + x0;
+  const int hy = ty == 0 ? -1 : (ty == TY4 - 1 ? 1 : 0);
+  const bool hyok = hy != 0 && x0 < nx && y + hy >= 0 && y + hy < ny;
+  const int64_t hycol = col + (int64_t)hy * nx;
+  // x halos: the point left of the tile (thread tx = 0) and right of it (tx = TX4 - 1)
+  const int hx = tx == 0 ? -1 : (tx == TX4 - 1 ? 4 : 0);
+  const bool hxok = hx != 0 && y < ny && x0 + hx >= 0 && x0 + hx < nx;
+  const int64_t hxcol = col + hx;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  auto ld4 = [&](int64_t c, int zz, bool ok) -> float4 {
+    if (!ok || zz < 0 || zz >= nz) return zero4;
+    return __ldg(reinterpret_cast<const float4*>(e.u + c + (int64_t)zz * pxy));
+  };
+  auto ld1 = [&](int64_t c, int zz, bool ok) -> float {
+    if (!ok || zz < 0 || zz >= nz) return 0.0f;
+    return __ldg(e.u + c + (int64_t)zz * pxy);
+  };
+  float4 ub = ld4(col, z0 - 1, in), uc = ld4(col, z0, in), ua = ld4(col, z0 + 1, in);
+  float4 hyv = ld4(hycol, z0, hyok);
+  float hxv = ld1(hxcol, z0, hxok);
+  const float wc = e.wc, a1 = e.c1 * e.dinv_u, c2 = e.c2;
+  int set = 0;
+  for (int z = z0; z < z1; ++z) {
+    float (*P)[kRow4] = sm[set];
+    *reinterpret_cast<float4*>(&P[ty + 1][4 + 4 * tx]) = uc;
+    if (hy) *reinterpret_cast<float4*>(&P[ty + 1 + hy][4 + 4 * tx]) = hyv;
+    if (hx < 0) P[ty + 1][3] = hxv;
+    if (hx > 0) P[ty + 1][4 + 4 * TX4] = hxv;
+    // next plane's values in flight during the barrier and the arithmetic
+    const float4 nz4 = ld4(col, z + 2, in);
+    const float4 nhy = ld4(hycol, z + 1, hyok);
+    const float nhx = ld1(hxcol, z + 1, hxok);
+    __syncthreads();
+    if (in) {
+      const float4 ym = *reinterpret_cast<const float4*>(&P[ty][4 + 4 * tx]);
+      const float4 yp = *reinterpret_cast<const float4*>(&P[ty + 2][4 + 4 * tx]);
+      const float xl = P[ty + 1][3 + 4 * tx], xr = P[ty + 1][8 + 4 * tx];
+      const float xm[4] = {xl, uc.x, uc.y, uc.z}, xp[4] = {uc.y, uc.z, uc.w, xr};
+      const float c[4] = {uc.x, uc.y, uc.z, uc.w}, dn[4] = {ub.x, ub.y, ub.z, ub.w};
+      const float up[4] = {ua.x, ua.y, ua.z, ua.w};
+      const float yM[4] = {ym.x, ym.y, ym.z, ym.w}, yP[4] = {yp.x, yp.y, yp.z, yp.w};
+      float av[4], cv[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        float a;
+        if constexpr (POISSON) {
+          float s = (xm[l] + xp[l]) + (yM[l] + yP[l]);
+          s += dn[l] + up[l];
+          a = fmaf(wc, c[l], -s);
+        } else {  // weights in the order -z, -y, -x, centre, +x, +y, +z
+          a = e.w[0] * dn[l];
+          a = fmaf(e.w[1], yM[l], a);
+          a = fmaf(e.w[2], xm[l], a);
+          a = fmaf(e.w[3], c[l], a);
+          a = fmaf(e.w[4], xp[l], a);
+          a = fmaf(e.w[5], yP[l], a);
+          a = fmaf(e.w[6], up[l], a);
+        }
+        float cc = c[l];
+        if constexpr (FIRST) {  // uniform M^{-1}: A (d r) = d (A r)
+          a *= e.dinv_u;
+          cc *= e.dinv_u;
+        }
+        av[l] = a;
+        cv[l] = cc;
+      }
+      const int64_t i = (int64_t)z * pxy + col;
+      if constexpr (FIRST) *reinterpret_cast<float4*>(e.z1 + i) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+      *reinterpret_cast<float4*>(e.y + i) = make_float4(av[0], av[1], av[2], av[3]);
+      if (e.znext) {
+        float4 zp = zero4;
+        if (e.zprev) zp = __ldg(reinterpret_cast<const float4*>(e.zprev + i));
+        const float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+        float zn[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) zn[l] = fmaf(a1, av[l], fmaf(-c2, cv[l], -zpv[l]));
+        *reinterpret_cast<float4*>(e.znext + i) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+      }
+    }
+    ub = uc;
+    uc = ua;
+    ua = nz4;
+    hyv = nhy;
+    hxv = nhx;
+    set ^= 1;
+  }
+}
+
 template <bool FIRST, bool SCALE>
 __global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
   if (e.ctrl && e.ctrl->done) return;
@@ -625,6 +731,22 @@ cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st
   if (A.kind == SSTEP_MATRIX_STENCIL) {
     const StencilOp& op = A.st;
     if (op.points == 27) return cudaErrorNotSupported;  // the mixed path takes 27 points as CSR
+    if (op.points == 7 && op.nx % 4 == 0 && !scale && e.dinv == nullptr) {
+      // vector kernel: about four 256-thread CTAs per SM, z chunks of at least 8 planes
+      const int gx = (op.nx + 4 * TX4 - 1) / (4 * TX4), gy = (op.ny + TY4 - 1) / TY4;
+      int64_t gz = std::max<int64_t>(1, (int64_t)num_sms() * 4 / std::max(1, gx * gy));
+      gz = std::min<int64_t>(gz, std::max(1, op.nz / 8));
+      const int zc = (int)((op.nz + gz - 1) / gz);
+      const dim3 grid(gx, gy, (op.nz + zc - 1) / zc);
+      if (e.first) {
+        if (op.poisson) k_stencil7f4<true, true><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+        else k_stencil7f4<false, true><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+      } else {
+        if (op.poisson) k_stencil7f4<true, false><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+        else k_stencil7f4<false, false><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+      }
+      return cudaGetLastError();
+    }
     StencilGrid g = stencil_grid(op);
     const int threads = TX * TY;
 #define L7(P, POI)                                                                           \
