@@ -585,7 +585,7 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
 
 // b2 = -Q^T AZ (line 12) from FP32 blocks, then beta = FGS(W, b2) (line 13).
 template <int S>
-__global__ void __launch_bounds__(kThreads, 1) k_gram_b2f(MixedArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   if (a.ctrl->done) return;
   constexpr int K = S * S;
   __shared__ double buf[kTiledSmem];
@@ -1476,7 +1476,7 @@ cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
     k_gram_b2f<S><<<occ_grid(k_gram_b2f<S>, a.n, occ), kThreads, 0, st>>>(a); \
     return cudaGetLastError();                                             \
   }
-    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
     default: return cudaErrorNotSupported;
   }
