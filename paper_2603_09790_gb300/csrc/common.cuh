@@ -161,6 +161,35 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* NV * 32
   __syncthreads();
 }
 
+// Final step of a "last CTA to arrive" reduction with per-entry partials: for E = T * K entries
+// (T tiles of K values; entry e = tt * K + k), out[e] = sum over b < nblk of
+// partials[(tt * nblk + b) * K + k].  Every thread of the CTA works: thread idx takes entry
+// idx % E and the partials b = idx / E, idx / E + G, ... (G = blockDim / E groups); then one
+// thread per entry adds the G group sums in increasing order.  A fixed order for a given launch
+// shape, so deterministic; with a few entries it keeps many loads in flight instead of a
+// serial chain over the CTAs per entry.  E <= 1024.  Ends with __syncthreads().
+__device__ __forceinline__ void sum_partials(const double* partials, unsigned int nblk, int K,
+                                             int T, double* out) {
+  constexpr int kScratch = 1024;
+  __shared__ double scratch[kScratch];
+  const int E = K * T;
+  const int G = max(1, min((int)blockDim.x, kScratch) / E);
+  for (int idx = threadIdx.x; idx < G * E; idx += blockDim.x) {
+    const int e = idx % E, g = idx / E;
+    const double* p = partials + (size_t)(e / K) * nblk * K + (e % K);
+    double v = 0.0;
+    for (unsigned int b = g; b < nblk; b += G) v += __ldcg(p + (size_t)b * K);
+    scratch[idx] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < G; ++g) v += scratch[g * E + e];
+    out[e] = v;
+  }
+  __syncthreads();
+}
+
 // Deterministic grid reduction: every CTA contributes NV values; the last CTA to arrive sums
 // the per-CTA partials in a fixed order and returns true (result in `tot`, valid in all of
 // its threads).  No CTA waits for another: the last arriving CTA does the final step.

@@ -428,14 +428,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiled(GramTiles g) {
   if (!last) return;
   __threadfence();
   double* sums = buf;  // ne entries, then the tail's scratch
-  for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
-    const int tt = idx / K, k = idx % K;
-    const int e = g.out[tt][k];
-    if (e < 0) continue;
-    double v = 0.0;
-    for (unsigned int bx = 0; bx < gridDim.x; ++bx)
-      v += __ldcg(g.partials + ((size_t)tt * gridDim.x + bx) * K + k);
-    sums[e] = v;
+  {
+    __shared__ double tot[kMaxTiles * kTileMaxR * kTileMaxC];
+    sum_partials(g.partials, gridDim.x, K, (int)gridDim.y, tot);
+    for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
+      const int e = g.out[idx / K][idx % K];
+      if (e >= 0) sums[e] = tot[idx];
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) g.ctrl->ticket[TK_GRAM] = 0u;
@@ -527,12 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   if (!last) return;
   __threadfence();
   double* sums = buf;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = 0.0;
-    for (unsigned int bx = 0; bx < gridDim.x; ++bx) v += __ldcg(a.partials + (size_t)bx * K + k);
-    sums[k] = v;
-  }
-  __syncthreads();
+  sum_partials(a.partials, gridDim.x, K, 1, sums);
   if (threadIdx.x == 0) a.ctrl->ticket[TK_GRAM] = 0u;
   for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = sums[e];
   gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + K);
@@ -573,12 +567,7 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = 0.0;
-    for (unsigned int bx = 0; bx < gridDim.x; ++bx) v += __ldcg(partials + (size_t)bx * K + k);
-    buf[k] = v;
-  }
-  __syncthreads();
+  sum_partials(partials, gridDim.x, K, 1, buf);
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }
@@ -597,12 +586,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // four consecutive points per thread and trip (16-byte loads: more bytes in flight)
   const int64_t n4 = a.n >> 2;
+  // column pointers formed once: the loop body indexes them with v alone
+  const float4* qc[S];
+  const float4* zc[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    qc[i] = reinterpret_cast<const float4*>(a.Q + i * ld);
+    zc[i] = reinterpret_cast<const float4*>(a.AZ + i * ld);
+  }
   for (int64_t v = gid; v < n4; v += stride) {
     float4 q[S], z[S];
 #pragma unroll
-    for (int i = 0; i < S; ++i) q[i] = __ldg(reinterpret_cast<const float4*>(a.Q + i * ld) + v);
+    for (int i = 0; i < S; ++i) q[i] = __ldg(qc[i] + v);
 #pragma unroll
-    for (int j = 0; j < S; ++j) z[j] = __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+    for (int j = 0; j < S; ++j) z[j] = __ldg(zc[j] + v);
 #pragma unroll
     for (int i = 0; i < S; ++i)
 #pragma unroll
@@ -876,14 +873,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
   if (!last) return;
   __threadfence();
   double* sums = buf;
-  for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
-    const int tt = idx / K, k = idx % K;
-    const int e = g.out[tt][k];
-    if (e < 0) continue;
-    double v = 0.0;
-    for (unsigned int bx = 0; bx < gridDim.x; ++bx)
-      v += __ldcg(g.partials + ((size_t)tt * gridDim.x + bx) * K + k);
-    sums[e] = v;
+  {
+    __shared__ double tot[kMaxTiles * kTileMaxR * kTileMaxC];
+    sum_partials(g.partials, gridDim.x, K, (int)gridDim.y, tot);
+    for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
+      const int e = g.out[idx / K][idx % K];
+      if (e >= 0) sums[e] = tot[idx];
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) g.ctrl->ticket[TK_GRAM] = 0u;
