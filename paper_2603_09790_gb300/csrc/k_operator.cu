@@ -393,45 +393,36 @@ __global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
   reduce_and_finish<EPI>(e, red);
 }
 
-// G threads per row (G = 4, 8, 16).  A warp owns 32 consecutive rows and takes them 32 / G at a
-// time: lane l of a row's group reads the entries k0 + l, k0 + l + G, ... (consecutive entries
-// across the warp), the group's partial sums are added by shuffles and parked in shared
-// memory; then lane j runs the epilogue of row j, so the vector loads and stores of the
-// epilogue stay coalesced.  The loop is uniform per warp, which keeps every lane in the
-// shuffles.
+// G threads per row (G = 4, 8, 16): lane l of a row's group takes the entries k0 + l,
+// k0 + l + G, ...; the group's partial sums are added by shuffles and the group's first lane
+// runs the epilogue.  A warp covers 32 / G consecutive rows, so each load instruction reads
+// consecutive entries of the CSR arrays.  The loop is uniform per warp (rows past n have no
+// entries), which keeps every lane in the shuffles.
 template <int EPI, bool SCALE, int G>
 __global__ void __launch_bounds__(kThreads) k_csr_g(CsrOp A, EpiArgs e) {
   if (skip<EPI>(e)) return;
-  __shared__ double rows[kThreads];
   double red[2] = {0.0, 0.0};
   const double* __restrict__ u = e.u;
   const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-  double* wrow = rows + (threadIdx.x & ~31);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < A.n; base += nwarps * 32) {
-#pragma unroll
-    for (int p = 0; p < G; ++p) {
-      const int r = p * (32 / G) + lane / G;
-      const int64_t i = base + r;
-      double a = 0.0;
-      if (i < A.n) {
-        const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
-        for (int64_t k = k0 + sub; k < k1; k += G) {
-          const int32_t c = __ldg(A.colind + k);
-          double v = __ldg(u + c);
-          if constexpr (SCALE) v *= __ldg(e.M.dinv + c);
-          a = fma(__ldg(A.vals + k), v, a);
-        }
+  constexpr int kRows = 32 / G;
+  for (int64_t base = warp * kRows; base < A.n; base += nwarps * kRows) {
+    const int64_t i = base + lane / G;
+    const bool valid = i < A.n;
+    double a = 0.0;
+    if (valid) {
+      const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+      for (int64_t k = k0 + sub; k < k1; k += G) {
+        const int32_t c = __ldg(A.colind + k);
+        double v = __ldg(u + c);
+        if constexpr (SCALE) v *= __ldg(e.M.dinv + c);
+        a = fma(__ldg(A.vals + k), v, a);
       }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (sub == 0) wrow[r] = a;
     }
-    __syncwarp();
-    const int64_t i = base + lane;
-    if (i < A.n) {
-      double a = wrow[lane];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (valid && sub == 0) {
       double uc = __ldg(u + i);
       if constexpr (SCALE) uc *= __ldg(e.M.dinv + i);
       if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
@@ -440,7 +431,6 @@ __global__ void __launch_bounds__(kThreads) k_csr_g(CsrOp A, EpiArgs e) {
       }
       epilogue<EPI>(e, i, a, uc, red);
     }
-    __syncwarp();
   }
   reduce_and_finish<EPI>(e, red);
 }
@@ -667,34 +657,26 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
 template <bool FIRST, bool SCALE, int G>
 __global__ void __launch_bounds__(kThreads) k_csrf_g(CsrOp A, MpkF32Args e) {
   if (e.ctrl && e.ctrl->done) return;
-  __shared__ float rows[kThreads];
   const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-  float* wrow = rows + (threadIdx.x & ~31);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < A.n; base += nwarps * 32) {
-#pragma unroll
-    for (int p = 0; p < G; ++p) {
-      const int r = p * (32 / G) + lane / G;
-      const int64_t i = base + r;
-      float a = 0.0f;
-      if (i < A.n) {
-        const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
-        for (int64_t k = k0 + sub; k < k1; k += G) {
-          const int32_t c = __ldg(A.colind + k);
-          float v = __ldg(e.u + c);
-          if constexpr (SCALE) v *= __ldg(e.dinv + c);
-          a = fmaf(__ldg(e.valsf + k), v, a);
-        }
+  constexpr int kRows = 32 / G;
+  for (int64_t base = warp * kRows; base < A.n; base += nwarps * kRows) {
+    const int64_t i = base + lane / G;
+    const bool valid = i < A.n;
+    float a = 0.0f;
+    if (valid) {
+      const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+      for (int64_t k = k0 + sub; k < k1; k += G) {
+        const int32_t c = __ldg(A.colind + k);
+        float v = __ldg(e.u + c);
+        if constexpr (SCALE) v *= __ldg(e.dinv + c);
+        a = fmaf(__ldg(e.valsf + k), v, a);
       }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (sub == 0) wrow[r] = a;
     }
-    __syncwarp();
-    const int64_t i = base + lane;
-    if (i < A.n) {
-      float a = wrow[lane];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (valid && sub == 0) {
       float uc = __ldg(e.u + i);
       if constexpr (SCALE) uc *= __ldg(e.dinv + i);
       if constexpr (FIRST && !SCALE) {
@@ -703,7 +685,6 @@ __global__ void __launch_bounds__(kThreads) k_csrf_g(CsrOp A, MpkF32Args e) {
       }
       mpk_f32_epilogue(e, i, a, uc, FIRST);
     }
-    __syncwarp();
   }
 }
 
@@ -777,7 +758,6 @@ cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t s
 }
 
 int csr_ctas(int64_t n, int lanes = 1) {
-  // lanes > 1: a warp covers 32 rows in `lanes` passes; aim for the same warps per row block
   int64_t want = (n * std::max(1, lanes) + kThreads - 1) / kThreads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * kCsrCtasPerSm));
 }
