@@ -660,7 +660,7 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
     CK(cudaMemcpyAsync(h->rowptr, A->rowptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(h->colind, A->colind, sizeof(int32_t) * A->nnz, cudaMemcpyDefault, h->st));
     CK(cudaMemcpyAsync(h->vals, A->vals, sizeof(double) * A->nnz, cudaMemcpyDefault, h->st));
-    h->op.csr = CsrOp{A->n, h->rowptr, h->colind, h->vals, csr_lanes(A->n, A->nnz)};
+    h->op.csr = CsrOp{A->n, h->rowptr, h->colind, h->vals};
     h->nnz = A->nnz;
     {
       int* bad = nullptr;
@@ -1324,7 +1324,7 @@ sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, const int32_t*
   g_err.clear();
   if (n < 1 || !rowptr || !colind || !lam || !x || !grad_vals)
     return fail(SSTEP_ERR_INVALID, "bad pattern_grad arguments");
-  CsrOp A{n, rowptr, colind, nullptr, 1};
+  CsrOp A{n, rowptr, colind, nullptr};
   CK(launch_pattern_grad(A, lam, x, grad_vals, scale, accumulate, (cudaStream_t)stream));
   return SSTEP_OK;
 }

@@ -84,15 +84,7 @@ struct CsrOp {
   const int64_t* rowptr;
   const int32_t* colind;
   const double* vals;
-  int lanes;  // threads per row of the SpMV kernels: 1, 4, 8 or 16 (0 counts as 1)
 };
-
-// Threads per CSR row for a mean of nnz / n entries per row: enough lanes that one warp reads
-// consecutive rows' entries in few cache lines, few enough that most lanes have work.
-inline int csr_lanes(int64_t n, int64_t nnz) {
-  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-  return avg <= 2.0 ? 1 : (avg <= 12.0 ? 4 : (avg <= 40.0 ? 8 : 16));
-}
 
 // Preconditioner: dinv == nullptr means the uniform scalar dinv_u (M = I gives dinv_u = 1).
 struct Prec {

@@ -393,48 +393,6 @@ __global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
   reduce_and_finish<EPI>(e, red);
 }
 
-// G threads per row (G = 4, 8, 16): lane l of a row's group takes the entries k0 + l,
-// k0 + l + G, ...; the group's partial sums are added by shuffles and the group's first lane
-// runs the epilogue.  A warp covers 32 / G consecutive rows, so each load instruction reads
-// consecutive entries of the CSR arrays.  The loop is uniform per warp (rows past n have no
-// entries), which keeps every lane in the shuffles.
-template <int EPI, bool SCALE, int G>
-__global__ void __launch_bounds__(kThreads) k_csr_g(CsrOp A, EpiArgs e) {
-  if (skip<EPI>(e)) return;
-  double red[2] = {0.0, 0.0};
-  const double* __restrict__ u = e.u;
-  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  constexpr int kRows = 32 / G;
-  for (int64_t base = warp * kRows; base < A.n; base += nwarps * kRows) {
-    const int64_t i = base + lane / G;
-    const bool valid = i < A.n;
-    double a = 0.0;
-    if (valid) {
-      const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
-      for (int64_t k = k0 + sub; k < k1; k += G) {
-        const int32_t c = __ldg(A.colind + k);
-        double v = __ldg(u + c);
-        if constexpr (SCALE) v *= __ldg(e.M.dinv + c);
-        a = fma(__ldg(A.vals + k), v, a);
-      }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (valid && sub == 0) {
-      double uc = __ldg(u + i);
-      if constexpr (SCALE) uc *= __ldg(e.M.dinv + i);
-      if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
-        a *= e.M.dinv_u;
-        uc *= e.M.dinv_u;
-      }
-      epilogue<EPI>(e, i, a, uc, red);
-    }
-  }
-  reduce_and_finish<EPI>(e, red);
-}
-
 // ---------------------------------------------------------------- FP32 MPK step (mixed path)
 
 __device__ __forceinline__ void mpk_f32_epilogue(const MpkF32Args& e, int64_t i, float y,
@@ -653,41 +611,6 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
   }
 }
 
-// FP32 counterpart of k_csr_g.
-template <bool FIRST, bool SCALE, int G>
-__global__ void __launch_bounds__(kThreads) k_csrf_g(CsrOp A, MpkF32Args e) {
-  if (e.ctrl && e.ctrl->done) return;
-  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  constexpr int kRows = 32 / G;
-  for (int64_t base = warp * kRows; base < A.n; base += nwarps * kRows) {
-    const int64_t i = base + lane / G;
-    const bool valid = i < A.n;
-    float a = 0.0f;
-    if (valid) {
-      const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
-      for (int64_t k = k0 + sub; k < k1; k += G) {
-        const int32_t c = __ldg(A.colind + k);
-        float v = __ldg(e.u + c);
-        if constexpr (SCALE) v *= __ldg(e.dinv + c);
-        a = fmaf(__ldg(e.valsf + k), v, a);
-      }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (valid && sub == 0) {
-      float uc = __ldg(e.u + i);
-      if constexpr (SCALE) uc *= __ldg(e.dinv + i);
-      if constexpr (FIRST && !SCALE) {
-        a *= e.dinv_u;
-        uc *= e.dinv_u;
-      }
-      mpk_f32_epilogue(e, i, a, uc, FIRST);
-    }
-  }
-}
-
 template <bool FIRST, bool SCALE>
 __global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
   if (e.ctrl && e.ctrl->done) return;
@@ -757,20 +680,14 @@ cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t s
   return cudaGetLastError();
 }
 
-int csr_ctas(int64_t n, int lanes = 1) {
-  int64_t want = (n * std::max(1, lanes) + kThreads - 1) / kThreads;
+int csr_ctas(int64_t n) {
+  int64_t want = (n + kThreads - 1) / kThreads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * kCsrCtasPerSm));
 }
 
 template <int EPI, bool SCALE>
 cudaError_t launch_csr(const CsrOp& A, const EpiArgs& e, cudaStream_t st) {
-  const int grid = csr_ctas(A.n, A.lanes);
-  switch (A.lanes) {
-    case 4: k_csr_g<EPI, SCALE, 4><<<grid, kThreads, 0, st>>>(A, e); break;
-    case 8: k_csr_g<EPI, SCALE, 8><<<grid, kThreads, 0, st>>>(A, e); break;
-    case 16: k_csr_g<EPI, SCALE, 16><<<grid, kThreads, 0, st>>>(A, e); break;
-    default: k_csr<EPI, SCALE><<<grid, kThreads, 0, st>>>(A, e); break;
-  }
+  k_csr<EPI, SCALE><<<csr_ctas(A.n), kThreads, 0, st>>>(A, e);
   return cudaGetLastError();
 }
 
@@ -792,7 +709,7 @@ int operator_grid_ctas(const OpDesc& A) {
     StencilGrid g = stencil_grid(A.st);
     return (int)(g.grid.x * g.grid.y * g.grid.z);
   }
-  return csr_ctas(A.csr.n, A.csr.lanes);
+  return csr_ctas(A.csr.n);
 }
 
 cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st) {
@@ -851,23 +768,13 @@ cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st
 #undef L7
     return cudaGetLastError();
   }
-  const int grid = csr_ctas(A.csr.n, A.csr.lanes);
-#define LF(F, S)                                                                         \
-  do {                                                                                   \
-    switch (A.csr.lanes) {                                                               \
-      case 4: k_csrf_g<F, S, 4><<<grid, kThreads, 0, st>>>(A.csr, e); break;             \
-      case 8: k_csrf_g<F, S, 8><<<grid, kThreads, 0, st>>>(A.csr, e); break;             \
-      case 16: k_csrf_g<F, S, 16><<<grid, kThreads, 0, st>>>(A.csr, e); break;           \
-      default: k_csrf<F, S><<<grid, kThreads, 0, st>>>(A.csr, e); break;                 \
-    }                                                                                    \
-  } while (0)
+  const int grid = csr_ctas(A.csr.n);
   if (e.first) {
-    if (scale) LF(true, true);
-    else LF(true, false);
+    if (scale) k_csrf<true, true><<<grid, kThreads, 0, st>>>(A.csr, e);
+    else k_csrf<true, false><<<grid, kThreads, 0, st>>>(A.csr, e);
   } else {
-    LF(false, false);
+    k_csrf<false, false><<<grid, kThreads, 0, st>>>(A.csr, e);
   }
-#undef LF
   return cudaGetLastError();
 }
 
