@@ -640,9 +640,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
   float hi[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-  const int64_t ld = a.ld;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto accum = [&](const float (&qn)[S], const float (&an)[S], float rh, float rl) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
+      df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
+      lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
+    }
+  };
+  // four consecutive points per thread and trip: 16-byte loads and stores
+  const int64_t n4 = a.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 qn4[S], an4[S];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        qn4[j] = __ldg(reinterpret_cast<const float4*>(a.Z + j * ld) + v);
+        an4[j] = __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+      }
+    } else {
+      float4 qo4[S], ao4[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo4[l] = reinterpret_cast<const float4*>(a.Q + l * ld)[v];
+        ao4[l] = reinterpret_cast<const float4*>(a.AQ + l * ld)[v];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float4 vq = __ldg(reinterpret_cast<const float4*>(a.Z + j * ld) + v);
+        float4 va = __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const float bl = sb[l + j * S];
+          vq.x = fmaf(qo4[l].x, bl, vq.x);
+          vq.y = fmaf(qo4[l].y, bl, vq.y);
+          vq.z = fmaf(qo4[l].z, bl, vq.z);
+          vq.w = fmaf(qo4[l].w, bl, vq.w);
+          va.x = fmaf(ao4[l].x, bl, va.x);
+          va.y = fmaf(ao4[l].y, bl, va.y);
+          va.z = fmaf(ao4[l].z, bl, va.z);
+          va.w = fmaf(ao4[l].w, bl, va.w);
+        }
+        qn4[j] = vq;
+        an4[j] = va;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      reinterpret_cast<float4*>(a.Q + j * ld)[v] = qn4[j];
+      reinterpret_cast<float4*>(a.AQ + j * ld)[v] = an4[j];
+    }
+    const float4 rh4 = __ldg(reinterpret_cast<const float4*>(a.rhi) + v);
+    const float4 rl4 = __ldg(reinterpret_cast<const float4*>(a.rlo) + v);
+    float qn[S], an[S];
+#define SSTEP_UPD_LANE(c)                   \
+    for (int j = 0; j < S; ++j) {           \
+      qn[j] = qn4[j].c;                     \
+      an[j] = an4[j].c;                     \
+    }                                       \
+    accum(qn, an, rh4.c, rl4.c);
+    SSTEP_UPD_LANE(x)
+    SSTEP_UPD_LANE(y)
+    SSTEP_UPD_LANE(z)
+    SSTEP_UPD_LANE(w)
+#undef SSTEP_UPD_LANE
+  }
+  for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
     float qn[S], an[S];
     if constexpr (FIRST) {
 #pragma unroll
@@ -1507,7 +1574,7 @@ cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStrea
     }                                                                                      \
     return cudaGetLastError();                                                             \
   }
-    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
     default: return cudaErrorNotSupported;
   }
