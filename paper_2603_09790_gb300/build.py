@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(err)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n%s" % p.stderr)

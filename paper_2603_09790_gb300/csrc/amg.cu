@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -110,41 +111,65 @@ void members(const std::vector<int32_t>& agg, int64_t nc, std::vector<int64_t>& 
   for (size_t i = 0; i < agg.size(); ++i) mem[fill[agg[i]]++] = (int32_t)i;
 }
 
-// P^T A P in the fixed order described at the top of the file.
+// P^T A P in the fixed order described at the top of the file.  Coarse rows are independent,
+// so contiguous blocks of them are formed by host threads and concatenated in row order: the
+// result does not depend on the number of threads.
 void galerkin(const HostCsr& A, const std::vector<int32_t>& agg, int64_t nc, HostCsr& C) {
   std::vector<int64_t> mptr;
   std::vector<int32_t> mem;
   members(agg, nc, mptr, mem);
   C.n = nc;
   C.rp.assign(nc + 1, 0);
-  C.ci.clear();
-  C.v.clear();
-  std::vector<int64_t> pos(nc, -1);
-  std::vector<std::pair<int32_t, double>> row;
-  for (int64_t J = 0; J < nc; ++J) {
-    row.clear();
-    for (int64_t m = mptr[J]; m < mptr[J + 1]; ++m) {
-      const int64_t i = mem[m];
-      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-        const int32_t Jc = agg[A.ci[k]];
-        if (pos[Jc] < 0) {
-          pos[Jc] = (int64_t)row.size();
-          row.emplace_back(Jc, A.v[k]);
-        } else {
-          row[pos[Jc]].second += A.v[k];
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int T = nc < 8192 ? 1 : std::min(16, hw);
+  std::vector<std::vector<int32_t>> tci(T);
+  std::vector<std::vector<double>> tv(T);
+  std::vector<int64_t> cnt(nc, 0);
+  auto work = [&](int t) {
+    const int64_t J0 = nc * t / T, J1 = nc * (t + 1) / T;
+    std::vector<int64_t> pos(nc, -1);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t J = J0; J < J1; ++J) {
+      row.clear();
+      for (int64_t m = mptr[J]; m < mptr[J + 1]; ++m) {
+        const int64_t i = mem[m];
+        for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+          const int32_t Jc = agg[A.ci[k]];
+          if (pos[Jc] < 0) {
+            pos[Jc] = (int64_t)row.size();
+            row.emplace_back(Jc, A.v[k]);
+          } else {
+            row[pos[Jc]].second += A.v[k];
+          }
         }
       }
+      for (auto& e : row) pos[e.first] = -1;
+      std::sort(row.begin(), row.end(),
+                [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                  return a.first < b.first;
+                });
+      for (auto& e : row) {
+        tci[t].push_back(e.first);
+        tv[t].push_back(e.second);
+      }
+      cnt[J] = (int64_t)row.size();
     }
-    for (auto& e : row) pos[e.first] = -1;
-    std::sort(row.begin(), row.end(),
-              [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
-                return a.first < b.first;
-              });
-    for (auto& e : row) {
-      C.ci.push_back(e.first);
-      C.v.push_back(e.second);
-    }
-    C.rp[J + 1] = (int64_t)C.ci.size();
+  };
+  if (T == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  for (int64_t J = 0; J < nc; ++J) C.rp[J + 1] = C.rp[J] + cnt[J];
+  C.ci.clear();
+  C.v.clear();
+  C.ci.reserve(C.rp[nc]);
+  C.v.reserve(C.rp[nc]);
+  for (int t = 0; t < T; ++t) {
+    C.ci.insert(C.ci.end(), tci[t].begin(), tci[t].end());
+    C.v.insert(C.v.end(), tv[t].begin(), tv[t].end());
   }
 }
 

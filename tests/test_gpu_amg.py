@@ -32,7 +32,8 @@ def q1(dims, seed=3, sigma=1.0, corr=4.0):
     return rp, ci, v
 
 
-CASES = [("q1", (14, 12, 10), 64), ("poisson", (20, 18, 16), 100), ("q1", (9, 17, 11), 30)]
+CASES = [("q1", (14, 12, 10), 64), ("poisson", (20, 18, 16), 100), ("q1", (9, 17, 11), 30),
+         ("q1", (40, 36, 32), 512)]  # large enough for the threaded host set-up (>= 8192 rows)
 
 
 def problem(kind, dims):
