@@ -339,14 +339,8 @@ __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T
       al[j] = __double2float_rn(sh.alpha[j] - (double)ah[j]);
     }
     float rrh[1] = {0.0f}, rrl[1] = {0.0f};
-    for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
-      float q[S], aq[S];
-#pragma unroll
-      for (int j = 0; j < S; ++j) {
-        q[j] = Q[j * ld + p];
-        aq[j] = AQ[j * ld + p];
-      }
-      float xh = v.xh[p], xl = v.xl[p], rh = v.rh[p], rl = v.rl[p];
+    auto point = [&](const float (&q)[S], const float (&aq)[S], float& xh, float& xl, float& rh,
+                     float& rl) {
       float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -357,12 +351,50 @@ __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T
       }
       df_add(xh, xl, dxh, dxl);
       df_add(rh, rl, -drh, -drl);
+      df_acc_prod(rrh[0], rrl[0], rh, rh);
+      rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
+    };
+    // four consecutive points per thread (16-byte accesses; rg.lo and ld are multiples of 4)
+    const int v0 = rg.lo >> 2, v1 = rg.hi >> 2;
+    for (int vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {
+      float4 q4[S], aq4[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q4[j] = reinterpret_cast<const float4*>(Q + j * ld)[vi];
+        aq4[j] = reinterpret_cast<const float4*>(AQ + j * ld)[vi];
+      }
+      float4 xh = reinterpret_cast<float4*>(v.xh)[vi], xl = reinterpret_cast<float4*>(v.xl)[vi];
+      float4 rh = reinterpret_cast<float4*>(v.rh)[vi], rl = reinterpret_cast<float4*>(v.rl)[vi];
+      float q[S], aq[S];
+#define SSTEP_BXR_LANE(c)            \
+      for (int j = 0; j < S; ++j) {  \
+        q[j] = q4[j].c;              \
+        aq[j] = aq4[j].c;            \
+      }                              \
+      point(q, aq, xh.c, xl.c, rh.c, rl.c);
+      SSTEP_BXR_LANE(x)
+      SSTEP_BXR_LANE(y)
+      SSTEP_BXR_LANE(z)
+      SSTEP_BXR_LANE(w)
+#undef SSTEP_BXR_LANE
+      reinterpret_cast<float4*>(v.xh)[vi] = xh;
+      reinterpret_cast<float4*>(v.xl)[vi] = xl;
+      reinterpret_cast<float4*>(v.rh)[vi] = rh;
+      reinterpret_cast<float4*>(v.rl)[vi] = rl;
+    }
+    for (int p = 4 * v1 + threadIdx.x; p < rg.hi; p += blockDim.x) {  // the last n mod 4 points
+      float q[S], aq[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        q[j] = Q[j * ld + p];
+        aq[j] = AQ[j * ld + p];
+      }
+      float xh = v.xh[p], xl = v.xl[p], rh = v.rh[p], rl = v.rl[p];
+      point(q, aq, xh, xl, rh, rl);
       v.xh[p] = xh;
       v.xl[p] = xl;
       v.rh[p] = rh;
       v.rl[p] = rl;
-      df_acc_prod(rrh[0], rrl[0], rh, rh);
-      rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
     }
     csum_df<S, 1>(cl, rrh, rrl, sh, par);
   }
@@ -394,7 +426,26 @@ __device__ bool b2_beta(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q,
     float hi[K], lo[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-    for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
+    // the MPK wrote AZ with another point-to-thread map: make its writes visible in the CTA
+    __syncthreads();
+    const int v0 = rg.lo >> 2, v1 = rg.hi >> 2;
+    for (int vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {  // four points per thread
+      float4 q4[S], z4[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) q4[i] = reinterpret_cast<const float4*>(Q + i * ld)[vi];
+#pragma unroll
+      for (int j = 0; j < S; ++j) z4[j] = reinterpret_cast<const float4*>(AZ + j * ld)[vi];
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          df_acc_prod(hi[i + j * S], lo[i + j * S], q4[i].x, z4[j].x);
+          df_acc_prod(hi[i + j * S], lo[i + j * S], q4[i].y, z4[j].y);
+          df_acc_prod(hi[i + j * S], lo[i + j * S], q4[i].z, z4[j].z);
+          df_acc_prod(hi[i + j * S], lo[i + j * S], q4[i].w, z4[j].w);
+        }
+    }
+    for (int p = 4 * v1 + threadIdx.x; p < rg.hi; p += blockDim.x) {
       float q[S], z[S];
 #pragma unroll
       for (int i = 0; i < S; ++i) q[i] = Q[i * ld + p];
@@ -467,7 +518,71 @@ __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* 
     float hi[K], lo[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-    for (int p = rg.lo + threadIdx.x; p < rg.hi; p += blockDim.x) {
+    auto accum = [&](const float (&qn)[S], const float (&an)[S], float rh, float rl) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
+        df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
+        lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
+      }
+    };
+    // the MPK wrote Z, AZ with another point-to-thread map: make its writes visible in the CTA
+    __syncthreads();
+    const int v0 = rg.lo >> 2, v1 = rg.hi >> 2;
+    for (int vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {  // four points per thread
+      float4 qn4[S], an4[S];
+      if constexpr (FIRST) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          qn4[j] = reinterpret_cast<const float4*>(Zn + j * ld)[vi];
+          an4[j] = reinterpret_cast<const float4*>(AZn + j * ld)[vi];
+        }
+      } else {
+        float4 qo4[S], ao4[S];
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          qo4[l] = reinterpret_cast<const float4*>(Qo + l * ld)[vi];
+          ao4[l] = reinterpret_cast<const float4*>(AQo + l * ld)[vi];
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          float4 vq = reinterpret_cast<const float4*>(Zn + j * ld)[vi];
+          float4 va = reinterpret_cast<const float4*>(AZn + j * ld)[vi];
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const float bl = sh.betaf[l + j * S];
+            vq.x = fmaf(qo4[l].x, bl, vq.x);
+            vq.y = fmaf(qo4[l].y, bl, vq.y);
+            vq.z = fmaf(qo4[l].z, bl, vq.z);
+            vq.w = fmaf(qo4[l].w, bl, vq.w);
+            va.x = fmaf(ao4[l].x, bl, va.x);
+            va.y = fmaf(ao4[l].y, bl, va.y);
+            va.z = fmaf(ao4[l].z, bl, va.z);
+            va.w = fmaf(ao4[l].w, bl, va.w);
+          }
+          qn4[j] = vq;
+          an4[j] = va;
+          reinterpret_cast<float4*>(Zn + j * ld)[vi] = vq;
+          reinterpret_cast<float4*>(AZn + j * ld)[vi] = va;
+        }
+      }
+      const float4 rh4 = reinterpret_cast<const float4*>(v.rh)[vi];
+      const float4 rl4 = reinterpret_cast<const float4*>(v.rl)[vi];
+      float qn[S], an[S];
+#define SSTEP_BUG_LANE(c)            \
+      for (int j = 0; j < S; ++j) {  \
+        qn[j] = qn4[j].c;            \
+        an[j] = an4[j].c;            \
+      }                              \
+      accum(qn, an, rh4.c, rl4.c);
+      SSTEP_BUG_LANE(x)
+      SSTEP_BUG_LANE(y)
+      SSTEP_BUG_LANE(z)
+      SSTEP_BUG_LANE(w)
+#undef SSTEP_BUG_LANE
+    }
+    for (int p = 4 * v1 + threadIdx.x; p < rg.hi; p += blockDim.x) {  // the last n mod 4 points
       float qn[S], an[S];
       if constexpr (FIRST) {
 #pragma unroll
@@ -496,14 +611,7 @@ __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* 
           AZn[j * ld + p] = va;
         }
       }
-      const float rh = v.rh[p], rl = v.rl[p];
-#pragma unroll
-      for (int i = 0; i < S; ++i) {
-#pragma unroll
-        for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
-        df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
-        lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
-      }
+      accum(qn, an, v.rh[p], v.rl[p]);
     }
     csum_df<S, K>(cl, hi, lo, sh, par);
   }
