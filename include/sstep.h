@@ -45,7 +45,7 @@ typedef enum {
   SSTEP_ERR_NONFINITE = 4,  /* non-finite residual norm */
   SSTEP_ERR_CUDA = 5,       /* a CUDA runtime call failed */
   SSTEP_ERR_OOM = 6,        /* device allocation failed */
-  SSTEP_ERR_UNSUPPORTED = 7 /* valid request this build does not implement */
+  SSTEP_ERR_UNSUPPORTED = 7 /* valid request that the library does not implement */
 } sstep_status;
 
 /* ------------------------------------------------------------------ operator A */
