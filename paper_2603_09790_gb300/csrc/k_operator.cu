@@ -767,7 +767,8 @@ __global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs
 
 template <int EPI, bool SCALE>
 cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t st) {
-  if constexpr ((EPI == EP_MPK || EPI == EP_MPK_FIRST) && !SCALE) {
+  // the middle steps only: with its three outputs the first step ran faster in the scalar kernel
+  if constexpr (EPI == EP_MPK && !SCALE) {
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };  // null passes
     const bool aligned = a16(e.u) && a16(e.y) && a16(e.znext) && a16(e.zprev) && a16(e.z1);
     if (op.points == 7 && op.nx % 2 == 0 && e.M.dinv == nullptr && aligned) {
