@@ -361,11 +361,15 @@ def run_q1(N, dev, sstep, I, torch):
         x.zero_()
         torch.cuda.synchronize()
         info = S.solve(bd, x)
+        ph = S.profile(bd, iters=3) if label.startswith("fp") and "pcg" not in label else None
         S.free()
         sol[label] = x
         out[label] = {"s": info.ms_solve / 1e3, "status": info.status, "outer_iters": info.outer_iters,
                       "relres_true": info.relres_true,
                       "rel_error_vs_x_true": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
+        if ph is not None:
+            out[label]["phase_ms_per_outer"] = {"mpk": ph[0], "gram_b2": ph[1], "update_w": ph[2],
+                                                "update_xr": ph[3]}
     ref = sol["fp64_s8_nu30"]
     for label in ("fp32_rr_s8_nu30", "fp32_rr_s8_nu3", "fp64_pcg"):
         out[label]["rel_diff_vs_fp64_s8"] = float(torch.linalg.norm(sol[label] - ref) / torch.linalg.norm(ref))
