@@ -337,43 +337,51 @@ def run_batch(spec, dev, sstep, I, torch, shape="0:0"):
 
 def run_q1(N, dev, sstep, I, torch):
     """Q1 trilinear diffusion with log-normal conductivity (sigma 1, correlation 8 cells) on an
-    N^3 grid of interior vertices, CSR, Jacobi, s = 8, rtol 1e-8: the FP32-basis form against
-    the FP64 form and FP64 classical PCG of the same library."""
+    N^3 grid of interior vertices, Jacobi, s = 8, rtol 1e-8: the FP32-basis form against the
+    FP64 form and FP64 classical PCG of the same library, with the assembled CSR matrix and
+    with the matrix-free operator (keys mf_*) on the same conductivities."""
     dims = (N, N, N)
     t0 = time.perf_counter()
     (rp, ci, v), kappa, xt, b = I.q1_lognormal_problem(dims)
     t_gen = time.perf_counter() - t0
     n = N ** 3
-    A = sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
-                  torch.from_numpy(v).to(dev))
+    ops = {"": sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                         torch.from_numpy(v).to(dev)),
+           "mf_": sstep.Q1(N, N, N, torch.from_numpy(np.ascontiguousarray(kappa)).to(dev))}
     bd = torch.from_numpy(b).to(dev)
     xtd = torch.from_numpy(xt).to(dev)
-    out = {"workload": f"q1_lognormal_{N}^3_csr_jacobi_literal_s8", "n": n, "nnz": int(rp[-1]),
+    out = {"workload": f"q1_lognormal_{N}^3_jacobi_literal_s8", "n": n, "nnz": int(rp[-1]),
+           "operators": {"(no prefix)": "CSR assembled by the input generator",
+                         "mf_": "matrix-free Q1 from the cell conductivities"},
            "generation_s": t_gen}
     sol = {}
-    for label, kw in (("fp64_s8_nu30", dict(s=8, sweeps=30)),
-                      ("fp32_rr_s8_nu30", dict(s=8, sweeps=30, precision="fp32_rr", rr_period=8)),
-                      ("fp32_rr_s8_nu3", dict(s=8, sweeps=3, precision="fp32_rr", rr_period=8)),
-                      ("fp64_pcg", dict(algo="pcg"))):
-        S = sstep.Solver(A, rtol=1e-8, power_iters=20, power_tol=0.0, lambda_min=-1.0, **kw)
-        x = torch.zeros_like(bd)
-        S.solve(bd, x)  # warm-up (graph instantiation)
-        x.zero_()
-        torch.cuda.synchronize()
-        info = S.solve(bd, x)
-        ph = S.profile(bd, iters=3) if label.startswith("fp") and "pcg" not in label else None
-        S.free()
-        sol[label] = x
-        out[label] = {"s": info.ms_solve / 1e3, "status": info.status, "outer_iters": info.outer_iters,
-                      "relres_true": info.relres_true,
-                      "rel_error_vs_x_true": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
-        if ph is not None:
-            out[label]["phase_ms_per_outer"] = {"mpk": ph[0], "gram_b2": ph[1], "update_w": ph[2],
-                                                "update_xr": ph[3]}
+    for pre, A in ops.items():
+        for label, kw in (("fp64_s8_nu30", dict(s=8, sweeps=30)),
+                          ("fp32_rr_s8_nu30", dict(s=8, sweeps=30, precision="fp32_rr", rr_period=8)),
+                          ("fp32_rr_s8_nu3", dict(s=8, sweeps=3, precision="fp32_rr", rr_period=8)),
+                          ("fp64_pcg", dict(algo="pcg"))):
+            S = sstep.Solver(A, rtol=1e-8, power_iters=20, power_tol=0.0, lambda_min=-1.0, **kw)
+            x = torch.zeros_like(bd)
+            S.solve(bd, x)  # warm-up (graph instantiation)
+            x.zero_()
+            torch.cuda.synchronize()
+            info = S.solve(bd, x)
+            ph = S.profile(bd, iters=3) if "pcg" not in label else None
+            S.free()
+            key = pre + label
+            sol[key] = x
+            out[key] = {"s": info.ms_solve / 1e3, "status": info.status,
+                        "outer_iters": info.outer_iters, "relres_true": info.relres_true,
+                        "rel_error_vs_x_true": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
+            if ph is not None:
+                out[key]["phase_ms_per_outer"] = {"mpk": ph[0], "gram_b2": ph[1], "update_w": ph[2],
+                                                  "update_xr": ph[3]}
     ref = sol["fp64_s8_nu30"]
-    for label in ("fp32_rr_s8_nu30", "fp32_rr_s8_nu3", "fp64_pcg"):
-        out[label]["rel_diff_vs_fp64_s8"] = float(torch.linalg.norm(sol[label] - ref) / torch.linalg.norm(ref))
-        out[label]["time_over_fp64_s8"] = out[label]["s"] / out["fp64_s8_nu30"]["s"]
+    for key in sol:
+        if key == "fp64_s8_nu30":
+            continue
+        out[key]["rel_diff_vs_fp64_s8"] = float(torch.linalg.norm(sol[key] - ref) / torch.linalg.norm(ref))
+        out[key]["time_over_fp64_s8"] = out[key]["s"] / out["fp64_s8_nu30"]["s"]
     out["timing"] = "host wall time of one sstep_solve (device buffers) after a warm-up solve"
     return out
 

@@ -49,7 +49,7 @@ typedef enum {
 } sstep_status;
 
 /* ------------------------------------------------------------------ operator A */
-enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1 };
+enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1, SSTEP_MATRIX_Q1 = 2 };
 
 /* The SPD matrix A of Ax = b (Section 1).
  * CSR: n rows, rowptr[n+1] (int64), colind[nnz] (int32, 0-based), vals[nnz]; device or host
@@ -59,7 +59,19 @@ enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1 };
  *      (row index i + nx*(j + ny*k); Dirichlet neighbours dropped).  points = 5 (2D, nz = 1),
  *      7 or 27 (3D).  weights: NULL for the Poisson weights (diagonal 4 / 6 / 26, neighbours -1),
  *      or `points` host doubles in the order of increasing linear offset (for 7 points:
- *      -z, -y, -x, centre, +x, +y, +z; for 27: dz-major, then dy, then dx). */
+ *      -z, -y, -x, centre, +x, +y, +z; for 27: dz-major, then dy, then dx).
+ * Q1: matrix-free trilinear (Q1) finite-element diffusion operator (a variable-coefficient
+ *      SPD matrix; the method takes any SPD A, Section 1): the nx*ny*nz interior vertices
+ *      (row index i + nx*(j + ny*k)) of a grid of (nx+1)*(ny+1)*(nz+1) unit cells, Dirichlet boundary vertices eliminated.  weights: the
+ *      per-cell conductivities kappa, (nx+1)*(ny+1)*(nz+1) doubles, cell cx + (nx+1)*(cy +
+ *      (ny+1)*cz) (device or host pointer; copied at set-up).  Every kappa must be finite and
+ *      positive (else SSTEP_ERR_INVALID).  Entries: a_ii = (1/3) sum of the 8 kappa around
+ *      vertex i; -(1/12) times the sum of the kappa of the cells shared with a neighbour two or
+ *      three offsets of +-1 away; 0 for the six axis neighbours (21 entries per interior row).
+ *      The same matrix as assembling the Q1 element stiffness kappa_e (K1 x M1 x M1 + M1 x K1 x
+ *      M1 + M1 x M1 x K1), K1 = [[1,-1],[-1,1]], M1 = [[1/3,1/6],[1/6,1/3]], over the cells.
+ *      points is ignored; n may be 0 or nx*ny*nz.  Preconditioners NONE and JACOBI; the
+ *      FP64 and FP32-basis s-step forms and PCG. */
 typedef struct {
   int kind;
   int64_t n;
@@ -296,8 +308,10 @@ SSTEP_API sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, cons
                                           const double* lam, const double* x, double* grad_vals,
                                           double scale, int accumulate, void* stream);
 
-/* Replace the values of the handle's CSR operator (same pattern), device or host vals[nnz];
- * M^{-1} (Jacobi) and the FP32 copies are refreshed.  The Chebyshev interval is kept. */
+/* Replace the values of the handle's operator, device or host: CSR vals[nnz] (same pattern), or
+ * the Q1 cell conductivities ((nx+1)(ny+1)(nz+1) doubles, checked like at set-up).  M^{-1}
+ * (Jacobi), the AMG hierarchy and the FP32 copies are refreshed; the Chebyshev interval is
+ * kept.  Constant stencils: SSTEP_ERR_INVALID. */
 SSTEP_API sstep_status sstep_update_values(sstep_handle h, const double* vals);
 
 /* Residual history of the last solve: relres[k] = ||r^(k)|| / ||b|| for k = 0..iters

@@ -70,6 +70,9 @@ struct sstep_ctx {
   int32_t* colind = nullptr;
   double* vals = nullptr;
   double* dinv = nullptr;
+  double* kappa = nullptr;  // Q1 operator: cell conductivities
+  int64_t ncell = 0;
+  double q1_gersh = 0.0;    // Q1 operator: Gershgorin lower bound found at set-up
   double *Z = nullptr, *AZ = nullptr, *Q = nullptr, *AQ = nullptr;
   double *x = nullptr, *r = nullptr, *b = nullptr, *p = nullptr, *Ap = nullptr;
   double* partials = nullptr;
@@ -87,7 +90,7 @@ struct sstep_ctx {
   int64_t ldf = 0;
   float *Zf = nullptr, *AZf = nullptr, *Qf = nullptr, *AQf = nullptr;
   float *rhi = nullptr, *rlo = nullptr, *xhi = nullptr, *xlo = nullptr;
-  float *valsf = nullptr, *dinvf = nullptr;
+  float *valsf = nullptr, *dinvf = nullptr, *kappaf = nullptr;
   // graphs of one outer iteration, per algorithm (index 3: the mixed literal form, rr_period
   // outer iterations followed by a residual replacement)
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -566,12 +569,13 @@ void destroy(sstep_ctx* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
-  void* fbufs[] = {h->Zf, h->AZf, h->Qf, h->AQf, h->rhi, h->rlo, h->xhi, h->xlo, h->valsf, h->dinvf};
+  void* fbufs[] = {h->Zf,  h->AZf, h->Qf,    h->AQf,   h->rhi,   h->rlo,
+                   h->xhi, h->xlo, h->valsf, h->dinvf, h->kappaf};
   for (void* p : fbufs)
     if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
                   h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl, h->eta_a, h->eta_b,
-                  h->whist};
+                  h->whist, h->kappa};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -582,6 +586,28 @@ void destroy(sstep_ctx* h) {
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->st && h->own_stream) cudaStreamDestroy(h->st);
   delete h;
+}
+
+// Q1 set-up pass: conductivities finite and positive, M^{-1} = 1 / a_ii into h->dinv (when
+// allocated), and the Gershgorin lower bound of M^{-1} A (Jacobi) or A into h->q1_gersh.
+sstep_status q1_setup(sstep_ctx* h) {
+  const int g = q1_setup_ctas(h->n);
+  int* bad = nullptr;
+  CK(cudaMallocAsync((void**)&bad, sizeof(int), h->st));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
+  CK(launch_q1_setup(h->op.q1, h->prec_kind == SSTEP_PREC_JACOBI, h->dinv, h->partials, bad,
+                     h->st));
+  std::vector<double> mins(g);
+  int hbad = 0;
+  CK(cudaMemcpyAsync(mins.data(), h->partials, sizeof(double) * g, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaFreeAsync(bad, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (hbad) return fail(SSTEP_ERR_INVALID, "Q1 conductivities must be finite and positive");
+  double lo = 1e308;
+  for (double v : mins) lo = std::min(lo, v);
+  h->q1_gersh = lo;
+  return SSTEP_OK;
 }
 
 sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
@@ -673,6 +699,15 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
       cudaFree(bad);
       if (hbad) return fail(SSTEP_ERR_INVALID, "CSR arrays are inconsistent (row pointers or column indices)");
     }
+  } else if (A->kind == SSTEP_MATRIX_Q1) {
+    if (A->nx < 1 || A->ny < 1 || A->nz < 1 || !A->weights)
+      return fail(SSTEP_ERR_INVALID, "Q1 needs nx, ny, nz >= 1 and the cell conductivities");
+    h->n = (int64_t)A->nx * A->ny * A->nz;
+    if (A->n != 0 && A->n != h->n) return fail(SSTEP_ERR_INVALID, "Q1 n != nx*ny*nz");
+    h->ncell = (int64_t)(A->nx + 1) * (A->ny + 1) * (A->nz + 1);
+    CK(cudaMalloc(&h->kappa, sizeof(double) * h->ncell));
+    CK(cudaMemcpyAsync(h->kappa, A->weights, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
+    h->op.q1 = Q1Op{A->nx, A->ny, A->nz, h->kappa, nullptr};
   } else {
     return fail(SSTEP_ERR_INVALID, "unknown matrix kind");
   }
@@ -713,6 +748,14 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   CK(cudaEventCreateWithFlags(&h->poll_ev[1], cudaEventDisableTiming));
   CK(gram_init());
 
+  // ---- Q1: check the conductivities, Jacobi M^{-1} and the Gershgorin bound in one pass
+  if (A->kind == SSTEP_MATRIX_Q1) {
+    if (h->prec_kind == SSTEP_PREC_JACOBI) CKS(alloc(&h->dinv, ld));
+    CKS(q1_setup(h));
+    h->M.dinv = h->dinv;
+    h->M.dinv_u = h->dinv ? 0.0 : 1.0;
+  }
+
   // ---- Jacobi M^{-1} for CSR
   if (A->kind == SSTEP_MATRIX_CSR) {
     if (h->prec_kind == SSTEP_PREC_AMG) {
@@ -747,6 +790,8 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   } else if (o->lambda_min < 0.0) {
     if (A->kind == SSTEP_MATRIX_STENCIL) {
       h->lmin = stencil_gershgorin(h->op.st, jac);
+    } else if (A->kind == SSTEP_MATRIX_Q1) {
+      h->lmin = h->q1_gersh > 0.0 ? h->q1_gersh : 0.0;
     } else {
       const int g = gershgorin_ctas(h->n);
       CK(launch_gershgorin_csr(h->op.csr, jac, h->partials, h->st));
@@ -791,6 +836,14 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
     if (A->kind == SSTEP_MATRIX_CSR) {
       CK(fal(&h->valsf, A->nnz));
       CK(launch_d2f(h->vals, h->valsf, A->nnz, h->st));
+      if (h->dinv) {
+        CK(fal(&h->dinvf, lf));
+        CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
+      }
+    } else if (A->kind == SSTEP_MATRIX_Q1) {
+      CK(fal(&h->kappaf, h->ncell));
+      CK(launch_d2f(h->kappa, h->kappaf, h->ncell, h->st));
+      h->op.q1.kappaf = h->kappaf;
       if (h->dinv) {
         CK(fal(&h->dinvf, lf));
         CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
@@ -1333,7 +1386,16 @@ sstep_status sstep_update_values(sstep_handle h, const double* vals) {
   g_err.clear();
   if (!h || !vals) return fail(SSTEP_ERR_INVALID, "null argument");
   if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
-  if (h->op.kind != SSTEP_MATRIX_CSR) return fail(SSTEP_ERR_INVALID, "the handle's operator is not CSR");
+  if (h->op.kind == SSTEP_MATRIX_Q1) {  // new conductivities
+    CK(cudaMemcpyAsync(h->kappa, vals, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
+    CKS(q1_setup(h));
+    if (h->kappaf) CK(launch_d2f(h->kappa, h->kappaf, h->ncell, h->st));
+    if (h->dinvf) CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return SSTEP_OK;
+  }
+  if (h->op.kind != SSTEP_MATRIX_CSR)
+    return fail(SSTEP_ERR_INVALID, "the handle's operator is a constant stencil");
   const int64_t nnz = h->nnz;
   CK(cudaMemcpyAsync(h->vals, vals, sizeof(double) * nnz, cudaMemcpyDefault, h->st));
   if (h->dinv) {

@@ -86,6 +86,15 @@ struct CsrOp {
   const double* vals;
 };
 
+// Matrix-free Q1 (trilinear finite-element) diffusion operator on the nx*ny*nz interior
+// vertices of a grid of (nx+1)(ny+1)(nz+1) unit cells, per-cell conductivity kappa (cell
+// cx + (nx+1)(cy + (ny+1) cz)), Dirichlet boundary vertices eliminated.
+struct Q1Op {
+  int nx, ny, nz;
+  const double* kappa;  // FP64 conductivities
+  const float* kappaf;  // FP32 copy for the FP32-basis path (null when unused)
+};
+
 // Preconditioner: dinv == nullptr means the uniform scalar dinv_u (M = I gives dinv_u = 1).
 struct Prec {
   const double* dinv;
@@ -258,6 +267,7 @@ struct OpDesc {
   int kind;  // SSTEP_MATRIX_*
   StencilOp st;
   CsrOp csr;
+  Q1Op q1;
   int64_t n;
 };
 
@@ -311,6 +321,17 @@ struct MpkF32Args {
   Ctrl* ctrl;
 };
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st);
+
+// Q1 operator kernels (k_q1.cu), reached through launch_operator / launch_mpk_f32.
+cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st);
+cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t st);
+int q1_grid_ctas(const Q1Op& A);
+// Set-up pass over the vertices: *bad = 1 when a conductivity is not finite and positive;
+// dinv (if non-null) = 1 / a_ii; out_min[CTA] = the CTA's minimum of the Gershgorin lower
+// bound (jacobi: 1 - sum_j |a_ij| / a_ii, else a_ii - sum_j |a_ij|, j != i).
+int q1_setup_ctas(int64_t n);
+cudaError_t launch_q1_setup(const Q1Op& A, int jacobi, double* dinv, double* out_min, int* bad,
+                            cudaStream_t st);
 
 // Blocks of the mixed path: Q, AQ, Z, AZ in FP32; x and r as FP64 plus FP32 (hi, lo)
 // increments; Gram sums accumulated in double-float (TwoProd + TwoSum on the FP32 pipe).

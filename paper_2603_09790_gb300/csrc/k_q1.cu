@@ -1,0 +1,348 @@
+// k_q1.cu -- the Q1 (trilinear finite-element) diffusion operator, matrix-free from the
+// per-cell conductivities: y = A u with the same fused epilogues as the stencil and CSR
+// kernels (one Matrix-Powers-Kernel step of Algorithm 2, residuals, power-method step, PCG
+// product), in FP64, and the FP32 MPK step of the FP32-basis path.
+//
+// Operator.  The element stiffness of the unit cube with conductivity kappa_e is
+// kappa_e (K1 x M1 x M1 + M1 x K1 x M1 + M1 x M1 x K1) (K1 = [[1,-1],[-1,1]],
+// M1 = [[1/3,1/6],[1/6,1/3]]): 1/3 on the diagonal, 0 between corners one edge apart, -1/12
+// between corners two or three edges apart.  Summed over the eight cells around an interior
+// vertex v:
+//   a_vv = (1/3) sum of the 8 kappa,
+//   face diagonal (two offsets of +-1): -(1/12) (sum of the 2 kappa sharing that face diagonal),
+//   body diagonal (three offsets of +-1): -(1/12) (kappa of the one cell between them),
+//   axis neighbours: 0.
+// So a row holds 21 entries, and one application reads one conductivity per cell and one
+// value per vertex (8 bytes per vertex in FP32) where the assembled CSR matrix reads about 170.
+//
+// Tiling.  A CTA owns 32 x 8 vertices of the xy plane and marches through a chunk of z planes:
+// u planes z-1, z, z+1 (one-vertex xy halo) and cell planes z, z+1 are staged in shared memory
+// (four u slots and three cell slots, so one barrier per plane suffices), and the next plane is
+// loaded into registers before the arithmetic of the current one.
+#include <algorithm>
+
+#include "common.cuh"
+#include "epilogue.cuh"
+
+namespace sstep {
+
+namespace {
+
+constexpr int QX = 32, QY = 8, QT = QX * QY;  // vertex tile, threads per CTA
+constexpr int UW = QX + 2, UH = QY + 2;       // staged u plane with its halo
+constexpr int KW = QX + 1, KH = QY + 1;       // staged cell plane (cells x0..x0+QX)
+constexpr int kUPer = (UW * UH + QT - 1) / QT;  // staged u values per thread
+constexpr int kKPer = (KW * KH + QT - 1) / QT;  // staged conductivities per thread
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
+struct Q1Smem {
+  T u[4][UH * UW];
+  T k[3][KH * KW];
+};
+
+// (A u)_v from the staged planes.  Um, Uc, Up: u planes z-1, z, z+1; K0, K1: cell planes z and
+// z+1 (the cells below and above the vertex plane).  Cell (a, b, c) of the vertex is
+// (x + a, y + b, z + c): the neighbour at offset (dx, dy, dz) lies in the cells with
+// a = (dx + 1) / 2 (any a when dx = 0), and so on.
+template <typename T>
+__device__ __forceinline__ T q1_vertex(const T* Um, const T* Uc, const T* Up, const T* K0,
+                                       const T* K1, int tx, int ty, T& uc) {
+  auto U = [&](const T* P, int dx, int dy) -> T { return P[(ty + 1 + dy) * UW + tx + 1 + dx]; };
+  auto C = [&](const T* P, int a, int b) -> T { return P[(ty + b) * KW + tx + a]; };
+  const T k000 = C(K0, 0, 0), k100 = C(K0, 1, 0), k010 = C(K0, 0, 1), k110 = C(K0, 1, 1);
+  const T k001 = C(K1, 0, 0), k101 = C(K1, 1, 0), k011 = C(K1, 0, 1), k111 = C(K1, 1, 1);
+  // face-diagonal couplings: the two cells that share each diagonal
+  const T z00 = k000 + k001, z10 = k100 + k101, z01 = k010 + k011, z11 = k110 + k111;  // dz = 0
+  const T y00 = k000 + k010, y10 = k100 + k110, y01 = k001 + k011, y11 = k101 + k111;  // dy = 0
+  const T x00 = k000 + k100, x10 = k010 + k110, x01 = k001 + k101, x11 = k011 + k111;  // dx = 0
+  const T k8 = (z00 + z10) + (z01 + z11);
+  T s = z00 * U(Uc, -1, -1);
+  s = fmaT(z10, U(Uc, 1, -1), s);
+  s = fmaT(z01, U(Uc, -1, 1), s);
+  s = fmaT(z11, U(Uc, 1, 1), s);
+  s = fmaT(y00, U(Um, -1, 0), s);
+  s = fmaT(y10, U(Um, 1, 0), s);
+  s = fmaT(y01, U(Up, -1, 0), s);
+  s = fmaT(y11, U(Up, 1, 0), s);
+  s = fmaT(x00, U(Um, 0, -1), s);
+  s = fmaT(x10, U(Um, 0, 1), s);
+  s = fmaT(x01, U(Up, 0, -1), s);
+  s = fmaT(x11, U(Up, 0, 1), s);
+  s = fmaT(k000, U(Um, -1, -1), s);
+  s = fmaT(k100, U(Um, 1, -1), s);
+  s = fmaT(k010, U(Um, -1, 1), s);
+  s = fmaT(k110, U(Um, 1, 1), s);
+  s = fmaT(k001, U(Up, -1, -1), s);
+  s = fmaT(k101, U(Up, 1, -1), s);
+  s = fmaT(k011, U(Up, -1, 1), s);
+  s = fmaT(k111, U(Up, 1, 1), s);
+  uc = U(Uc, 0, 0);
+  const T third = T(1) / T(3), twelfth = T(1) / T(12);
+  return fmaT(k8 * third, uc, -(s * twelfth));
+}
+
+// The z march shared by the FP64 and FP32 kernels.  load_u(idx) returns the (possibly
+// M^{-1}-scaled) input at vertex idx; at(z, y, uc, in) consumes the vertex of plane z.
+template <typename T, class LoadU, class At>
+__device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ kap, int zc,
+                                         Q1Smem<T>& sh, LoadU load_u, At at) {
+  const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int64_t pxy = (int64_t)nx * ny;
+  const int64_t cpxy = (int64_t)(nx + 1) * (ny + 1);
+  // the staged elements of this thread: u tile element j = tid + p QT, cell tile likewise
+  int64_t uoff[kUPer], koff[kKPer];
+  bool uok[kUPer], kok[kKPer];
+#pragma unroll
+  for (int p = 0; p < kUPer; ++p) {
+    const int j = tid + p * QT;
+    const int gx = x0 - 1 + j % UW, gy = y0 - 1 + j / UW;
+    uok[p] = j < UW * UH && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    uoff[p] = (int64_t)gy * nx + gx;
+  }
+#pragma unroll
+  for (int p = 0; p < kKPer; ++p) {
+    const int j = tid + p * QT;
+    const int cx = x0 + j % KW, cy = y0 + j / KW;
+    kok[p] = j < KW * KH && cx <= nx && cy <= ny;
+    koff[p] = (int64_t)cy * (nx + 1) + cx;
+  }
+  auto ldu = [&](int p, int zz) -> T {
+    if (!uok[p] || zz < 0 || zz >= nz) return T(0);
+    return load_u(uoff[p] + (int64_t)zz * pxy);
+  };
+  auto ldk = [&](int p, int cz) -> T {
+    if (!kok[p] || cz > nz) return T(0);
+    return __ldg(kap + koff[p] + (int64_t)cz * cpxy);
+  };
+  auto put_u = [&](int slot, int p, T v) {
+    const int j = tid + p * QT;
+    if (j < UW * UH) sh.u[slot][j] = v;
+  };
+  auto put_k = [&](int slot, int p, T v) {
+    const int j = tid + p * QT;
+    if (j < KW * KH) sh.k[slot][j] = v;
+  };
+  // u plane zz lives in slot (zz - z0 + 1) & 3, cell plane cz in slot (cz - z0) % 3
+  T nu[kUPer], nk[kKPer];
+#pragma unroll
+  for (int p = 0; p < kUPer; ++p) {
+    put_u(0, p, ldu(p, z0 - 1));
+    put_u(1, p, ldu(p, z0));
+    nu[p] = ldu(p, z0 + 1);
+  }
+#pragma unroll
+  for (int p = 0; p < kKPer; ++p) {
+    put_k(0, p, ldk(p, z0));
+    nk[p] = ldk(p, z0 + 1);
+  }
+  const int x = x0 + tx, y = y0 + ty;
+  const bool in = x < nx && y < ny;
+  int ks = 0;  // slot of cell plane z
+  for (int z = z0; z < z1; ++z) {
+    const int iu = z - z0;
+    const int ks1 = ks == 2 ? 0 : ks + 1;
+#pragma unroll
+    for (int p = 0; p < kUPer; ++p) put_u((iu + 2) & 3, p, nu[p]);
+#pragma unroll
+    for (int p = 0; p < kKPer; ++p) put_k(ks1, p, nk[p]);
+    __syncthreads();
+    if (z + 1 < z1) {
+#pragma unroll
+      for (int p = 0; p < kUPer; ++p) nu[p] = ldu(p, z + 2);
+#pragma unroll
+      for (int p = 0; p < kKPer; ++p) nk[p] = ldk(p, z + 2);
+    }
+    T uc = T(0), yv = T(0);
+    if (in)
+      yv = q1_vertex<T>(sh.u[iu & 3], sh.u[(iu + 1) & 3], sh.u[(iu + 2) & 3], sh.k[ks], sh.k[ks1],
+                        tx, ty, uc);
+    at((int64_t)z * pxy + (int64_t)y * nx + x, yv, uc, in);
+    ks = ks1;
+  }
+}
+
+template <int EPI, bool SCALE>
+__global__ void __launch_bounds__(QT) k_q1(Q1Op A, EpiArgs e, int zc) {
+  if (skip<EPI>(e)) return;
+  __shared__ Q1Smem<double> sh;
+  double red[2] = {0.0, 0.0};
+  const double* __restrict__ u = e.u;
+  auto load_u = [&](int64_t idx) -> double {
+    double v = __ldg(u + idx);
+    if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
+    return v;
+  };
+  q1_march<double>(A, A.kappa, zc, sh, load_u, [&](int64_t i, double yv, double uc, bool in) {
+    if (!in) return;
+    if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
+      yv *= e.M.dinv_u;
+      uc *= e.M.dinv_u;
+    }
+    epilogue<EPI>(e, i, yv, uc, red);
+  });
+  reduce_and_finish<EPI>(e, red);
+}
+
+template <bool FIRST, bool SCALE>
+__global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
+  if (e.ctrl && e.ctrl->done) return;
+  __shared__ Q1Smem<float> sh;
+  const float* __restrict__ u = e.u;
+  auto load_u = [&](int64_t idx) -> float {
+    float v = __ldg(u + idx);
+    if constexpr (SCALE) v *= __ldg(e.dinv + idx);
+    return v;
+  };
+  q1_march<float>(A, A.kappaf, zc, sh, load_u, [&](int64_t i, float yv, float uc, bool in) {
+    if (!in) return;
+    if constexpr (FIRST && !SCALE) {
+      yv *= e.dinv_u;
+      uc *= e.dinv_u;
+    }
+    mpk_f32_epilogue(e, i, yv, uc, FIRST);
+  });
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+struct Q1Grid {
+  dim3 grid;
+  int zc;
+};
+
+// xy tiles x z chunks: about eight CTAs per SM, z chunks of at least 8 planes.
+Q1Grid q1_grid(const Q1Op& A) {
+  const int gx = (A.nx + QX - 1) / QX, gy = (A.ny + QY - 1) / QY;
+  int64_t gz = std::max<int64_t>(1, (int64_t)sms() * 8 / std::max(1, gx * gy));
+  gz = std::min<int64_t>(gz, std::max(1, A.nz / 8));
+  const int zc = (int)((A.nz + gz - 1) / gz);
+  return {dim3(gx, gy, (A.nz + zc - 1) / zc), zc};
+}
+
+template <int EPI>
+cudaError_t launch_epi(const Q1Op& A, const EpiArgs& e, cudaStream_t st) {
+  const Q1Grid g = q1_grid(A);
+  if (EPI == EP_MPK_FIRST && e.M.dinv != nullptr)
+    k_q1<EPI, true><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+  else
+    k_q1<EPI, false><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+  return cudaGetLastError();
+}
+
+// Set-up pass: one vertex per thread, conductivities read from global memory.
+__global__ void __launch_bounds__(kThreads) k_q1_setup(Q1Op A, int jacobi, double* dinv,
+                                                       double* out_min, int* bad) {
+  __shared__ double sh[kThreads];
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t ncell = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t c = t0; c < ncell; c += stride) {
+    const double k = A.kappa[c];
+    if (!(k > 0.0) || !(k < 1.79e308)) *bad = 1;
+  }
+  double lo = 1.0e308;
+  for (int64_t i = t0; i < n; i += stride) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+    auto kap = [&](int a, int b, int c) -> double {
+      return A.kappa[((int64_t)(z + c) * (ny + 1) + (y + b)) * (nx + 1) + (x + a)];
+    };
+    double k8 = 0.0, off = 0.0;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) k8 += kap(a, b, c);
+    // interior neighbours at offsets with two or three non-zero components
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int nnzc = (dx != 0) + (dy != 0) + (dz != 0);
+          if (nnzc < 2) continue;
+          if (x + dx < 0 || x + dx >= nx || y + dy < 0 || y + dy >= ny || z + dz < 0 ||
+              z + dz >= nz)
+            continue;
+          double w = 0.0;  // sum of the conductivities of the cells holding both vertices
+          for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+              for (int a = 0; a < 2; ++a) {
+                if (dx != 0 && a != (dx + 1) / 2) continue;
+                if (dy != 0 && b != (dy + 1) / 2) continue;
+                if (dz != 0 && c != (dz + 1) / 2) continue;
+                w += kap(a, b, c);
+              }
+          off += w / 12.0;
+        }
+    const double d = k8 / 3.0;
+    if (dinv) dinv[i] = 1.0 / d;
+    lo = fmin(lo, jacobi ? 1.0 - off / d : d - off);
+  }
+  sh[threadIdx.x] = lo;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out_min[blockIdx.x] = sh[0];
+}
+
+}  // namespace
+
+int q1_grid_ctas(const Q1Op& A) {
+  const Q1Grid g = q1_grid(A);
+  return (int)(g.grid.x * g.grid.y * g.grid.z);
+}
+
+cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st) {
+  switch (e.epi) {
+    case EP_SPMV: return launch_epi<EP_SPMV>(A, e, st);
+    case EP_MPK: return launch_epi<EP_MPK>(A, e, st);
+    case EP_MPK_FIRST: return launch_epi<EP_MPK_FIRST>(A, e, st);
+    case EP_RESID: return launch_epi<EP_RESID>(A, e, st);
+    case EP_POWER: return launch_epi<EP_POWER>(A, e, st);
+    case EP_PCG_AP: return launch_epi<EP_PCG_AP>(A, e, st);
+    case EP_TRUERES: return launch_epi<EP_TRUERES>(A, e, st);
+    case EP_RR: return launch_epi<EP_RR>(A, e, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t st) {
+  if (!A.kappaf) return cudaErrorInvalidValue;
+  const Q1Grid g = q1_grid(A);
+  if (e.first) {
+    if (e.dinv) k_q1f<true, true><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+    else k_q1f<true, false><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+  } else {
+    k_q1f<false, false><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+  }
+  return cudaGetLastError();
+}
+
+int q1_setup_ctas(int64_t n) {
+  const int64_t want = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * 4));
+}
+
+cudaError_t launch_q1_setup(const Q1Op& A, int jacobi, double* dinv, double* out_min, int* bad,
+                            cudaStream_t st) {
+  const int64_t n = (int64_t)A.nx * A.ny * A.nz;
+  k_q1_setup<<<q1_setup_ctas(n), kThreads, 0, st>>>(A, jacobi, dinv, out_min, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace sstep

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsstep.so")
 
 OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED = range(8)
-MATRIX_CSR, MATRIX_STENCIL = 0, 1
+MATRIX_CSR, MATRIX_STENCIL, MATRIX_Q1 = 0, 1, 2
 PREC = {"none": 0, "jacobi": 1, "amg": 2}
 ALGO = {"onesync": 0, "literal": 1, "pcg": 2}
 GRAM = {"fgs": 0, "cholesky": 1}
@@ -168,6 +168,25 @@ class CSR:
 
 
 @dataclass
+class Q1:
+    """Matrix-free Q1 finite-element diffusion operator on the nx x ny x nz interior vertices of
+    a grid of (nx+1)(ny+1)(nz+1) unit cells; kappa: the cell conductivities, float64, shape
+    (nz+1, ny+1, nx+1) or flat, torch (any device) or numpy."""
+    nx: int
+    ny: int
+    nz: int
+    kappa: object
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def ncell(self):
+        return (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+
+
+@dataclass
 class Info:
     status: int
     outer_iters: int
@@ -194,7 +213,7 @@ class Solver:
                  lambda_max=0.0, power_v0=None, check_every=0, gram_blocks="full", precision="fp64",
                  rr_period=0, persistent=False, cluster=0, block_threads=0, amg_coarse_max=0,
                  amg_max_levels=0, stream=None):
-        """A: a Stencil or CSR (one system), or a list of 7-point Stencils (the batched
+        """A: a Stencil, CSR or Q1 (one system), or a list of 7-point Stencils (the batched
         persistent solver; also used for a single Stencil when persistent=True)."""
         lib = load()
         mats = list(A) if isinstance(A, (list, tuple)) else [A]
@@ -211,13 +230,23 @@ class Solver:
                     w = np.ascontiguousarray(a.weights, dtype=np.float64)
                     self._weights.append(w)
                     m.weights = w.ctypes.data
+            elif isinstance(a, Q1):
+                k = a.kappa
+                numel = k.numel() if hasattr(k, "numel") else int(np.asarray(k).size)
+                dt = str(getattr(k, "dtype", ""))
+                if numel != a.ncell or "float64" not in dt:
+                    raise ValueError("Q1 kappa must hold (nx+1)(ny+1)(nz+1) float64 values")
+                m.kind = MATRIX_Q1
+                m.n = a.n
+                m.nx, m.ny, m.nz = a.nx, a.ny, a.nz
+                m.weights = _ptr(k)
             elif isinstance(a, CSR):
                 m.kind = MATRIX_CSR
                 m.n = a.n
                 m.nnz = a.nnz
                 m.rowptr, m.colind, m.vals = _ptr(a.rowptr), _ptr(a.colind), _ptr(a.vals)
             else:
-                raise TypeError("A must be a Stencil or a CSR, or a list of Stencils")
+                raise TypeError("A must be a Stencil, a CSR or a Q1, or a list of Stencils")
         self.nsys = len(mats)
         self.sizes = [int(m.n) for m in marr]
         self.batched = self.nsys > 1 or bool(persistent)
@@ -357,8 +386,9 @@ class Solver:
         return list(ms)
 
     def update_values(self, vals):
-        """sstep_update_values: new values for the handle's CSR operator (same pattern); the
-        Jacobi diagonal is recomputed, the Chebyshev interval is kept."""
+        """sstep_update_values: new values for the handle's CSR operator (same pattern) or new
+        Q1 cell conductivities; the Jacobi diagonal is recomputed, the Chebyshev interval is
+        kept."""
         _check(load().sstep_update_values(self._h, _ptr(vals)))
 
     def get_history(self):
