@@ -45,7 +45,9 @@ typedef enum {
   SSTEP_ERR_NONFINITE = 4,  /* non-finite residual norm */
   SSTEP_ERR_CUDA = 5,       /* a CUDA runtime call failed */
   SSTEP_ERR_OOM = 6,        /* device allocation failed */
-  SSTEP_ERR_UNSUPPORTED = 7 /* valid request that the library does not implement */
+  SSTEP_ERR_UNSUPPORTED = 7, /* valid request that the library does not implement */
+  SSTEP_ERR_TIMEOUT = 8      /* a bounded device-side wait (a copy that never arrived) ran out;
+                                the solve stopped, the CUDA context stays usable */
 } sstep_status;
 
 /* ------------------------------------------------------------------ operator A */
@@ -71,7 +73,10 @@ enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1, SSTEP_MATRIX_Q1 = 2 };
  *      The same matrix as assembling the Q1 element stiffness kappa_e (K1 x M1 x M1 + M1 x K1 x
  *      M1 + M1 x M1 x K1), K1 = [[1,-1],[-1,1]], M1 = [[1/3,1/6],[1/6,1/3]], over the cells.
  *      points is ignored; n may be 0 or nx*ny*nz.  Preconditioners NONE and JACOBI; the
- *      FP64 and FP32-basis s-step forms and PCG. */
+ *      FP64 and FP32-basis s-step forms and PCG.  In the FP32-basis form with nx a multiple
+ *      of 4 (nx >= 40, ny >= 10) the middle MPK steps are fed by tensor-memory-accelerator
+ *      copies; SSTEP_Q1_TMA=0 in the environment at set-up selects plain loads (same results
+ *      bit for bit). */
 typedef struct {
   int kind;
   int64_t n;

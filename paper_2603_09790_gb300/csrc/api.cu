@@ -8,6 +8,7 @@
 // replayed.  The host reads the device stop flag every `check_every` iterations while the
 // next batch is already queued; launches after convergence return at kernel entry.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -73,6 +74,7 @@ struct sstep_ctx {
   double* kappa = nullptr;  // Q1 operator: cell conductivities
   int64_t ncell = 0;
   double q1_gersh = 0.0;    // Q1 operator: Gershgorin lower bound found at set-up
+  Q1TmaMaps* q1tma = nullptr;  // Q1 operator, FP32 path: tensor maps of the basis columns
   double *Z = nullptr, *AZ = nullptr, *Q = nullptr, *AQ = nullptr;
   double *x = nullptr, *r = nullptr, *b = nullptr, *p = nullptr, *Ap = nullptr;
   double* partials = nullptr;
@@ -565,6 +567,7 @@ void destroy(sstep_ctx* h) {
   if (!h) return;
   if (h->batch) batch_free(h->batch);
   if (h->amg) amg_free(h->amg);
+  if (h->q1tma) q1_tma_free(h->q1tma);
   if (h->t) cudaFree(h->t);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
@@ -707,7 +710,8 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
     h->ncell = (int64_t)(A->nx + 1) * (A->ny + 1) * (A->nz + 1);
     CK(cudaMalloc(&h->kappa, sizeof(double) * h->ncell));
     CK(cudaMemcpyAsync(h->kappa, A->weights, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
-    h->op.q1 = Q1Op{A->nx, A->ny, A->nz, h->kappa, nullptr};
+    h->op.q1 = Q1Op{A->nx, A->ny, A->nz, h->kappa, nullptr, (int)round_up(A->nx + 1, 4),
+                    nullptr};
   } else {
     return fail(SSTEP_ERR_INVALID, "unknown matrix kind");
   }
@@ -841,9 +845,15 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
         CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
       }
     } else if (A->kind == SSTEP_MATRIX_Q1) {
-      CK(fal(&h->kappaf, h->ncell));
-      CK(launch_d2f(h->kappa, h->kappaf, h->ncell, h->st));
+      CK(fal(&h->kappaf, (int64_t)h->op.q1.kpitch * (A->ny + 1) * (A->nz + 1)));
       h->op.q1.kappaf = h->kappaf;
+      CK(launch_q1_kappaf(h->op.q1, h->kappaf, h->st));
+      std::vector<const float*> cols(s);
+      for (int c = 0; c < s; ++c) cols[c] = h->Zf + c * lf;
+      // null (or SSTEP_Q1_TMA=0 in the environment): the plain-load kernel serves every step
+      const char* tma_env = std::getenv("SSTEP_Q1_TMA");
+      if (!(tma_env && tma_env[0] == '0')) h->q1tma = q1_tma_build(h->op.q1, cols.data(), s);
+      h->op.q1.tma = h->q1tma;
       if (h->dinv) {
         CK(fal(&h->dinvf, lf));
         CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
@@ -1140,6 +1150,7 @@ const char* sstep_status_string(sstep_status s) {
     case SSTEP_ERR_CUDA: return "CUDA error";
     case SSTEP_ERR_OOM: return "out of device memory";
     case SSTEP_ERR_UNSUPPORTED: return "unsupported";
+    case SSTEP_ERR_TIMEOUT: return "a bounded device-side wait ran out";
   }
   return "unknown status";
 }
@@ -1389,7 +1400,7 @@ sstep_status sstep_update_values(sstep_handle h, const double* vals) {
   if (h->op.kind == SSTEP_MATRIX_Q1) {  // new conductivities
     CK(cudaMemcpyAsync(h->kappa, vals, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
     CKS(q1_setup(h));
-    if (h->kappaf) CK(launch_d2f(h->kappa, h->kappaf, h->ncell, h->st));
+    if (h->kappaf) CK(launch_q1_kappaf(h->op.q1, h->kappaf, h->st));
     if (h->dinvf) CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
     CK(cudaStreamSynchronize(h->st));
     return SSTEP_OK;

@@ -89,10 +89,13 @@ struct CsrOp {
 // Matrix-free Q1 (trilinear finite-element) diffusion operator on the nx*ny*nz interior
 // vertices of a grid of (nx+1)(ny+1)(nz+1) unit cells, per-cell conductivity kappa (cell
 // cx + (nx+1)(cy + (ny+1) cz)), Dirichlet boundary vertices eliminated.
+struct Q1TmaMaps;  // TMA descriptors of the FP32 MPK step (k_q1.cu)
 struct Q1Op {
   int nx, ny, nz;
-  const double* kappa;  // FP64 conductivities
-  const float* kappaf;  // FP32 copy for the FP32-basis path (null when unused)
+  const double* kappa;    // FP64 conductivities, rows of nx+1
+  const float* kappaf;    // FP32 copy for the FP32-basis path (null when unused), rows of kpitch
+  int kpitch;             // row pitch of kappaf: nx+1 rounded up to a multiple of 4
+  const Q1TmaMaps* tma;   // tensor maps of the basis columns and kappaf, or null
 };
 
 // Preconditioner: dinv == nullptr means the uniform scalar dinv_u (M = I gives dinv_u = 1).
@@ -332,6 +335,13 @@ int q1_grid_ctas(const Q1Op& A);
 int q1_setup_ctas(int64_t n);
 cudaError_t launch_q1_setup(const Q1Op& A, int jacobi, double* dinv, double* out_min, int* bad,
                             cudaStream_t st);
+// FP32 conductivities with rows padded to kpitch (the layout the tensor map needs).
+cudaError_t launch_q1_kappaf(const Q1Op& A, float* kappaf, cudaStream_t st);
+// Tensor maps for the TMA-fed FP32 MPK step: one per basis column (cols[c], n floats each) and
+// one for kappaf.  Null when the grid does not allow them (nx not a multiple of 4) or the
+// driver cannot encode them; the step then runs on plain loads.
+Q1TmaMaps* q1_tma_build(const Q1Op& A, const float* const* cols, int ncols);
+void q1_tma_free(Q1TmaMaps* m);
 
 // Blocks of the mixed path: Q, AQ, Z, AZ in FP32; x and r as FP64 plus FP32 (hi, lo)
 // increments; Gram sums accumulated in double-float (TwoProd + TwoSum on the FP32 pipe).

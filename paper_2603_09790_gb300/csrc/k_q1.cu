@@ -18,7 +18,12 @@
 // Tiling.  A CTA owns 32 x 8 vertices of the xy plane and marches through a chunk of z planes:
 // u planes z-1, z, z+1 (one-vertex xy halo) and cell planes z, z+1 are staged in shared memory
 // (four u slots and three cell slots, so one barrier per plane suffices), and the next plane is
-// loaded into registers before the arithmetic of the current one.
+// loaded into registers before the arithmetic of the current one.  The middle steps of the
+// FP32 MPK (the bulk of the FP32-basis solve) instead bring every plane in with tensor-memory-
+// accelerator copies several planes ahead (k_q1f_tma), when the grid allows it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -87,14 +92,14 @@ __device__ __forceinline__ T q1_vertex(const T* Um, const T* Uc, const T* Up, co
 // The z march shared by the FP64 and FP32 kernels.  load_u(idx) returns the (possibly
 // M^{-1}-scaled) input at vertex idx; at(z, y, uc, in) consumes the vertex of plane z.
 template <typename T, class LoadU, class At>
-__device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ kap, int zc,
-                                         Q1Smem<T>& sh, LoadU load_u, At at) {
+__device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ kap, int kpitch,
+                                         int zc, Q1Smem<T>& sh, LoadU load_u, At at) {
   const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
   const int64_t pxy = (int64_t)nx * ny;
-  const int64_t cpxy = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t cpxy = (int64_t)kpitch * (ny + 1);
   // the staged elements of this thread: u tile element j = tid + p QT, cell tile likewise
   int64_t uoff[kUPer], koff[kKPer];
   bool uok[kUPer], kok[kKPer];
@@ -110,7 +115,7 @@ __device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ ka
     const int j = tid + p * QT;
     const int cx = x0 + j % KW, cy = y0 + j / KW;
     kok[p] = j < KW * KH && cx <= nx && cy <= ny;
-    koff[p] = (int64_t)cy * (nx + 1) + cx;
+    koff[p] = (int64_t)cy * kpitch + cx;
   }
   auto ldu = [&](int p, int zz) -> T {
     if (!uok[p] || zz < 0 || zz >= nz) return T(0);
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(QT) k_q1(Q1Op A, EpiArgs e, int zc) {
     if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
     return v;
   };
-  q1_march<double>(A, A.kappa, zc, sh, load_u, [&](int64_t i, double yv, double uc, bool in) {
+  q1_march<double>(A, A.kappa, A.nx + 1, zc, sh, load_u, [&](int64_t i, double yv, double uc, bool in) {
     if (!in) return;
     if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
       yv *= e.M.dinv_u;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
     if constexpr (SCALE) v *= __ldg(e.dinv + idx);
     return v;
   };
-  q1_march<float>(A, A.kappaf, zc, sh, load_u, [&](int64_t i, float yv, float uc, bool in) {
+  q1_march<float>(A, A.kappaf, A.kpitch, zc, sh, load_u, [&](int64_t i, float yv, float uc, bool in) {
     if (!in) return;
     if constexpr (FIRST && !SCALE) {
       yv *= e.dinv_u;
@@ -207,6 +212,183 @@ __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
     }
     mpk_f32_epilogue(e, i, yv, uc, FIRST);
   });
+}
+
+// ---------------------------------------------------------------- TMA-fed FP32 MPK step
+
+// Middle MPK steps of the FP32 path (input not scaled by M^{-1}): one thread issues, per z
+// plane, a 3D tiled copy of the u plane with its halo (a 40 x 10 box that starts 4 vertices left
+// of the tile, so that the x coordinate stays a multiple of 16 bytes) and one of the
+// conductivity plane (36 x 9 cells); both complete on the stage's mbarrier.  kNS stages keep
+// three planes in flight ahead of the three being read.  The copy zero-fills whatever lies
+// outside the grid, which is exactly the eliminated Dirichlet boundary.  Every wait is bounded:
+// a copy that never lands stops the solve with SSTEP_ERR_TIMEOUT instead of hanging.
+constexpr int TUW = 40, TUH = 10;  // u box (vertices)
+constexpr int TKW = 36, TKH = 9;   // conductivity box (cells)
+constexpr int kNS = 6;             // pipeline stages (z planes)
+constexpr int kUStage = 416;       // floats per u stage: 400 used, 1664 bytes (13 x 128)
+constexpr int kKStage = 352;       // floats per cell stage: 324 used, 1408 bytes (11 x 128)
+constexpr uint32_t kStageBytes = (TUW * TUH + TKW * TKH) * 4;
+constexpr uint32_t kWaitRounds = 1u << 22;  // try_wait rounds before a copy counts as lost
+
+struct __align__(128) TmaSmem {
+  float u[kNS][kUStage];
+  float k[kNS][kKStage];
+  unsigned long long full[kNS];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitRounds; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensorMap mu,
+                                                 const __grid_constant__ CUtensorMap mk, Q1Op A,
+                                                 MpkF32Args e, int zc) {
+  if (e.ctrl && e.ctrl->done) return;
+  __shared__ TmaSmem sh;
+  const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int np = z1 - z0 + 2;  // stage p holds u plane and cell plane z0 - 1 + p
+  const int64_t pxy = (int64_t)nx * ny;
+  int issued = 0;              // stages issued (thread 0's count)
+  auto issue = [&](int p) {
+    const int slot = p % kNS;
+    const uint32_t bar = smem_addr(&sh.full[slot]);
+    mbar_expect_tx(bar, kStageBytes);
+    tma_load_3d(smem_addr(sh.u[slot]), &mu, x0 - 4, y0 - 1, z0 - 1 + p, bar);
+    tma_load_3d(smem_addr(sh.k[slot]), &mk, x0, y0, z0 - 1 + p, bar);
+    issued = p + 1;
+  };
+  if (tid == 0) {
+    for (int i = 0; i < kNS; ++i) mbar_init(smem_addr(&sh.full[i]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int p = 0; p < min(kNS, np); ++p) issue(p);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool in = x < nx && y < ny;
+  int waited = 0;  // stages 0 .. waited-1 have landed
+  bool lost = false;
+  auto wait_stage = [&](int p) {
+    if (!lost && !mbar_wait(smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u)) lost = true;
+    if (!lost) waited = p + 1;
+  };
+  wait_stage(0);
+  wait_stage(1);
+  for (int i = 0; i < z1 - z0; ++i) {
+    const int64_t idx = (int64_t)(z0 + i) * pxy + (int64_t)y * nx + x;
+    float dv = e.dinv_u, zp = 0.0f;
+    if (in) {  // epilogue inputs, requested before the wait so that their latency overlaps it
+      if (e.dinv) dv = __ldg(e.dinv + idx);
+      if (e.zprev) zp = __ldg(e.zprev + idx);
+    }
+    wait_stage(i + 2);
+    if (!lost && in) {
+      // the u box starts at x0 - 4, y0 - 1: shift the staged planes to q1_vertex's layout
+      const float* Um = sh.u[i % kNS];
+      const float* Uc = sh.u[(i + 1) % kNS];
+      const float* Up = sh.u[(i + 2) % kNS];
+      const float* K0 = sh.k[(i + 1) % kNS];
+      const float* K1 = sh.k[(i + 2) % kNS];
+      auto U = [&](const float* P, int dx, int dy) -> float {
+        return P[(ty + 1 + dy) * TUW + tx + 4 + dx];
+      };
+      auto C = [&](const float* P, int a, int b) -> float { return P[(ty + b) * TKW + tx + a]; };
+      const float k000 = C(K0, 0, 0), k100 = C(K0, 1, 0), k010 = C(K0, 0, 1), k110 = C(K0, 1, 1);
+      const float k001 = C(K1, 0, 0), k101 = C(K1, 1, 0), k011 = C(K1, 0, 1), k111 = C(K1, 1, 1);
+      const float z00 = k000 + k001, z10 = k100 + k101, z01 = k010 + k011, z11 = k110 + k111;
+      const float y00 = k000 + k010, y10 = k100 + k110, y01 = k001 + k011, y11 = k101 + k111;
+      const float x00 = k000 + k100, x10 = k010 + k110, x01 = k001 + k101, x11 = k011 + k111;
+      const float k8 = (z00 + z10) + (z01 + z11);
+      float s = z00 * U(Uc, -1, -1);
+      s = fmaf(z10, U(Uc, 1, -1), s);
+      s = fmaf(z01, U(Uc, -1, 1), s);
+      s = fmaf(z11, U(Uc, 1, 1), s);
+      s = fmaf(y00, U(Um, -1, 0), s);
+      s = fmaf(y10, U(Um, 1, 0), s);
+      s = fmaf(y01, U(Up, -1, 0), s);
+      s = fmaf(y11, U(Up, 1, 0), s);
+      s = fmaf(x00, U(Um, 0, -1), s);
+      s = fmaf(x10, U(Um, 0, 1), s);
+      s = fmaf(x01, U(Up, 0, -1), s);
+      s = fmaf(x11, U(Up, 0, 1), s);
+      s = fmaf(k000, U(Um, -1, -1), s);
+      s = fmaf(k100, U(Um, 1, -1), s);
+      s = fmaf(k010, U(Um, -1, 1), s);
+      s = fmaf(k110, U(Um, 1, 1), s);
+      s = fmaf(k001, U(Up, -1, -1), s);
+      s = fmaf(k101, U(Up, 1, -1), s);
+      s = fmaf(k011, U(Up, -1, 1), s);
+      s = fmaf(k111, U(Up, 1, 1), s);
+      const float uc = U(Uc, 0, 0);
+      const float yv = fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
+      e.y[idx] = yv;  // A z_q
+      if (e.znext) {
+        const float t = e.zprev ? -zp : 0.0f;
+        e.znext[idx] = fmaf(e.c1 * dv, yv, fmaf(-e.c2, uc, t));
+      }
+    }
+    // stage i (plane z - 1) is read for the last time: refill its slot kNS planes ahead
+    if (__syncthreads_or(lost)) break;
+    if (tid == 0 && i + kNS < np) issue(i + kNS);
+  }
+  if (lost && tid == 0) {
+    // let the copies still in flight land before the CTA's shared memory is released
+    for (int p = waited; p < issued; ++p)
+      mbar_wait(smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u);
+    if (e.ctrl) {
+      e.ctrl->status = SSTEP_ERR_TIMEOUT;
+      e.ctrl->done = 1;
+    }
+  }
+}
+
+// FP32 conductivities with rows padded to kpitch (padding zero).
+__global__ void k_q1_kappaf(Q1Op A, float* out) {
+  const int64_t rows = (int64_t)(A.ny + 1) * (A.nz + 1);
+  const int64_t total = rows * A.kpitch;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = c / A.kpitch;
+    const int cx = (int)(c % A.kpitch);
+    out[c] = cx <= A.nx ? (float)A.kappa[row * (A.nx + 1) + cx] : 0.0f;
+  }
 }
 
 int sms() {
@@ -302,6 +484,15 @@ __global__ void __launch_bounds__(kThreads) k_q1_setup(Q1Op A, int jacobi, doubl
 
 }  // namespace
 
+constexpr int kMaxCols = 16;
+
+struct Q1TmaMaps {
+  int ncols;
+  const float* col[kMaxCols];
+  CUtensorMap mu[kMaxCols];
+  CUtensorMap mk;
+};
+
 int q1_grid_ctas(const Q1Op& A) {
   const Q1Grid g = q1_grid(A);
   return (int)(g.grid.x * g.grid.y * g.grid.z);
@@ -324,12 +515,84 @@ cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st)
 cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t st) {
   if (!A.kappaf) return cudaErrorInvalidValue;
   const Q1Grid g = q1_grid(A);
+  if (!e.first && A.tma) {
+    for (int c = 0; c < A.tma->ncols; ++c)
+      if (A.tma->col[c] == e.u) {
+        k_q1f_tma<<<g.grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, g.zc);
+        return cudaGetLastError();
+      }
+  }
   if (e.first) {
     if (e.dinv) k_q1f<true, true><<<g.grid, QT, 0, st>>>(A, e, g.zc);
     else k_q1f<true, false><<<g.grid, QT, 0, st>>>(A, e, g.zc);
   } else {
     k_q1f<false, false><<<g.grid, QT, 0, st>>>(A, e, g.zc);
   }
+  return cudaGetLastError();
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool encode_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+               uint64_t pitch_elems, uint32_t b0, uint32_t b1) {
+  auto enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)base & 15) != 0) return false;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {pitch_elems * 4, pitch_elems * d1 * 4};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+Q1TmaMaps* q1_tma_build(const Q1Op& A, const float* const* cols, int ncols) {
+  // rows of u must be 16-byte multiples (nx % 4 == 0); boxes no wider than the grid
+  if (A.nx % 4 != 0 || A.nx < TUW || A.ny < TUH || !A.kappaf || A.kpitch % 4 != 0 ||
+      ncols < 1 || ncols > kMaxCols)
+    return nullptr;
+  auto* m = new Q1TmaMaps{};
+  m->ncols = ncols;
+  bool ok = encode_3d(&m->mk, A.kappaf, (uint64_t)A.nx + 1, (uint64_t)A.ny + 1,
+                      (uint64_t)A.nz + 1, (uint64_t)A.kpitch, TKW, TKH);
+  for (int c = 0; ok && c < ncols; ++c) {
+    m->col[c] = cols[c];
+    ok = encode_3d(&m->mu[c], cols[c], (uint64_t)A.nx, (uint64_t)A.ny, (uint64_t)A.nz,
+                   (uint64_t)A.nx, TUW, TUH);
+  }
+  if (!ok) {
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void q1_tma_free(Q1TmaMaps* m) { delete m; }
+
+cudaError_t launch_q1_kappaf(const Q1Op& A, float* kappaf, cudaStream_t st) {
+  const int64_t total = (int64_t)(A.ny + 1) * (A.nz + 1) * A.kpitch;
+  const int64_t want = (total + kThreads - 1) / kThreads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * 8));
+  k_q1_kappaf<<<grid, kThreads, 0, st>>>(A, kappaf);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsstep.so")
 
-OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED = range(8)
+(OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED,
+ ERR_TIMEOUT) = range(9)
 MATRIX_CSR, MATRIX_STENCIL, MATRIX_Q1 = 0, 1, 2
 PREC = {"none": 0, "jacobi": 1, "amg": 2}
 ALGO = {"onesync": 0, "literal": 1, "pcg": 2}

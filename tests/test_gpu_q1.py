@@ -171,3 +171,23 @@ def test_q1_rejects_invalid():
         k[0, 0, 0] = -2.0
         with pytest.raises(sstep.SstepError):
             S.update_values(dev(k))
+
+
+@pytest.mark.parametrize("dims", [(64, 24, 20), (44, 12, 17), (40, 10, 9), (96, 33, 8)])
+def test_fp32_tma_steps_equal_plain_loads(dims, monkeypatch):
+    """nx a multiple of 4 (and the grid no smaller than the copy boxes): the middle MPK steps
+    take the tensor-memory-accelerator kernel.  It does the plain kernel's arithmetic in the
+    same order, so both give the same iterates bit for bit; the solve reaches the FP64 true
+    residual."""
+    csr, kappa, b = problem(dims, corr=4.0)
+    kw = dict(s=8, sweeps=30, rtol=1e-8, precision="fp32_rr", rr_period=8, lambda_max=1.97)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SSTEP_Q1_TMA", flag)
+        with sstep.Solver(q1(dims, kappa), **kw) as S:
+            x = torch.zeros(csr.n, dtype=torch.float64, device=DEV)
+            info = S.solve(dev(b), x)
+        out.append((info, x))
+    (i1, x1), (i0, x0) = out
+    assert i1.status == sstep.OK and i1.relres_true <= 2e-8
+    assert i1.outer_iters == i0.outer_iters and torch.equal(x1, x0)
