@@ -274,6 +274,67 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Per-thread register window of one staged plane: the 3 x 3 u values around the thread's
+// vertex column (v[dy + 1][dx + 1]), and the conductivities of its four cells in that plane
+// (k[b][a], cell (x + a, y + b)) with their in-plane pair sums.  A plane is read from shared
+// memory once and serves three vertex planes (u) or two (cells) from registers.
+struct UWin {
+  float v[3][3];
+};
+struct KWin {
+  float k[2][2];
+  float ya[2];  // ya[a] = k[0][a] + k[1][a]: the pair along y (face diagonals with dy = 0)
+  float xb[2];  // xb[b] = k[b][0] + k[b][1]: the pair along x (face diagonals with dx = 0)
+};
+
+__device__ __forceinline__ void read_plane(const float* P, const float* K, int tx, int ty,
+                                           UWin& w, KWin& c) {
+  // the u box starts at x0 - 4, y0 - 1; the cell box at x0, y0
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) w.v[dy + 1][dx + 1] = P[(ty + 1 + dy) * TUW + tx + 4 + dx];
+  c.k[0][0] = K[ty * TKW + tx];
+  c.k[0][1] = K[ty * TKW + tx + 1];
+  c.k[1][0] = K[(ty + 1) * TKW + tx];
+  c.k[1][1] = K[(ty + 1) * TKW + tx + 1];
+  c.ya[0] = c.k[0][0] + c.k[1][0];
+  c.ya[1] = c.k[0][1] + c.k[1][1];
+  c.xb[0] = c.k[0][0] + c.k[0][1];
+  c.xb[1] = c.k[1][0] + c.k[1][1];
+}
+
+// q1_vertex's arithmetic, term for term, from the windows: m, c, p = u planes z-1, z, z+1;
+// k0, k1 = cell planes z, z+1.
+__device__ __forceinline__ float q1_vertex_win(const UWin& m, const UWin& c, const UWin& p,
+                                               const KWin& k0, const KWin& k1, float& uc) {
+  const float z00 = k0.k[0][0] + k1.k[0][0], z10 = k0.k[0][1] + k1.k[0][1];
+  const float z01 = k0.k[1][0] + k1.k[1][0], z11 = k0.k[1][1] + k1.k[1][1];
+  const float k8 = (z00 + z10) + (z01 + z11);
+  float s = z00 * c.v[0][0];
+  s = fmaf(z10, c.v[0][2], s);
+  s = fmaf(z01, c.v[2][0], s);
+  s = fmaf(z11, c.v[2][2], s);
+  s = fmaf(k0.ya[0], m.v[1][0], s);
+  s = fmaf(k0.ya[1], m.v[1][2], s);
+  s = fmaf(k1.ya[0], p.v[1][0], s);
+  s = fmaf(k1.ya[1], p.v[1][2], s);
+  s = fmaf(k0.xb[0], m.v[0][1], s);
+  s = fmaf(k0.xb[1], m.v[2][1], s);
+  s = fmaf(k1.xb[0], p.v[0][1], s);
+  s = fmaf(k1.xb[1], p.v[2][1], s);
+  s = fmaf(k0.k[0][0], m.v[0][0], s);
+  s = fmaf(k0.k[0][1], m.v[0][2], s);
+  s = fmaf(k0.k[1][0], m.v[2][0], s);
+  s = fmaf(k0.k[1][1], m.v[2][2], s);
+  s = fmaf(k1.k[0][0], p.v[0][0], s);
+  s = fmaf(k1.k[0][1], p.v[0][2], s);
+  s = fmaf(k1.k[1][0], p.v[2][0], s);
+  s = fmaf(k1.k[1][1], p.v[2][2], s);
+  uc = c.v[1][1];
+  return fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
+}
+
 __global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensorMap mu,
                                                  const __grid_constant__ CUtensorMap mk, Q1Op A,
                                                  MpkF32Args e, int zc) {
@@ -283,9 +344,10 @@ __global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensor
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
-  const int np = z1 - z0 + 2;  // stage p holds u plane and cell plane z0 - 1 + p
+  const int nzc = z1 - z0;
+  const int np = nzc + 2;  // stage p holds u plane and cell plane z0 - 1 + p
   const int64_t pxy = (int64_t)nx * ny;
-  int issued = 0;              // stages issued (thread 0's count)
+  int issued = 0;          // stages issued (thread 0's count)
   auto issue = [&](int p) {
     const int slot = p % kNS;
     const uint32_t bar = smem_addr(&sh.full[slot]);
@@ -305,70 +367,64 @@ __global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensor
   const bool in = x < nx && y < ny;
   int waited = 0;  // stages 0 .. waited-1 have landed
   bool lost = false;
-  auto wait_stage = [&](int p) {
-    if (!lost && !mbar_wait(smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u)) lost = true;
-    if (!lost) waited = p + 1;
+  auto wait_stage = [&](int slot, uint32_t parity) {
+    if (!lost && !mbar_wait(smem_addr(&sh.full[slot]), parity)) lost = true;
+    if (!lost) ++waited;
   };
-  wait_stage(0);
-  wait_stage(1);
-  for (int i = 0; i < z1 - z0; ++i) {
-    const int64_t idx = (int64_t)(z0 + i) * pxy + (int64_t)y * nx + x;
-    float dv = e.dinv_u, zp = 0.0f;
-    if (in) {  // epilogue inputs, requested before the wait so that their latency overlaps it
-      if (e.dinv) dv = __ldg(e.dinv + idx);
-      if (e.zprev) zp = __ldg(e.zprev + idx);
-    }
-    wait_stage(i + 2);
-    if (!lost && in) {
-      // the u box starts at x0 - 4, y0 - 1: shift the staged planes to q1_vertex's layout
-      const float* Um = sh.u[i % kNS];
-      const float* Uc = sh.u[(i + 1) % kNS];
-      const float* Up = sh.u[(i + 2) % kNS];
-      const float* K0 = sh.k[(i + 1) % kNS];
-      const float* K1 = sh.k[(i + 2) % kNS];
-      auto U = [&](const float* P, int dx, int dy) -> float {
-        return P[(ty + 1 + dy) * TUW + tx + 4 + dx];
-      };
-      auto C = [&](const float* P, int a, int b) -> float { return P[(ty + b) * TKW + tx + a]; };
-      const float k000 = C(K0, 0, 0), k100 = C(K0, 1, 0), k010 = C(K0, 0, 1), k110 = C(K0, 1, 1);
-      const float k001 = C(K1, 0, 0), k101 = C(K1, 1, 0), k011 = C(K1, 0, 1), k111 = C(K1, 1, 1);
-      const float z00 = k000 + k001, z10 = k100 + k101, z01 = k010 + k011, z11 = k110 + k111;
-      const float y00 = k000 + k010, y10 = k100 + k110, y01 = k001 + k011, y11 = k101 + k111;
-      const float x00 = k000 + k100, x10 = k010 + k110, x01 = k001 + k101, x11 = k011 + k111;
-      const float k8 = (z00 + z10) + (z01 + z11);
-      float s = z00 * U(Uc, -1, -1);
-      s = fmaf(z10, U(Uc, 1, -1), s);
-      s = fmaf(z01, U(Uc, -1, 1), s);
-      s = fmaf(z11, U(Uc, 1, 1), s);
-      s = fmaf(y00, U(Um, -1, 0), s);
-      s = fmaf(y10, U(Um, 1, 0), s);
-      s = fmaf(y01, U(Up, -1, 0), s);
-      s = fmaf(y11, U(Up, 1, 0), s);
-      s = fmaf(x00, U(Um, 0, -1), s);
-      s = fmaf(x10, U(Um, 0, 1), s);
-      s = fmaf(x01, U(Up, 0, -1), s);
-      s = fmaf(x11, U(Up, 0, 1), s);
-      s = fmaf(k000, U(Um, -1, -1), s);
-      s = fmaf(k100, U(Um, 1, -1), s);
-      s = fmaf(k010, U(Um, -1, 1), s);
-      s = fmaf(k110, U(Um, 1, 1), s);
-      s = fmaf(k001, U(Up, -1, -1), s);
-      s = fmaf(k101, U(Up, 1, -1), s);
-      s = fmaf(k011, U(Up, -1, 1), s);
-      s = fmaf(k111, U(Up, 1, 1), s);
-      const float uc = U(Uc, 0, 0);
-      const float yv = fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
-      e.y[idx] = yv;  // A z_q
-      if (e.znext) {
-        const float t = e.zprev ? -zp : 0.0f;
-        e.znext[idx] = fmaf(e.c1 * dv, yv, fmaf(-e.c2, uc, t));
-      }
-    }
-    // stage i (plane z - 1) is read for the last time: refill its slot kNS planes ahead
-    if (__syncthreads_or(lost)) break;
-    if (tid == 0 && i + kNS < np) issue(i + kNS);
+  UWin uw[3];  // stage p in uw[p % 3]
+  KWin kw[2];  // stage p in kw[p % 2]
+  int64_t idx = (int64_t)z0 * pxy + (int64_t)y * nx + x;
+  float dv = e.dinv_u, zp = 0.0f;  // epilogue inputs of the current plane
+  if (in) {
+    if (e.dinv) dv = __ldg(e.dinv + idx);
+    if (e.zprev) zp = __ldg(e.zprev + idx);
   }
-  if (lost && tid == 0) {
+  wait_stage(0, 0);
+  wait_stage(1, 0);
+  if (!lost) {
+    read_plane(sh.u[0], sh.k[0], tx, ty, uw[0], kw[0]);
+    read_plane(sh.u[1], sh.k[1], tx, ty, uw[1], kw[1]);
+  }
+  bool stop = __syncthreads_or(lost);
+  if (!stop && tid == 0)
+    for (int p = kNS; p < min(kNS + 2, np); ++p) issue(p);
+  uint32_t ph = 0;  // phase parity of the stages in the current round of kNS
+  // unrolled by kNS (a multiple of both window periods): slots and windows are constants
+  for (int i0 = 0; i0 < nzc && !stop; i0 += kNS, ph ^= 1u) {
+#pragma unroll
+    for (int j = 0; j < kNS; ++j) {
+      const int i = i0 + j;
+      if (i >= nzc || stop) break;
+      float dvn = e.dinv_u, zpn = 0.0f;  // next plane's epilogue inputs, requested early
+      if (in && i + 1 < nzc) {
+        if (e.dinv) dvn = __ldg(e.dinv + idx + pxy);
+        if (e.zprev) zpn = __ldg(e.zprev + idx + pxy);
+      }
+      constexpr int kFill = 2;  // stage i + 2 enters the windows in iteration i
+      wait_stage((j + kFill) % kNS, ph ^ (uint32_t)((j + kFill) / kNS));
+      if (!lost)
+        read_plane(sh.u[(j + kFill) % kNS], sh.k[(j + kFill) % kNS], tx, ty, uw[(j + 2) % 3],
+                   kw[j % 2]);
+      // every thread has its copy of stage i + 2: refill that slot kNS stages ahead
+      stop = __syncthreads_or(lost);
+      if (stop) break;
+      if (tid == 0 && i + kFill + kNS < np) issue(i + kFill + kNS);
+      if (in) {
+        float uc;
+        const float yv = q1_vertex_win(uw[j % 3], uw[(j + 1) % 3], uw[(j + 2) % 3],
+                                       kw[(j + 1) % 2], kw[j % 2], uc);
+        e.y[idx] = yv;  // A z_q
+        if (e.znext) {
+          const float t = e.zprev ? -zp : 0.0f;
+          e.znext[idx] = fmaf(e.c1 * dv, yv, fmaf(-e.c2, uc, t));
+        }
+      }
+      dv = dvn;
+      zp = zpn;
+      idx += pxy;
+    }
+  }
+  if (stop && tid == 0) {
     // let the copies still in flight land before the CTA's shared memory is released
     for (int p = waited; p < issued; ++p)
       mbar_wait(smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u);
