@@ -64,26 +64,29 @@ __device__ __forceinline__ T q1_vertex(const T* Um, const T* Uc, const T* Up, co
   const T y00 = k000 + k010, y10 = k100 + k110, y01 = k001 + k011, y11 = k101 + k111;  // dy = 0
   const T x00 = k000 + k100, x10 = k010 + k110, x01 = k001 + k101, x11 = k011 + k111;  // dx = 0
   const T k8 = (z00 + z10) + (z01 + z11);
-  T s = z00 * U(Uc, -1, -1);
-  s = fmaT(z10, U(Uc, 1, -1), s);
-  s = fmaT(z01, U(Uc, -1, 1), s);
-  s = fmaT(z11, U(Uc, 1, 1), s);
-  s = fmaT(y00, U(Um, -1, 0), s);
-  s = fmaT(y10, U(Um, 1, 0), s);
-  s = fmaT(y01, U(Up, -1, 0), s);
-  s = fmaT(y11, U(Up, 1, 0), s);
-  s = fmaT(x00, U(Um, 0, -1), s);
-  s = fmaT(x10, U(Um, 0, 1), s);
-  s = fmaT(x01, U(Up, 0, -1), s);
-  s = fmaT(x11, U(Up, 0, 1), s);
-  s = fmaT(k000, U(Um, -1, -1), s);
-  s = fmaT(k100, U(Um, 1, -1), s);
-  s = fmaT(k010, U(Um, -1, 1), s);
-  s = fmaT(k110, U(Um, 1, 1), s);
-  s = fmaT(k001, U(Up, -1, -1), s);
-  s = fmaT(k101, U(Up, 1, -1), s);
-  s = fmaT(k011, U(Up, -1, 1), s);
-  s = fmaT(k111, U(Up, 1, 1), s);
+  // four independent partial sums (face diagonals in the plane, along y, along x; body
+  // diagonals) keep the dependent chain short
+  T sa = z00 * U(Uc, -1, -1);
+  T sb = y00 * U(Um, -1, 0);
+  T sc = x00 * U(Um, 0, -1);
+  T sd = k000 * U(Um, -1, -1);
+  T se = k001 * U(Up, -1, -1);
+  sa = fmaT(z10, U(Uc, 1, -1), sa);
+  sb = fmaT(y10, U(Um, 1, 0), sb);
+  sc = fmaT(x10, U(Um, 0, 1), sc);
+  sd = fmaT(k100, U(Um, 1, -1), sd);
+  se = fmaT(k101, U(Up, 1, -1), se);
+  sa = fmaT(z01, U(Uc, -1, 1), sa);
+  sb = fmaT(y01, U(Up, -1, 0), sb);
+  sc = fmaT(x01, U(Up, 0, -1), sc);
+  sd = fmaT(k010, U(Um, -1, 1), sd);
+  se = fmaT(k011, U(Up, -1, 1), se);
+  sa = fmaT(z11, U(Uc, 1, 1), sa);
+  sb = fmaT(y11, U(Up, 1, 0), sb);
+  sc = fmaT(x11, U(Up, 0, 1), sc);
+  sd = fmaT(k110, U(Um, 1, 1), sd);
+  se = fmaT(k111, U(Up, 1, 1), se);
+  const T s = (sa + sb) + (sc + (sd + se));
   uc = U(Uc, 0, 0);
   const T third = T(1) / T(3), twelfth = T(1) / T(12);
   return fmaT(k8 * third, uc, -(s * twelfth));
@@ -311,26 +314,27 @@ __device__ __forceinline__ float q1_vertex_win(const UWin& m, const UWin& c, con
   const float z00 = k0.k[0][0] + k1.k[0][0], z10 = k0.k[0][1] + k1.k[0][1];
   const float z01 = k0.k[1][0] + k1.k[1][0], z11 = k0.k[1][1] + k1.k[1][1];
   const float k8 = (z00 + z10) + (z01 + z11);
-  float s = z00 * c.v[0][0];
-  s = fmaf(z10, c.v[0][2], s);
-  s = fmaf(z01, c.v[2][0], s);
-  s = fmaf(z11, c.v[2][2], s);
-  s = fmaf(k0.ya[0], m.v[1][0], s);
-  s = fmaf(k0.ya[1], m.v[1][2], s);
-  s = fmaf(k1.ya[0], p.v[1][0], s);
-  s = fmaf(k1.ya[1], p.v[1][2], s);
-  s = fmaf(k0.xb[0], m.v[0][1], s);
-  s = fmaf(k0.xb[1], m.v[2][1], s);
-  s = fmaf(k1.xb[0], p.v[0][1], s);
-  s = fmaf(k1.xb[1], p.v[2][1], s);
-  s = fmaf(k0.k[0][0], m.v[0][0], s);
-  s = fmaf(k0.k[0][1], m.v[0][2], s);
-  s = fmaf(k0.k[1][0], m.v[2][0], s);
-  s = fmaf(k0.k[1][1], m.v[2][2], s);
-  s = fmaf(k1.k[0][0], p.v[0][0], s);
-  s = fmaf(k1.k[0][1], p.v[0][2], s);
-  s = fmaf(k1.k[1][0], p.v[2][0], s);
-  s = fmaf(k1.k[1][1], p.v[2][2], s);
+  float sa = z00 * c.v[0][0];
+  float sb = k0.ya[0] * m.v[1][0];
+  float sc = k0.xb[0] * m.v[0][1];
+  float sd = k0.k[0][0] * m.v[0][0];
+  float se = k1.k[0][0] * p.v[0][0];
+  sa = fmaf(z10, c.v[0][2], sa);
+  sb = fmaf(k0.ya[1], m.v[1][2], sb);
+  sc = fmaf(k0.xb[1], m.v[2][1], sc);
+  sd = fmaf(k0.k[0][1], m.v[0][2], sd);
+  se = fmaf(k1.k[0][1], p.v[0][2], se);
+  sa = fmaf(z01, c.v[2][0], sa);
+  sb = fmaf(k1.ya[0], p.v[1][0], sb);
+  sc = fmaf(k1.xb[0], p.v[0][1], sc);
+  sd = fmaf(k0.k[1][0], m.v[2][0], sd);
+  se = fmaf(k1.k[1][0], p.v[2][0], se);
+  sa = fmaf(z11, c.v[2][2], sa);
+  sb = fmaf(k1.ya[1], p.v[1][2], sb);
+  sc = fmaf(k1.xb[1], p.v[2][1], sc);
+  sd = fmaf(k0.k[1][1], m.v[2][2], sd);
+  se = fmaf(k1.k[1][1], p.v[2][2], se);
+  const float s = (sa + sb) + (sc + (sd + se));
   uc = c.v[1][1];
   return fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
 }
@@ -574,7 +578,21 @@ cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t s
   if (!e.first && A.tma) {
     for (int c = 0; c < A.tma->ncols; ++c)
       if (A.tma->col[c] == e.u) {
-        k_q1f_tma<<<g.grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, g.zc);
+        // one wave of resident CTAs, each marching a long z chunk: the pipeline fill (the
+        // first two planes' latency) is paid once per CTA
+        static int per_sm = 0;
+        if (!per_sm) {
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1f_tma, QT, 0) !=
+                  cudaSuccess ||
+              per_sm < 1)
+            per_sm = 1;
+        }
+        const int tiles = (int)(g.grid.x * g.grid.y);
+        int64_t gz = std::max<int64_t>(1, (int64_t)sms() * per_sm / tiles);
+        gz = std::min<int64_t>(gz, std::max(1, A.nz / 8));
+        const int zc = (int)((A.nz + gz - 1) / gz);
+        const dim3 grid(g.grid.x, g.grid.y, (A.nz + zc - 1) / zc);
+        k_q1f_tma<<<grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, zc);
         return cudaGetLastError();
       }
   }
