@@ -64,29 +64,26 @@ __device__ __forceinline__ T q1_vertex(const T* Um, const T* Uc, const T* Up, co
   const T y00 = k000 + k010, y10 = k100 + k110, y01 = k001 + k011, y11 = k101 + k111;  // dy = 0
   const T x00 = k000 + k100, x10 = k010 + k110, x01 = k001 + k101, x11 = k011 + k111;  // dx = 0
   const T k8 = (z00 + z10) + (z01 + z11);
-  // four independent partial sums (face diagonals in the plane, along y, along x; body
-  // diagonals) keep the dependent chain short
-  T sa = z00 * U(Uc, -1, -1);
-  T sb = y00 * U(Um, -1, 0);
-  T sc = x00 * U(Um, 0, -1);
-  T sd = k000 * U(Um, -1, -1);
-  T se = k001 * U(Up, -1, -1);
-  sa = fmaT(z10, U(Uc, 1, -1), sa);
-  sb = fmaT(y10, U(Um, 1, 0), sb);
-  sc = fmaT(x10, U(Um, 0, 1), sc);
-  sd = fmaT(k100, U(Um, 1, -1), sd);
-  se = fmaT(k101, U(Up, 1, -1), se);
-  sa = fmaT(z01, U(Uc, -1, 1), sa);
-  sb = fmaT(y01, U(Up, -1, 0), sb);
-  sc = fmaT(x01, U(Up, 0, -1), sc);
-  sd = fmaT(k010, U(Um, -1, 1), sd);
-  se = fmaT(k011, U(Up, -1, 1), se);
-  sa = fmaT(z11, U(Uc, 1, 1), sa);
-  sb = fmaT(y11, U(Up, 1, 0), sb);
-  sc = fmaT(x11, U(Up, 0, 1), sc);
-  sd = fmaT(k110, U(Um, 1, 1), sd);
-  se = fmaT(k111, U(Up, 1, 1), se);
-  const T s = (sa + sb) + (sc + (sd + se));
+  T s = z00 * U(Uc, -1, -1);
+  s = fmaT(z10, U(Uc, 1, -1), s);
+  s = fmaT(z01, U(Uc, -1, 1), s);
+  s = fmaT(z11, U(Uc, 1, 1), s);
+  s = fmaT(y00, U(Um, -1, 0), s);
+  s = fmaT(y10, U(Um, 1, 0), s);
+  s = fmaT(y01, U(Up, -1, 0), s);
+  s = fmaT(y11, U(Up, 1, 0), s);
+  s = fmaT(x00, U(Um, 0, -1), s);
+  s = fmaT(x10, U(Um, 0, 1), s);
+  s = fmaT(x01, U(Up, 0, -1), s);
+  s = fmaT(x11, U(Up, 0, 1), s);
+  s = fmaT(k000, U(Um, -1, -1), s);
+  s = fmaT(k100, U(Um, 1, -1), s);
+  s = fmaT(k010, U(Um, -1, 1), s);
+  s = fmaT(k110, U(Um, 1, 1), s);
+  s = fmaT(k001, U(Up, -1, -1), s);
+  s = fmaT(k101, U(Up, 1, -1), s);
+  s = fmaT(k011, U(Up, -1, 1), s);
+  s = fmaT(k111, U(Up, 1, 1), s);
   uc = U(Uc, 0, 0);
   const T third = T(1) / T(3), twelfth = T(1) / T(12);
   return fmaT(k8 * third, uc, -(s * twelfth));
@@ -219,18 +216,21 @@ __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
 
 // ---------------------------------------------------------------- TMA-fed FP32 MPK step
 
-// Middle MPK steps of the FP32 path (input not scaled by M^{-1}): one thread issues, per z
-// plane, a 3D tiled copy of the u plane with its halo (a 40 x 10 box that starts 4 vertices left
-// of the tile, so that the x coordinate stays a multiple of 16 bytes) and one of the
-// conductivity plane (36 x 9 cells); both complete on the stage's mbarrier.  kNS stages keep
-// three planes in flight ahead of the three being read.  The copy zero-fills whatever lies
-// outside the grid, which is exactly the eliminated Dirichlet boundary.  Every wait is bounded:
-// a copy that never lands stops the solve with SSTEP_ERR_TIMEOUT instead of hanging.
-constexpr int TUW = 40, TUH = 10;  // u box (vertices)
-constexpr int TKW = 36, TKH = 9;   // conductivity box (cells)
+// Middle MPK steps of the FP32 path (input not scaled by M^{-1}).  A CTA owns 64 x 8 vertices
+// (two x-adjacent vertices per thread) and marches a z chunk.  One thread issues, per z plane,
+// a 3D tiled copy of the u plane with its halo (a 72 x 10 box that starts 4 vertices left of
+// the tile, so that the x coordinate stays a multiple of 16 bytes) and one of the conductivity
+// plane (68 x 9 cells); both complete on the stage's mbarrier.  The copy zero-fills whatever
+// lies outside the grid, which is exactly the eliminated Dirichlet boundary.  Each thread reads
+// a landed plane from shared memory once into a register window that serves three vertex
+// planes (u) or two (cells), after which the slot is refilled kNS planes ahead.  Every wait is
+// bounded: a copy that never lands stops the solve with SSTEP_ERR_TIMEOUT instead of hanging.
+constexpr int TBX = 64;            // vertices per CTA along x (two per thread)
+constexpr int TUW = 72, TUH = 10;  // u box (vertices)
+constexpr int TKW = 68, TKH = 9;   // conductivity box (cells)
 constexpr int kNS = 6;             // pipeline stages (z planes)
-constexpr int kUStage = 416;       // floats per u stage: 400 used, 1664 bytes (13 x 128)
-constexpr int kKStage = 352;       // floats per cell stage: 324 used, 1408 bytes (11 x 128)
+constexpr int kUStage = 736;       // floats per u stage: 720 used, 2944 bytes (23 x 128)
+constexpr int kKStage = 640;       // floats per cell stage: 612 used, 2560 bytes (20 x 128)
 constexpr uint32_t kStageBytes = (TUW * TUH + TKW * TKH) * 4;
 constexpr uint32_t kWaitRounds = 1u << 22;  // try_wait rounds before a copy counts as lost
 
@@ -277,76 +277,88 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Per-thread register window of one staged plane: the 3 x 3 u values around the thread's
-// vertex column (v[dy + 1][dx + 1]), and the conductivities of its four cells in that plane
-// (k[b][a], cell (x + a, y + b)) with their in-plane pair sums.  A plane is read from shared
-// memory once and serves three vertex planes (u) or two (cells) from registers.
-struct UWin {
-  float v[3][3];
+// Register window of one staged plane for a thread's two vertices (x and x + 1): u at rows
+// y-1..y+1 and columns x-1..x+2 (v[dy + 1][c]); the conductivities of cells x..x+2 at rows
+// y, y+1 (k[b][a]) with their in-plane pair sums.
+struct UWin2 {
+  float v[3][4];
 };
-struct KWin {
-  float k[2][2];
-  float ya[2];  // ya[a] = k[0][a] + k[1][a]: the pair along y (face diagonals with dy = 0)
-  float xb[2];  // xb[b] = k[b][0] + k[b][1]: the pair along x (face diagonals with dx = 0)
+struct KWin2 {
+  float k[2][3];
+  float ya[3];     // ya[a] = k[0][a] + k[1][a]: the pair along y of cell column a
+  float xb[2][2];  // xb[d][b] = k[b][d] + k[b][d + 1]: the pair along x of vertex d, row b
 };
 
-__device__ __forceinline__ void read_plane(const float* P, const float* K, int tx, int ty,
-                                           UWin& w, KWin& c) {
-  // the u box starts at x0 - 4, y0 - 1; the cell box at x0, y0
+__device__ __forceinline__ void read_plane2(const float* P, const float* K, int tx, int ty,
+                                            UWin2& w, KWin2& c) {
+  // vertex x0 + 2 tx is column 2 tx + 4 of the u box and column 2 tx of the cell box
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
+  for (int r = 0; r < 3; ++r) {
+    const float* row = P + (ty + r) * TUW + 2 * tx + 3;
+    w.v[r][0] = row[0];
+    const float2 mid = *reinterpret_cast<const float2*>(row + 1);
+    w.v[r][1] = mid.x;
+    w.v[r][2] = mid.y;
+    w.v[r][3] = row[3];
+  }
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) w.v[dy + 1][dx + 1] = P[(ty + 1 + dy) * TUW + tx + 4 + dx];
-  c.k[0][0] = K[ty * TKW + tx];
-  c.k[0][1] = K[ty * TKW + tx + 1];
-  c.k[1][0] = K[(ty + 1) * TKW + tx];
-  c.k[1][1] = K[(ty + 1) * TKW + tx + 1];
-  c.ya[0] = c.k[0][0] + c.k[1][0];
-  c.ya[1] = c.k[0][1] + c.k[1][1];
-  c.xb[0] = c.k[0][0] + c.k[0][1];
-  c.xb[1] = c.k[1][0] + c.k[1][1];
+  for (int b = 0; b < 2; ++b) {
+    const float* row = K + (ty + b) * TKW + 2 * tx;
+    const float2 lo = *reinterpret_cast<const float2*>(row);
+    c.k[b][0] = lo.x;
+    c.k[b][1] = lo.y;
+    c.k[b][2] = row[2];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c.ya[a] = c.k[0][a] + c.k[1][a];
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) c.xb[d][b] = c.k[b][d] + c.k[b][d + 1];
 }
 
-// q1_vertex's arithmetic, term for term, from the windows: m, c, p = u planes z-1, z, z+1;
-// k0, k1 = cell planes z, z+1.
-__device__ __forceinline__ float q1_vertex_win(const UWin& m, const UWin& c, const UWin& p,
-                                               const KWin& k0, const KWin& k1, float& uc) {
-  const float z00 = k0.k[0][0] + k1.k[0][0], z10 = k0.k[0][1] + k1.k[0][1];
-  const float z01 = k0.k[1][0] + k1.k[1][0], z11 = k0.k[1][1] + k1.k[1][1];
+// q1_vertex's arithmetic, term for term, for vertex D of the pair: m, c, p = u planes z-1, z,
+// z+1; k0, k1 = cell planes z, z+1.
+template <int D>
+__device__ __forceinline__ float q1_vertex_win(const UWin2& m, const UWin2& c, const UWin2& p,
+                                               const KWin2& k0, const KWin2& k1, float& uc) {
+  auto U = [](const UWin2& w, int dx, int dy) -> float { return w.v[dy + 1][D + 1 + dx]; };
+  const float k000 = k0.k[0][D], k100 = k0.k[0][D + 1], k010 = k0.k[1][D], k110 = k0.k[1][D + 1];
+  const float k001 = k1.k[0][D], k101 = k1.k[0][D + 1], k011 = k1.k[1][D], k111 = k1.k[1][D + 1];
+  const float z00 = k000 + k001, z10 = k100 + k101, z01 = k010 + k011, z11 = k110 + k111;
   const float k8 = (z00 + z10) + (z01 + z11);
-  float sa = z00 * c.v[0][0];
-  float sb = k0.ya[0] * m.v[1][0];
-  float sc = k0.xb[0] * m.v[0][1];
-  float sd = k0.k[0][0] * m.v[0][0];
-  float se = k1.k[0][0] * p.v[0][0];
-  sa = fmaf(z10, c.v[0][2], sa);
-  sb = fmaf(k0.ya[1], m.v[1][2], sb);
-  sc = fmaf(k0.xb[1], m.v[2][1], sc);
-  sd = fmaf(k0.k[0][1], m.v[0][2], sd);
-  se = fmaf(k1.k[0][1], p.v[0][2], se);
-  sa = fmaf(z01, c.v[2][0], sa);
-  sb = fmaf(k1.ya[0], p.v[1][0], sb);
-  sc = fmaf(k1.xb[0], p.v[0][1], sc);
-  sd = fmaf(k0.k[1][0], m.v[2][0], sd);
-  se = fmaf(k1.k[1][0], p.v[2][0], se);
-  sa = fmaf(z11, c.v[2][2], sa);
-  sb = fmaf(k1.ya[1], p.v[1][2], sb);
-  sc = fmaf(k1.xb[1], p.v[2][1], sc);
-  sd = fmaf(k0.k[1][1], m.v[2][2], sd);
-  se = fmaf(k1.k[1][1], p.v[2][2], se);
-  const float s = (sa + sb) + (sc + (sd + se));
-  uc = c.v[1][1];
+  float s = z00 * U(c, -1, -1);
+  s = fmaf(z10, U(c, 1, -1), s);
+  s = fmaf(z01, U(c, -1, 1), s);
+  s = fmaf(z11, U(c, 1, 1), s);
+  s = fmaf(k0.ya[D], U(m, -1, 0), s);      // y00
+  s = fmaf(k0.ya[D + 1], U(m, 1, 0), s);   // y10
+  s = fmaf(k1.ya[D], U(p, -1, 0), s);      // y01
+  s = fmaf(k1.ya[D + 1], U(p, 1, 0), s);   // y11
+  s = fmaf(k0.xb[D][0], U(m, 0, -1), s);   // x00
+  s = fmaf(k0.xb[D][1], U(m, 0, 1), s);    // x10
+  s = fmaf(k1.xb[D][0], U(p, 0, -1), s);   // x01
+  s = fmaf(k1.xb[D][1], U(p, 0, 1), s);    // x11
+  s = fmaf(k000, U(m, -1, -1), s);
+  s = fmaf(k100, U(m, 1, -1), s);
+  s = fmaf(k010, U(m, -1, 1), s);
+  s = fmaf(k110, U(m, 1, 1), s);
+  s = fmaf(k001, U(p, -1, -1), s);
+  s = fmaf(k101, U(p, 1, -1), s);
+  s = fmaf(k011, U(p, -1, 1), s);
+  s = fmaf(k111, U(p, 1, 1), s);
+  uc = U(c, 0, 0);
   return fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
 }
 
-__global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensorMap mu,
+__global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUtensorMap mu,
                                                  const __grid_constant__ CUtensorMap mk, Q1Op A,
                                                  MpkF32Args e, int zc) {
   if (e.ctrl && e.ctrl->done) return;
   __shared__ TmaSmem sh;
   const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
+  const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * QY;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
   const int nzc = z1 - z0;
   const int np = nzc + 2;  // stage p holds u plane and cell plane z0 - 1 + p
@@ -367,27 +379,27 @@ __global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensor
   __syncthreads();
   if (tid == 0)
     for (int p = 0; p < min(kNS, np); ++p) issue(p);
-  const int x = x0 + tx, y = y0 + ty;
-  const bool in = x < nx && y < ny;
-  int waited = 0;  // stages 0 .. waited-1 have landed
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool in = x < nx && y < ny;  // nx is even: x + 1 < nx too
+  int waited = 0;                    // stages 0 .. waited-1 have landed
   bool lost = false;
   auto wait_stage = [&](int slot, uint32_t parity) {
     if (!lost && !mbar_wait(smem_addr(&sh.full[slot]), parity)) lost = true;
     if (!lost) ++waited;
   };
-  UWin uw[3];  // stage p in uw[p % 3]
-  KWin kw[2];  // stage p in kw[p % 2]
-  int64_t idx = (int64_t)z0 * pxy + (int64_t)y * nx + x;
-  float dv = e.dinv_u, zp = 0.0f;  // epilogue inputs of the current plane
+  UWin2 uw[3];  // stage p in uw[p % 3]
+  KWin2 kw[2];  // stage p in kw[p % 2]
+  int64_t idx = (int64_t)z0 * pxy + (int64_t)y * nx + x;  // even: 8-byte aligned pairs
+  float2 dv = make_float2(e.dinv_u, e.dinv_u), zp = make_float2(0.0f, 0.0f);
   if (in) {
-    if (e.dinv) dv = __ldg(e.dinv + idx);
-    if (e.zprev) zp = __ldg(e.zprev + idx);
+    if (e.dinv) dv = __ldg(reinterpret_cast<const float2*>(e.dinv + idx));
+    if (e.zprev) zp = __ldg(reinterpret_cast<const float2*>(e.zprev + idx));
   }
   wait_stage(0, 0);
   wait_stage(1, 0);
   if (!lost) {
-    read_plane(sh.u[0], sh.k[0], tx, ty, uw[0], kw[0]);
-    read_plane(sh.u[1], sh.k[1], tx, ty, uw[1], kw[1]);
+    read_plane2(sh.u[0], sh.k[0], tx, ty, uw[0], kw[0]);
+    read_plane2(sh.u[1], sh.k[1], tx, ty, uw[1], kw[1]);
   }
   bool stop = __syncthreads_or(lost);
   if (!stop && tid == 0)
@@ -399,28 +411,33 @@ __global__ void __launch_bounds__(QT) k_q1f_tma(const __grid_constant__ CUtensor
     for (int j = 0; j < kNS; ++j) {
       const int i = i0 + j;
       if (i >= nzc || stop) break;
-      float dvn = e.dinv_u, zpn = 0.0f;  // next plane's epilogue inputs, requested early
-      if (in && i + 1 < nzc) {
-        if (e.dinv) dvn = __ldg(e.dinv + idx + pxy);
-        if (e.zprev) zpn = __ldg(e.zprev + idx + pxy);
+      float2 dvn = make_float2(e.dinv_u, e.dinv_u), zpn = make_float2(0.0f, 0.0f);
+      if (in && i + 1 < nzc) {  // next plane's epilogue inputs, requested early
+        if (e.dinv) dvn = __ldg(reinterpret_cast<const float2*>(e.dinv + idx + pxy));
+        if (e.zprev) zpn = __ldg(reinterpret_cast<const float2*>(e.zprev + idx + pxy));
       }
       constexpr int kFill = 2;  // stage i + 2 enters the windows in iteration i
       wait_stage((j + kFill) % kNS, ph ^ (uint32_t)((j + kFill) / kNS));
       if (!lost)
-        read_plane(sh.u[(j + kFill) % kNS], sh.k[(j + kFill) % kNS], tx, ty, uw[(j + 2) % 3],
-                   kw[j % 2]);
+        read_plane2(sh.u[(j + kFill) % kNS], sh.k[(j + kFill) % kNS], tx, ty, uw[(j + 2) % 3],
+                    kw[j % 2]);
       // every thread has its copy of stage i + 2: refill that slot kNS stages ahead
       stop = __syncthreads_or(lost);
       if (stop) break;
       if (tid == 0 && i + kFill + kNS < np) issue(i + kFill + kNS);
       if (in) {
-        float uc;
-        const float yv = q1_vertex_win(uw[j % 3], uw[(j + 1) % 3], uw[(j + 2) % 3],
-                                       kw[(j + 1) % 2], kw[j % 2], uc);
-        e.y[idx] = yv;  // A z_q
+        float2 yv, uc;
+        yv.x = q1_vertex_win<0>(uw[j % 3], uw[(j + 1) % 3], uw[(j + 2) % 3], kw[(j + 1) % 2],
+                                kw[j % 2], uc.x);
+        yv.y = q1_vertex_win<1>(uw[j % 3], uw[(j + 1) % 3], uw[(j + 2) % 3], kw[(j + 1) % 2],
+                                kw[j % 2], uc.y);
+        *reinterpret_cast<float2*>(e.y + idx) = yv;  // A z_q
         if (e.znext) {
-          const float t = e.zprev ? -zp : 0.0f;
-          e.znext[idx] = fmaf(e.c1 * dv, yv, fmaf(-e.c2, uc, t));
+          const float2 t = e.zprev ? make_float2(-zp.x, -zp.y) : make_float2(0.0f, 0.0f);
+          float2 zn;
+          zn.x = fmaf(e.c1 * dv.x, yv.x, fmaf(-e.c2, uc.x, t.x));
+          zn.y = fmaf(e.c1 * dv.y, yv.y, fmaf(-e.c2, uc.y, t.y));
+          *reinterpret_cast<float2*>(e.znext + idx) = zn;
         }
       }
       dv = dvn;
@@ -587,11 +604,11 @@ cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t s
               per_sm < 1)
             per_sm = 1;
         }
-        const int tiles = (int)(g.grid.x * g.grid.y);
-        int64_t gz = std::max<int64_t>(1, (int64_t)sms() * per_sm / tiles);
+        const int gx = (A.nx + TBX - 1) / TBX, gy = (A.ny + QY - 1) / QY;
+        int64_t gz = std::max<int64_t>(1, (int64_t)sms() * per_sm / std::max(1, gx * gy));
         gz = std::min<int64_t>(gz, std::max(1, A.nz / 8));
         const int zc = (int)((A.nz + gz - 1) / gz);
-        const dim3 grid(g.grid.x, g.grid.y, (A.nz + zc - 1) / zc);
+        const dim3 grid(gx, gy, (A.nz + zc - 1) / zc);
         k_q1f_tma<<<grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, zc);
         return cudaGetLastError();
       }
@@ -640,9 +657,9 @@ bool encode_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint6
 }  // namespace
 
 Q1TmaMaps* q1_tma_build(const Q1Op& A, const float* const* cols, int ncols) {
-  // rows of u must be 16-byte multiples (nx % 4 == 0); boxes no wider than the grid
-  if (A.nx % 4 != 0 || A.nx < TUW || A.ny < TUH || !A.kappaf || A.kpitch % 4 != 0 ||
-      ncols < 1 || ncols > kMaxCols)
+  // rows of u must be 16-byte multiples (nx % 4 == 0); boxes no larger than the grid
+  if (A.nx % 4 != 0 || A.nx < TUW || A.ny < TUH || A.nx + 1 < TKW || !A.kappaf ||
+      A.kpitch % 4 != 0 || ncols < 1 || ncols > kMaxCols)
     return nullptr;
   auto* m = new Q1TmaMaps{};
   m->ncols = ncols;
