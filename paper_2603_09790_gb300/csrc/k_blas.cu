@@ -848,9 +848,49 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
   if (!FIRST)
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
   __syncthreads();
-  const int64_t ld = a.ld;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // four consecutive points per thread and trip: 16-byte loads and stores
+  const int64_t n4 = a.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        reinterpret_cast<float4*>(a.Q + j * ld)[v] =
+            __ldg(reinterpret_cast<const float4*>(a.Z + j * ld) + v);
+        reinterpret_cast<float4*>(a.AQ + j * ld)[v] =
+            __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+      }
+    } else {
+      float4 qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = reinterpret_cast<const float4*>(a.Q + l * ld)[v];
+        ao[l] = reinterpret_cast<const float4*>(a.AQ + l * ld)[v];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float4 vq = __ldg(reinterpret_cast<const float4*>(a.Z + j * ld) + v);
+        float4 va = __ldg(reinterpret_cast<const float4*>(a.AZ + j * ld) + v);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const float bl = sb[l + j * S];
+          vq.x = fmaf(qo[l].x, bl, vq.x);
+          vq.y = fmaf(qo[l].y, bl, vq.y);
+          vq.z = fmaf(qo[l].z, bl, vq.z);
+          vq.w = fmaf(qo[l].w, bl, vq.w);
+          va.x = fmaf(ao[l].x, bl, va.x);
+          va.y = fmaf(ao[l].y, bl, va.y);
+          va.z = fmaf(ao[l].z, bl, va.z);
+          va.w = fmaf(ao[l].w, bl, va.w);
+        }
+        reinterpret_cast<float4*>(a.Q + j * ld)[v] = vq;
+        reinterpret_cast<float4*>(a.AQ + j * ld)[v] = va;
+      }
+    }
+  }
+  for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
     if constexpr (FIRST) {
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -898,24 +938,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
   float hi[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    float xv[NR], yv[NC], yl[NC];
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // four consecutive points per thread and trip (columns are 16-byte aligned): more bytes in
+  // flight per thread, one set of index computations per four points
+  const int64_t n4 = g.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 xv[NR], yv[NC];
+    float4 yl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) xv[i] = __ldg(reinterpret_cast<const float4*>(xp[i]) + v);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) yv[j] = __ldg(reinterpret_cast<const float4*>(yp[j]) + v);
+    if (ylo) yl = __ldg(reinterpret_cast<const float4*>(ylo) + v);
+#define SSTEP_DF_LANE(c)                                                          \
+    _Pragma("unroll") for (int i = 0; i < NR; ++i) {                              \
+      _Pragma("unroll") for (int j = 0; j < NC; ++j)                              \
+        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i].c, yv[j].c);            \
+      lo[i * NC + NC - 1] = fmaf(xv[i].c, yl.c, lo[i * NC + NC - 1]);             \
+    }
+    SSTEP_DF_LANE(x)
+    SSTEP_DF_LANE(y)
+    SSTEP_DF_LANE(z)
+    SSTEP_DF_LANE(w)
+#undef SSTEP_DF_LANE
+  }
+  for (int64_t p = 4 * n4 + gid; p < g.n; p += stride) {  // the last n mod 4 points
+    float xv[NR], yv[NC];
 #pragma unroll
     for (int i = 0; i < NR; ++i) xv[i] = __ldg(xp[i] + p);
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      yv[j] = __ldg(yp[j] + p);
-      yl[j] = 0.0f;
+    for (int j = 0; j < NC; ++j) yv[j] = __ldg(yp[j] + p);
+    const float yl = ylo ? __ldg(ylo + p) : 0.0f;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i], yv[j]);
+      lo[i * NC + NC - 1] = fmaf(xv[i], yl, lo[i * NC + NC - 1]);
     }
-    if (ylo) yl[NC - 1] = __ldg(ylo + p);
-#pragma unroll
-    for (int i = 0; i < NR; ++i)
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i], yv[j]);
-        lo[i * NC + j] = fmaf(xv[i], yl[j], lo[i * NC + j]);
-      }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
