@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
 // counterpart of k_gram_tiled).  A column may carry a second FP32 vector (ylo) holding the
 // low part of an FP64 vector split as hi + lo.
 template <int NR, int NC>
-__global__ void __launch_bounds__(kThreads, 1) k_gram_df(GramTilesF g) {
+__global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
   if (g.ctrl->done) return;
   constexpr int K = NR * NC;
   __shared__ double buf[kTiledSmem];
@@ -943,31 +943,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_df(GramTilesF g) {
   // four consecutive points per thread and trip (columns are 16-byte aligned): more bytes in
   // flight per thread, one set of index computations per four points
   const int64_t n4 = g.n >> 2;
-  // the next trip's loads are issued before this trip's products (registers double-buffered),
-  // so that their latency overlaps the arithmetic
-  float4 xv[NR], yv[NC];
-  float4 yl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  auto load = [&](int64_t v) {
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 xv[NR], yv[NC];
+    float4 yl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < NR; ++i) xv[i] = __ldg(reinterpret_cast<const float4*>(xp[i]) + v);
 #pragma unroll
     for (int j = 0; j < NC; ++j) yv[j] = __ldg(reinterpret_cast<const float4*>(yp[j]) + v);
     if (ylo) yl = __ldg(reinterpret_cast<const float4*>(ylo) + v);
-  };
-  if (gid < n4) load(gid);
-  for (int64_t v = gid; v < n4; v += stride) {
-    const float4 yc = yl;
-    float4 xc[NR], ycol[NC];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) xc[i] = xv[i];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) ycol[j] = yv[j];
-    if (v + stride < n4) load(v + stride);
 #define SSTEP_DF_LANE(c)                                                          \
     _Pragma("unroll") for (int i = 0; i < NR; ++i) {                              \
       _Pragma("unroll") for (int j = 0; j < NC; ++j)                              \
-        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xc[i].c, ycol[j].c);          \
-      lo[i * NC + NC - 1] = fmaf(xc[i].c, yc.c, lo[i * NC + NC - 1]);             \
+        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i].c, yv[j].c);            \
+      lo[i * NC + NC - 1] = fmaf(xv[i].c, yl.c, lo[i * NC + NC - 1]);             \
     }
     SSTEP_DF_LANE(x)
     SSTEP_DF_LANE(y)
