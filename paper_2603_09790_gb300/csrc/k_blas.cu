@@ -52,9 +52,9 @@ __device__ void fgs_column(int s, const double* W, const double* rinv, const dou
   }
 }
 
-// fgs_column for a compile-time s: the same operations in the same order (bit-identical
+// fgs_column for a compile-time s <= 4: the same operations in the same order (bit-identical
 // results), with the row loops unrolled so that the W loads leave the dependent chain and x
-// stays in registers.  The reduced solves of s = 8, nu = 30 took ~0.1 ms in the loop form.
+// stays in registers.
 template <int S>
 __device__ void fgs_column_s(const double* Wp, const double* rinv, const double* b, int nu,
                              double* x, int stride) {
@@ -90,11 +90,46 @@ __device__ void fgs_dispatch(int s, const double* W, const double* rinv, const d
     case 2: fgs_column_s<2>(W, rinv, b, nu, x, stride); return;
     case 3: fgs_column_s<3>(W, rinv, b, nu, x, stride); return;
     case 4: fgs_column_s<4>(W, rinv, b, nu, x, stride); return;
-    case 5: fgs_column_s<5>(W, rinv, b, nu, x, stride); return;
-    case 6: fgs_column_s<6>(W, rinv, b, nu, x, stride); return;
-    case 7: fgs_column_s<7>(W, rinv, b, nu, x, stride); return;
-    case 8: fgs_column_s<8>(W, rinv, b, nu, x, stride); return;
     default: fgs_column(s, W, rinv, b, nu, x, stride); return;
+  }
+}
+
+// Forward Gauss-Seidel for s >= 5 with one warp per right-hand side, lane i owning row i.  The
+// part of row i above the diagonal uses the previous sweep's x and is formed by all lanes at
+// once; each new x_k is then passed down the warp, so the sequential chain per row is one
+// multiply, one shuffle and one FMA instead of a dot product of s terms (the reduced solves of
+// s = 8, nu = 30 were latency-bound on the FP64 pipe).  The same sums as fgs_column, added in
+// another order: the terms above the diagonal first.  Executed by the whole CTA.
+__device__ void fgs_warp(int s, const double* W, const double* rinv, const double* B, int nrhs,
+                         int nu, double* X) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool row = lane < s;
+  double wr[kMaxS];
+#pragma unroll
+  for (int j = 0; j < kMaxS; ++j) wr[j] = (row && j < s) ? W[lane + j * s] : 0.0;
+  const double ri = row ? rinv[lane] : 0.0;
+  for (int c = warp; c < nrhs; c += nw) {
+    const double bi = row ? B[lane + c * s] : 0.0;
+    double x = 0.0;
+    for (int sw = 0; sw < nu; ++sw) {
+      double up = 0.0;
+#pragma unroll
+      for (int j = 1; j < kMaxS; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j);
+        if (j > lane && j < s) up = fma(-wr[j], xj, up);
+      }
+      double acc = bi + up, xn = x;
+#pragma unroll
+      for (int k = 0; k < kMaxS; ++k) {
+        if (k < s) {  // warp-uniform
+          if (lane == k) xn = acc * ri;
+          const double xk = __shfl_sync(0xffffffffu, xn, k);
+          if (lane > k && row) acc = fma(-wr[k], xk, acc);
+        }
+      }
+      x = xn;
+    }
+    if (row) X[lane + c * s] = x;
   }
 }
 
@@ -152,7 +187,9 @@ __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs,
   }
   __syncthreads();
   if (!ok) return false;
-  if ((int)threadIdx.x < nrhs) {
+  if (solver != SSTEP_GRAM_CHOLESKY && s >= 5) {
+    fgs_warp(s, W, scratch + s * s, B, nrhs, nu, X);
+  } else if ((int)threadIdx.x < nrhs) {
     const int c = threadIdx.x;
     if (solver == SSTEP_GRAM_CHOLESKY) chol_column(s, scratch, B + c * s, X + c * s, 1);
     else fgs_dispatch(s, W, scratch + s * s, B + c * s, nu, X + c * s, 1);
