@@ -13,7 +13,6 @@
 #include <algorithm>
 
 #include "common.cuh"
-#include "tma.cuh"
 
 namespace sstep {
 
@@ -680,101 +679,46 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
   return true;
 }
 
-// b2 = -Q^T AZ (line 12) from FP32 blocks, then beta = FGS(W, b2) (line 13).  The 2s columns
-// reach shared memory through 1D bulk copies (one per column and chunk of 512 points, issued
-// by one thread, completing on the stage's mbarrier) kB2Stages chunks ahead of the arithmetic,
-// so that the double-float products (about ten FP32 operations each) never wait for DRAM;
-// each thread takes two points of every chunk.  Waits are bounded like the Q1 step's.
-constexpr int kB2Pts = 2 * kThreads;  // points per chunk
-constexpr int kB2Stages = 3;
-
-template <int S>
-constexpr size_t b2f_dyn_smem() {
-  return (size_t)kB2Stages * 2 * S * kB2Pts * sizeof(float);
-}
-
+// b2 = -Q^T AZ (line 12) from FP32 blocks, then beta = FGS(W, b2) (line 13).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   if (a.ctrl->done) return;
-  constexpr int K = S * S, NC = 2 * S;
-  extern __shared__ __align__(128) float stg[];  // [kB2Stages][NC][kB2Pts]
-  __shared__ unsigned long long full[kB2Stages];
+  constexpr int K = S * S;
   __shared__ double buf[kTiledSmem];
   float hi[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
-  const int64_t ld = a.ld;        // a multiple of 64: every column is 16-byte aligned
-  const int64_t n4 = a.n & ~(int64_t)3;  // points the bulk copies cover (16-byte sizes)
-  const int64_t nchunks = (n4 + kB2Pts - 1) / kB2Pts;
-  const int64_t my = (int64_t)blockIdx.x < nchunks
-                         ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // this CTA's chunks
-  const int tid = threadIdx.x;
-  int64_t issued = 0, waited = 0;  // thread 0's counts
-  auto issue = [&](int64_t k) {    // k-th chunk of this CTA into slot k % kB2Stages
-    const int slot = (int)(k % kB2Stages);
-    const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kB2Pts;
-    const int64_t pts = n4 - p0 < kB2Pts ? n4 - p0 : (int64_t)kB2Pts;
-    const uint32_t bytes = (uint32_t)(pts * sizeof(float));
-    const uint32_t bar = smem_addr(&full[slot]);
-    mbar_expect_tx(bar, bytes * NC);
-    float* dst = stg + (size_t)slot * NC * kB2Pts;
-#pragma unroll
-    for (int i = 0; i < S; ++i) bulk_load_1d(smem_addr(dst + i * kB2Pts), a.Q + i * ld + p0, bytes, bar);
-#pragma unroll
-    for (int j = 0; j < S; ++j)
-      bulk_load_1d(smem_addr(dst + (S + j) * kB2Pts), a.AZ + j * ld + p0, bytes, bar);
-    issued = k + 1;
-  };
-  if (tid == 0) {
-    for (int i = 0; i < kB2Stages; ++i) mbar_init(smem_addr(&full[i]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (tid == 0)
-    for (int64_t k = 0; k < kB2Stages && k < my; ++k) issue(k);
-  bool lost = false;
-  for (int64_t k = 0; k < my; ++k) {
-    const int slot = (int)(k % kB2Stages);
-    if (!mbar_wait(smem_addr(&full[slot]), (uint32_t)(k / kB2Stages) & 1u)) lost = true;
-    if (!lost) {
-      if (tid == 0) waited = k + 1;
-      const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kB2Pts;
-      const int q = 2 * tid;
-      if (p0 + q < n4) {  // n4 and p0 are multiples of 4, q is even: point q + 1 is in too
-        const float* src = stg + (size_t)slot * NC * kB2Pts + q;
-        float2 qv[S], zv[S];
-#pragma unroll
-        for (int i = 0; i < S; ++i) qv[i] = *reinterpret_cast<const float2*>(src + i * kB2Pts);
-#pragma unroll
-        for (int j = 0; j < S; ++j)
-          zv[j] = *reinterpret_cast<const float2*>(src + (S + j) * kB2Pts);
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-#pragma unroll
-          for (int j = 0; j < S; ++j) {
-            df_acc_prod(hi[i + j * S], lo[i + j * S], qv[i].x, zv[j].x);
-            df_acc_prod(hi[i + j * S], lo[i + j * S], qv[i].y, zv[j].y);
-          }
-      }
-    }
-    // every thread is done with this slot: refill it kB2Stages chunks ahead
-    if (__syncthreads_or(lost)) {
-      lost = true;
-      break;
-    }
-    if (tid == 0 && k + kB2Stages < my) issue(k + kB2Stages);
-  }
-  if (lost && tid == 0) {
-    // let the copies still in flight land before the shared memory is released; the sums
-    // below still run so that the grid reduction's ticket stays consistent
-    for (int64_t k = waited; k < issued; ++k)
-      mbar_wait(smem_addr(&full[k % kB2Stages]), (uint32_t)(k / kB2Stages) & 1u);
-    a.ctrl->status = SSTEP_ERR_TIMEOUT;
-    a.ctrl->done = 1;
-  }
+  const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = n4 + (int64_t)blockIdx.x * blockDim.x + tid; p < a.n; p += stride) {
-    float q[S], z[S];  // the last n mod 4 points
+  // four consecutive points per thread and trip (16-byte loads: more bytes in flight)
+  const int64_t n4 = a.n >> 2;
+  // column pointers formed once: the loop body indexes them with v alone
+  const float4* qc[S];
+  const float4* zc[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    qc[i] = reinterpret_cast<const float4*>(a.Q + i * ld);
+    zc[i] = reinterpret_cast<const float4*>(a.AZ + i * ld);
+  }
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 q[S], z[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) q[i] = __ldg(qc[i] + v);
+#pragma unroll
+    for (int j = 0; j < S; ++j) z[j] = __ldg(zc[j] + v);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].x, z[j].x);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].y, z[j].y);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].z, z[j].z);
+        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].w, z[j].w);
+      }
+  }
+  for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
+    float q[S], z[S];
 #pragma unroll
     for (int i = 0; i < S; ++i) q[i] = __ldg(a.Q + i * ld + p);
 #pragma unroll
@@ -1756,20 +1700,11 @@ cudaError_t launch_gram_df_split(int mode, const MixedArgs& a, int s, const floa
 cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
   if (s > 4) return launch_gram_df_split(GM_LITERAL_B2, a, s, a.Q, a.AZ, false, st);
   switch (s) {
-#define CASE(S)                                                                            \
-  case S: {                                                                                \
-    static int occ = 0;                                                                    \
-    constexpr size_t dyn = b2f_dyn_smem<S>();                                              \
-    if (!occ) {                                                                            \
-      cudaFuncSetAttribute(k_gram_b2f<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                           (int)dyn);                                                      \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_b2f<S>, kThreads, dyn);   \
-      if (occ < 1) occ = 1;                                                                \
-    }                                                                                      \
-    const int64_t chunks = (a.n + kB2Pts - 1) / kB2Pts;                                    \
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, chunks)); \
-    k_gram_b2f<S><<<grid, kThreads, dyn, st>>>(a);                                         \
-    return cudaGetLastError();                                                             \
+#define CASE(S)                                                            \
+  case S: {                                                                \
+    static int occ = 0;                                                    \
+    k_gram_b2f<S><<<occ_grid(k_gram_b2f<S>, a.n, occ), kThreads, 0, st>>>(a); \
+    return cudaGetLastError();                                             \
   }
     CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE

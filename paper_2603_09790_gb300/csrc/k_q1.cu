@@ -28,7 +28,6 @@
 
 #include "common.cuh"
 #include "epilogue.cuh"
-#include "tma.cuh"
 
 namespace sstep {
 
@@ -233,12 +232,50 @@ constexpr int kNS = 6;             // pipeline stages (z planes)
 constexpr int kUStage = 736;       // floats per u stage: 720 used, 2944 bytes (23 x 128)
 constexpr int kKStage = 640;       // floats per cell stage: 612 used, 2560 bytes (20 x 128)
 constexpr uint32_t kStageBytes = (TUW * TUH + TKW * TKH) * 4;
+constexpr uint32_t kWaitRounds = 1u << 22;  // try_wait rounds before a copy counts as lost
 
 struct __align__(128) TmaSmem {
   float u[kNS][kUStage];
   float k[kNS][kKStage];
   unsigned long long full[kNS];
 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitRounds; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
 
 // Register window of one staged plane for a thread's two vertices (x and x + 1): u at rows
 // y-1..y+1 and columns x-1..x+2 (v[dy + 1][c]); the conductivities of cells x..x+2 at rows
