@@ -359,6 +359,17 @@ struct MixedArgs {
   double* partials;
   double* hist;
 };
+// Tiles of FP32 Gram products (double-float accumulation); ylo: optional low part of a column.
+struct GramTilesF {
+  int64_t n;
+  int ntiles, mode, ne;
+  const float* x[kMaxTiles][kTileMaxR];
+  const float* y[kMaxTiles][kTileMaxC];
+  const float* ylo[kMaxTiles][kTileMaxC];
+  short out[kMaxTiles][kTileMaxR * kTileMaxC];
+  Ctrl* ctrl;
+  double* partials;
+};
 cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st);
 cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st);
 cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st);

@@ -1026,103 +1026,99 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
   }
 }
 
-// FP32 Gram products X^T [Y | r] for 5 <= s <= 8 in one pass, warp-cooperative: a warp
-// stages 32 points of every column in shared memory (one coalesced load per lane and column)
-// and lane L owns the entries L, L + 32, ... of the result, accumulating them in double-float
-// over the warp's points; per product one shared load of each operand and the ~10 FP32
-// operations of TwoProd + TwoSum.  Each column is read once (the 2 x 2 tiles read each twice),
-// and a thread holds EPL entries instead of a whole tile, so occupancy stays high.  Entry
-// e = i + j s is x_i^T y_j; with r, entries s^2 + i are x_i^T (rhi + rlo).
-struct GramWarpArgs {
-  int64_t n, ld;
-  int mode;
-  const float* x;  // column c at x + c ld
-  const float* y;
-  const float* rhi;
-  const float* rlo;
-  Ctrl* ctrl;
-  double* partials;
-};
-
-constexpr int kGwWarps = kThreads / 32;
-
-template <int S, bool R>
-__global__ void __launch_bounds__(kThreads) k_gram_dfw(GramWarpArgs g) {
+// Register-tiled Gram products of FP32 vectors with double-float accumulation (the FP32
+// counterpart of k_gram_tiled).  A column may carry a second FP32 vector (ylo) holding the
+// low part of an FP64 vector split as hi + lo.
+template <int NR, int NC>
+__global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
   if (g.ctrl->done) return;
-  constexpr int NC = 2 * S + (R ? 2 : 0);  // staged columns: x_0..x_{s-1}, y_0..y_{s-1}, rhi, rlo
-  constexpr int K = S * S + (R ? S : 0);
-  constexpr int EPL = (K + 31) / 32;       // entries per lane
-  __shared__ float st[kGwWarps][NC][33];   // stride 33: lanes reading different columns of one
-                                           // point hit different banks
-  __shared__ double wsum[kGwWarps][K];
+  constexpr int K = NR * NC;
   __shared__ double buf[kTiledSmem];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int xc[EPL], yc[EPL];  // staged column of each operand; yc = 2S marks an r entry
-  bool on[EPL];
-  float hi[EPL], lo[EPL];
+  const int t = blockIdx.y;
+  const float* xp[NR];
+  const float* yp[NC];
 #pragma unroll
-  for (int t = 0; t < EPL; ++t) {
-    const int e = lane + 32 * t;
-    on[t] = e < K;
-    const int ee = on[t] ? e : 0;
-    if (ee < S * S) {
-      xc[t] = ee % S;
-      yc[t] = S + ee / S;
-    } else {
-      xc[t] = ee - S * S;
-      yc[t] = 2 * S;
+  for (int i = 0; i < NR; ++i) xp[i] = g.x[t][i];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) yp[j] = g.y[t][j];
+  const float* ylo = g.ylo[t][NC - 1];  // only the last column may carry a low part
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // four consecutive points per thread and trip (columns are 16-byte aligned): more bytes in
+  // flight per thread, one set of index computations per four points
+  const int64_t n4 = g.n >> 2;
+  for (int64_t v = gid; v < n4; v += stride) {
+    float4 xv[NR], yv[NC];
+    float4 yl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) xv[i] = __ldg(reinterpret_cast<const float4*>(xp[i]) + v);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) yv[j] = __ldg(reinterpret_cast<const float4*>(yp[j]) + v);
+    if (ylo) yl = __ldg(reinterpret_cast<const float4*>(ylo) + v);
+#define SSTEP_DF_LANE(c)                                                          \
+    _Pragma("unroll") for (int i = 0; i < NR; ++i) {                              \
+      _Pragma("unroll") for (int j = 0; j < NC; ++j)                              \
+        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i].c, yv[j].c);            \
+      lo[i * NC + NC - 1] = fmaf(xv[i].c, yl.c, lo[i * NC + NC - 1]);             \
     }
-    hi[t] = lo[t] = 0.0f;
+    SSTEP_DF_LANE(x)
+    SSTEP_DF_LANE(y)
+    SSTEP_DF_LANE(z)
+    SSTEP_DF_LANE(w)
+#undef SSTEP_DF_LANE
   }
-  const int64_t step = (int64_t)gridDim.x * kGwWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kGwWarps + warp) * 32; base < g.n; base += step) {
-    const int64_t p = base + lane;
-    const bool in = p < g.n;
+  for (int64_t p = 4 * n4 + gid; p < g.n; p += stride) {  // the last n mod 4 points
+    float xv[NR], yv[NC];
 #pragma unroll
-    for (int c = 0; c < S; ++c) {
-      st[warp][c][lane] = in ? __ldg(g.x + c * g.ld + p) : 0.0f;
-      st[warp][S + c][lane] = in ? __ldg(g.y + c * g.ld + p) : 0.0f;
-    }
-    if constexpr (R) {
-      st[warp][2 * S][lane] = in ? __ldg(g.rhi + p) : 0.0f;
-      st[warp][2 * S + 1][lane] = in ? __ldg(g.rlo + p) : 0.0f;
-    }
-    __syncwarp();
-    const int np = g.n - base < 32 ? (int)(g.n - base) : 32;
-    for (int q = 0; q < np; ++q) {
+    for (int i = 0; i < NR; ++i) xv[i] = __ldg(xp[i] + p);
 #pragma unroll
-      for (int t = 0; t < EPL; ++t) {
-        if (!on[t]) continue;
-        const float xv = st[warp][xc[t]][q];
-        df_acc_prod(hi[t], lo[t], xv, st[warp][yc[t]][q]);
-        if (R && yc[t] == 2 * S) lo[t] = fmaf(xv, st[warp][2 * S + 1][q], lo[t]);
-      }
+    for (int j = 0; j < NC; ++j) yv[j] = __ldg(yp[j] + p);
+    const float yl = ylo ? __ldg(ylo + p) : 0.0f;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i], yv[j]);
+      lo[i * NC + NC - 1] = fmaf(xv[i], yl, lo[i * NC + NC - 1]);
     }
-    __syncwarp();
   }
-  // warp results (one owner lane per entry) -> CTA partial per entry -> grid
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int t = 0; t < EPL; ++t)
-    if (on[t]) wsum[warp][lane + 32 * t] = (double)hi[t] + (double)lo[t];
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum((double)hi[k] + (double)lo[k]);
+    if (lane == 0) buf[wid * K + k] = v;
+  }
   __syncthreads();
-  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+  const unsigned int cta = blockIdx.x + gridDim.x * blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < kGwWarps; ++w) v += wsum[w][e];
-    g.partials[(size_t)blockIdx.x * K + e] = v;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    g.partials[(size_t)cta * K + k] = v;
   }
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    last = (atomicAdd(&g.ctrl->ticket[TK_GRAM], 1u) == gridDim.x - 1);
+    last = (atomicAdd(&g.ctrl->ticket[TK_GRAM], 1u) == gridDim.x * gridDim.y - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  sum_partials(g.partials, gridDim.x, K, 1, buf);
+  double* sums = buf;
+  {
+    __shared__ double tot[kMaxTiles * kTileMaxR * kTileMaxC];
+    sum_partials(g.partials, gridDim.x, K, (int)gridDim.y, tot);
+    for (int idx = threadIdx.x; idx < (int)gridDim.y * K; idx += blockDim.x) {
+      const int e = g.out[idx / K][idx % K];
+      if (e >= 0) sums[e] = tot[idx];
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) g.ctrl->ticket[TK_GRAM] = 0u;
-  for (int e = threadIdx.x; e < K; e += blockDim.x) g.ctrl->sums[e] = buf[e];
-  gram_tail(g.mode, g.ctrl, buf, buf + K);
+  for (int e = threadIdx.x; e < g.ne; e += blockDim.x) g.ctrl->sums[e] = sums[e];
+  gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
 }
 
 __global__ void __launch_bounds__(kThreads) k_fold_x(double* x, float* xh, float* xl, int64_t n) {
@@ -1636,41 +1632,65 @@ int occ_grid(KernelT k, int64_t n, int& cache) {
 
 namespace {
 
-// X^T [Y | r] for 5 <= s <= 8 (k_gram_dfw), grid filling every SM at the kernel's occupancy.
-template <int S, bool R>
-cudaError_t launch_gram_dfw_s(const GramWarpArgs& g, cudaStream_t st) {
+template <int NR, int NC>
+cudaError_t launch_gram_df_shape(const GramTilesF& g, cudaStream_t st) {
   static int occ = 0;
   if (!occ) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_dfw<S, R>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_df<NR, NC>, kThreads, 0);
     if (occ < 1) occ = 1;
   }
-  const int64_t rounds = (g.n + kGwWarps * 32 - 1) / (kGwWarps * 32);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, rounds));
-  k_gram_dfw<S, R><<<grid, kThreads, 0, st>>>(g);
+  const int64_t want = ((int64_t)sm_count() * occ + g.ntiles - 1) / g.ntiles;
+  const int64_t rows = (g.n + kThreads - 1) / kThreads;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, rows));
+  k_gram_df<NR, NC><<<dim3(gx, g.ntiles), kThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_dfw(int mode, const MixedArgs& a, int s, const float* X, const float* Y,
-                            bool with_r, cudaStream_t st) {
-  GramWarpArgs g{};
+// 2 x 2 tiles of X^T [Y | r]: X = s FP32 columns, Y = s FP32 columns (entries i + j s),
+// r = rhi + rlo (entries s^2 + i, kept from the tiles of the first column half), as the
+// literal-form layouts expect.  Padding rows/columns point at column 0 and are not kept.
+cudaError_t launch_gram_df_split(int mode, const MixedArgs& a, int s, const float* X,
+                                 const float* Y, bool with_r, cudaStream_t st) {
+  GramTilesF g{};
   g.n = a.n;
-  g.ld = a.ld;
   g.mode = mode;
-  g.x = X;
-  g.y = Y;
-  g.rhi = a.rhi;
-  g.rlo = a.rlo;
   g.ctrl = a.ctrl;
   g.partials = a.partials;
-  switch (s * 2 + (with_r ? 1 : 0)) {
-    case 10: return launch_gram_dfw_s<5, false>(g, st);
-    case 11: return launch_gram_dfw_s<5, true>(g, st);
-    case 12: return launch_gram_dfw_s<6, false>(g, st);
-    case 13: return launch_gram_dfw_s<6, true>(g, st);
-    case 14: return launch_gram_dfw_s<7, false>(g, st);
-    case 15: return launch_gram_dfw_s<7, true>(g, st);
-    case 16: return launch_gram_dfw_s<8, false>(g, st);
-    case 17: return launch_gram_dfw_s<8, true>(g, st);
+  g.ntiles = 4;
+  const int h = (s + 1) / 2;
+  const int nr = h, nc = h + (with_r ? 1 : 0);
+  g.ne = s * s + (with_r ? s : 0);
+  for (auto& tt : g.out)
+    for (auto& o : tt) o = -1;
+  for (int t = 0; t < 4; ++t) {
+    const int i0 = (t >> 1) * h, j0 = (t & 1) * h;
+    for (int ri = 0; ri < nr; ++ri) {
+      const int i = i0 + ri;
+      g.x[t][ri] = X + (int64_t)(i < s ? i : 0) * a.ld;
+    }
+    for (int c = 0; c < h; ++c) {
+      const int j = j0 + c;
+      g.y[t][c] = Y + (int64_t)(j < s ? j : 0) * a.ld;
+      for (int ri = 0; ri < nr; ++ri) {
+        const int i = i0 + ri;
+        if (i < s && j < s) g.out[t][ri * nc + c] = (short)(i + j * s);
+      }
+    }
+    if (with_r) {
+      g.y[t][h] = a.rhi;
+      g.ylo[t][h] = a.rlo;
+      if (j0 == 0)
+        for (int ri = 0; ri < nr; ++ri) {
+          const int i = i0 + ri;
+          if (i < s) g.out[t][ri * nc + h] = (short)(s * s + i);
+        }
+    }
+  }
+  switch (nr * 16 + nc) {
+    case 3 * 16 + 3: return launch_gram_df_shape<3, 3>(g, st);
+    case 3 * 16 + 4: return launch_gram_df_shape<3, 4>(g, st);
+    case 4 * 16 + 4: return launch_gram_df_shape<4, 4>(g, st);
+    case 4 * 16 + 5: return launch_gram_df_shape<4, 5>(g, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -1678,7 +1698,7 @@ cudaError_t launch_gram_dfw(int mode, const MixedArgs& a, int s, const float* X,
 }  // namespace
 
 cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
-  if (s > 4) return launch_gram_dfw(GM_LITERAL_B2, a, s, a.Q, a.AZ, false, st);
+  if (s > 4) return launch_gram_df_split(GM_LITERAL_B2, a, s, a.Q, a.AZ, false, st);
   switch (s) {
 #define CASE(S)                                                            \
   case S: {                                                                \
@@ -1707,7 +1727,7 @@ cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStrea
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_gram_dfw(GM_LITERAL_W, a, s, a.Q, a.AQ, true, st);
+    return launch_gram_df_split(GM_LITERAL_W, a, s, a.Q, a.AQ, true, st);
   }
   switch (s) {
 #define CASE(S)                                                                            \
