@@ -74,7 +74,7 @@ enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1, SSTEP_MATRIX_Q1 = 2 };
  *      M1 + M1 x M1 x K1), K1 = [[1,-1],[-1,1]], M1 = [[1/3,1/6],[1/6,1/3]], over the cells.
  *      points is ignored; n may be 0 or nx*ny*nz.  Preconditioners NONE and JACOBI; the
  *      FP64 and FP32-basis s-step forms and PCG.  In the FP32-basis form with nx a multiple
- *      of 4 (nx >= 40, ny >= 10) the middle MPK steps are fed by tensor-memory-accelerator
+ *      of 4 (nx >= 72, ny >= 10) the middle MPK steps are fed by tensor-memory-accelerator
  *      copies; SSTEP_Q1_TMA=0 in the environment at set-up selects plain loads (same results
  *      bit for bit). */
 typedef struct {

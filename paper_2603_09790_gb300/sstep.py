@@ -216,7 +216,6 @@ class Solver:
                  amg_max_levels=0, stream=None):
         """A: a Stencil, CSR or Q1 (one system), or a list of 7-point Stencils (the batched
         persistent solver; also used for a single Stencil when persistent=True)."""
-        lib = load()
         mats = list(A) if isinstance(A, (list, tuple)) else [A]
         if not mats:
             raise ValueError("no system given")
@@ -248,6 +247,7 @@ class Solver:
                 m.rowptr, m.colind, m.vals = _ptr(a.rowptr), _ptr(a.colind), _ptr(a.vals)
             else:
                 raise TypeError("A must be a Stencil, a CSR or a Q1, or a list of Stencils")
+        lib = load()
         self.nsys = len(mats)
         self.sizes = [int(m.n) for m in marr]
         self.batched = self.nsys > 1 or bool(persistent)

@@ -173,12 +173,14 @@ def test_q1_rejects_invalid():
             S.update_values(dev(k))
 
 
-@pytest.mark.parametrize("dims", [(64, 24, 20), (44, 12, 17), (40, 10, 9), (96, 33, 8)])
+@pytest.mark.parametrize("dims", [(72, 10, 9), (76, 12, 17), (128, 24, 20), (96, 33, 8),
+                                  (64, 24, 20)])
 def test_fp32_tma_steps_equal_plain_loads(dims, monkeypatch):
-    """nx a multiple of 4 (and the grid no smaller than the copy boxes): the middle MPK steps
-    take the tensor-memory-accelerator kernel.  It does the plain kernel's arithmetic in the
-    same order, so both give the same iterates bit for bit; the solve reaches the FP64 true
-    residual."""
+    """nx a multiple of 4 and the grid no smaller than the copy boxes (nx >= 72, ny >= 10): the
+    middle MPK steps take the tensor-memory-accelerator kernel (64 x 8 vertex tiles: one full
+    tile, a ragged x tail, several tiles and z chunks).  It does the plain kernel's arithmetic
+    in the same order, so both give the same iterates bit for bit; the solve reaches the FP64
+    true residual.  (64, 24, 20) is below the box width and takes plain loads either way."""
     csr, kappa, b = problem(dims, corr=4.0)
     kw = dict(s=8, sweeps=30, rtol=1e-8, precision="fp32_rr", rr_period=8, lambda_max=1.97)
     out = []
