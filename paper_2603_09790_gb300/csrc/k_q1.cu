@@ -90,10 +90,12 @@ __device__ __forceinline__ T q1_vertex(const T* Um, const T* Uc, const T* Up, co
 }
 
 // The z march shared by the FP64 and FP32 kernels.  load_u(idx) returns the (possibly
-// M^{-1}-scaled) input at vertex idx; at(z, y, uc, in) consumes the vertex of plane z.
-template <typename T, class LoadU, class At>
+// M^{-1}-scaled) input at vertex idx; vertex(Um, Uc, Up, K0, K1, tx, ty, i, uc) forms (A u)_i
+// from the staged planes; at(i, y, uc, in) consumes the vertex of plane z.
+template <typename T, class LoadU, class Vertex, class At>
 __device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ kap, int kpitch,
-                                         int zc, Q1Smem<T>& sh, LoadU load_u, At at) {
+                                         int zc, Q1Smem<T>& sh, LoadU load_u, Vertex vertex,
+                                         At at) {
   const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
@@ -164,12 +166,55 @@ __device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ ka
       for (int p = 0; p < kKPer; ++p) nk[p] = ldk(p, z + 2);
     }
     T uc = T(0), yv = T(0);
+    const int64_t i = (int64_t)z * pxy + (int64_t)y * nx + x;
     if (in)
-      yv = q1_vertex<T>(sh.u[iu & 3], sh.u[(iu + 1) & 3], sh.u[(iu + 2) & 3], sh.k[ks], sh.k[ks1],
-                        tx, ty, uc);
-    at((int64_t)z * pxy + (int64_t)y * nx + x, yv, uc, in);
+      yv = vertex(sh.u[iu & 3], sh.u[(iu + 1) & 3], sh.u[(iu + 2) & 3], sh.k[ks], sh.k[ks1], tx,
+                  ty, i, uc);
+    at(i, yv, uc, in);
     ks = ks1;
   }
+}
+
+// (A u)_v in FP64 from the vertex's precomputed coefficients (k_q1_coef: a_vv and the twelve
+// face-diagonal entries, -1/12 of a pair sum each) and the staged planes; the body diagonals
+// take the conductivities of the staged cell planes.  22 FP64 operations per vertex instead of
+// the 38 of q1_vertex: the FP64 kernels are bound by the FP64 pipe, HBM has room for the
+// 104 bytes of coefficients.
+__device__ __forceinline__ double q1_vertex_coef(const double* __restrict__ c, int64_t n,
+                                                 const double* Um, const double* Uc,
+                                                 const double* Up, const double* K0,
+                                                 const double* K1, int tx, int ty, int64_t i,
+                                                 double& uc) {
+  auto U = [&](const double* P, int dx, int dy) -> double {
+    return P[(ty + 1 + dy) * UW + tx + 1 + dx];
+  };
+  auto C = [&](const double* P, int a, int b) -> double { return P[(ty + b) * KW + tx + a]; };
+  double cf[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) cf[k] = __ldg(c + k * n + i);
+  uc = U(Uc, 0, 0);
+  double y = cf[12] * uc;
+  y = fma(cf[0], U(Uc, -1, -1), y);  // face diagonals in the plane (dz = 0)
+  y = fma(cf[1], U(Uc, 1, -1), y);
+  y = fma(cf[2], U(Uc, -1, 1), y);
+  y = fma(cf[3], U(Uc, 1, 1), y);
+  y = fma(cf[4], U(Um, -1, 0), y);   // dy = 0
+  y = fma(cf[5], U(Um, 1, 0), y);
+  y = fma(cf[6], U(Up, -1, 0), y);
+  y = fma(cf[7], U(Up, 1, 0), y);
+  y = fma(cf[8], U(Um, 0, -1), y);   // dx = 0
+  y = fma(cf[9], U(Um, 0, 1), y);
+  y = fma(cf[10], U(Up, 0, -1), y);
+  y = fma(cf[11], U(Up, 0, 1), y);
+  double b = C(K0, 0, 0) * U(Um, -1, -1);  // body diagonals: one cell each
+  b = fma(C(K0, 1, 0), U(Um, 1, -1), b);
+  b = fma(C(K0, 0, 1), U(Um, -1, 1), b);
+  b = fma(C(K0, 1, 1), U(Um, 1, 1), b);
+  b = fma(C(K1, 0, 0), U(Up, -1, -1), b);
+  b = fma(C(K1, 1, 0), U(Up, 1, -1), b);
+  b = fma(C(K1, 0, 1), U(Up, -1, 1), b);
+  b = fma(C(K1, 1, 1), U(Up, 1, 1), b);
+  return fma(-1.0 / 12.0, b, y);
 }
 
 template <int EPI, bool SCALE>
@@ -178,12 +223,17 @@ __global__ void __launch_bounds__(QT) k_q1(Q1Op A, EpiArgs e, int zc) {
   __shared__ Q1Smem<double> sh;
   double red[2] = {0.0, 0.0};
   const double* __restrict__ u = e.u;
+  const int64_t n = (int64_t)A.nx * A.ny * A.nz;
   auto load_u = [&](int64_t idx) -> double {
     double v = __ldg(u + idx);
     if constexpr (SCALE) v *= __ldg(e.M.dinv + idx);
     return v;
   };
-  q1_march<double>(A, A.kappa, A.nx + 1, zc, sh, load_u, [&](int64_t i, double yv, double uc, bool in) {
+  auto vertex = [&](const double* Um, const double* Uc, const double* Up, const double* K0,
+                    const double* K1, int tx, int ty, int64_t i, double& uc) -> double {
+    return q1_vertex_coef(A.coef, n, Um, Uc, Up, K0, K1, tx, ty, i, uc);
+  };
+  q1_march<double>(A, A.kappa, A.nx + 1, zc, sh, load_u, vertex, [&](int64_t i, double yv, double uc, bool in) {
     if (!in) return;
     if constexpr (EPI == EP_MPK_FIRST && !SCALE) {
       yv *= e.M.dinv_u;
@@ -204,7 +254,11 @@ __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
     if constexpr (SCALE) v *= __ldg(e.dinv + idx);
     return v;
   };
-  q1_march<float>(A, A.kappaf, A.kpitch, zc, sh, load_u, [&](int64_t i, float yv, float uc, bool in) {
+  auto vertex = [&](const float* Um, const float* Uc, const float* Up, const float* K0,
+                    const float* K1, int tx, int ty, int64_t, float& uc) -> float {
+    return q1_vertex<float>(Um, Uc, Up, K0, K1, tx, ty, uc);
+  };
+  q1_march<float>(A, A.kappaf, A.kpitch, zc, sh, load_u, vertex, [&](int64_t i, float yv, float uc, bool in) {
     if (!in) return;
     if constexpr (FIRST && !SCALE) {
       yv *= e.dinv_u;
@@ -456,6 +510,41 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
   }
 }
 
+// FP64 coefficients of every vertex, structure of arrays c[k * n + v]: k = 0..3 face diagonals
+// with dz = 0 at (dx, dy) = (-1,-1), (1,-1), (-1,1), (1,1); k = 4..7 with dy = 0 at
+// (dx, dz) in the same order; k = 8..11 with dx = 0 at (dy, dz); each -1/12 of the two
+// conductivities that share the diagonal.  k = 12: a_vv = (1/3) sum of the eight around v.
+__global__ void k_q1_coef(Q1Op A, double* c) {
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+    double k[2][2][2];  // k[c][b][a]: cell (x + a, y + b, z + c)
+    for (int cc = 0; cc < 2; ++cc)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          k[cc][b][a] = A.kappa[((int64_t)(z + cc) * (ny + 1) + (y + b)) * (nx + 1) + (x + a)];
+    const double w = -1.0 / 12.0;
+    double* o = c + v;
+    o[0 * n] = w * (k[0][0][0] + k[1][0][0]);
+    o[1 * n] = w * (k[0][0][1] + k[1][0][1]);
+    o[2 * n] = w * (k[0][1][0] + k[1][1][0]);
+    o[3 * n] = w * (k[0][1][1] + k[1][1][1]);
+    o[4 * n] = w * (k[0][0][0] + k[0][1][0]);
+    o[5 * n] = w * (k[0][0][1] + k[0][1][1]);
+    o[6 * n] = w * (k[1][0][0] + k[1][1][0]);
+    o[7 * n] = w * (k[1][0][1] + k[1][1][1]);
+    o[8 * n] = w * (k[0][0][0] + k[0][0][1]);
+    o[9 * n] = w * (k[0][1][0] + k[0][1][1]);
+    o[10 * n] = w * (k[1][0][0] + k[1][0][1]);
+    o[11 * n] = w * (k[1][1][0] + k[1][1][1]);
+    const double k8 = ((k[0][0][0] + k[1][0][0]) + (k[0][0][1] + k[1][0][1])) +
+                      ((k[0][1][0] + k[1][1][0]) + (k[0][1][1] + k[1][1][1]));
+    o[12 * n] = k8 / 3.0;
+  }
+}
+
 // FP32 conductivities with rows padded to kpitch (padding zero).
 __global__ void k_q1_kappaf(Q1Op A, float* out) {
   const int64_t rows = (int64_t)(A.ny + 1) * (A.nz + 1);
@@ -575,7 +664,16 @@ int q1_grid_ctas(const Q1Op& A) {
   return (int)(g.grid.x * g.grid.y * g.grid.z);
 }
 
+cudaError_t launch_q1_coef(const Q1Op& A, double* coef, cudaStream_t st) {
+  const int64_t n = (int64_t)A.nx * A.ny * A.nz;
+  const int64_t want = (n + kThreads - 1) / kThreads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * 8));
+  k_q1_coef<<<grid, kThreads, 0, st>>>(A, coef);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st) {
+  if (!A.coef) return cudaErrorInvalidValue;  // the FP64 kernels read the set-up coefficients
   switch (e.epi) {
     case EP_SPMV: return launch_epi<EP_SPMV>(A, e, st);
     case EP_MPK: return launch_epi<EP_MPK>(A, e, st);
