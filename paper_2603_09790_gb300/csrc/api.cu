@@ -71,8 +71,7 @@ struct sstep_ctx {
   int32_t* colind = nullptr;
   double* vals = nullptr;
   double* dinv = nullptr;
-  double* kappa = nullptr;  // Q1 operator: cell conductivities
-  double* q1coef = nullptr; // Q1 operator: 13 x n vertex coefficients of the FP64 kernels
+  double* kappa = nullptr;  // Q1 operator: cell conductivities, then the vertex coefficients
   int64_t ncell = 0;
   double q1_gersh = 0.0;    // Q1 operator: Gershgorin lower bound found at set-up
   Q1TmaMaps* q1tma = nullptr;  // Q1 operator, FP32 path: tensor maps of the basis columns
@@ -579,7 +578,7 @@ void destroy(sstep_ctx* h) {
     if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
                   h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl, h->eta_a, h->eta_b,
-                  h->whist, h->kappa, h->q1coef};
+                  h->whist, h->kappa};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -709,10 +708,12 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
     h->n = (int64_t)A->nx * A->ny * A->nz;
     if (A->n != 0 && A->n != h->n) return fail(SSTEP_ERR_INVALID, "Q1 n != nx*ny*nz");
     h->ncell = (int64_t)(A->nx + 1) * (A->ny + 1) * (A->nz + 1);
-    CK(cudaMalloc(&h->kappa, sizeof(double) * h->ncell));
+    // conductivities, then (256-byte aligned) the 13 x n vertex coefficients that the set-up
+    // pass writes for the FP64 kernels
+    CK(cudaMalloc(&h->kappa, sizeof(double) * (round_up(h->ncell, 32) + 13 * h->n)));
     CK(cudaMemcpyAsync(h->kappa, A->weights, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
     h->op.q1 = Q1Op{A->nx, A->ny, A->nz, h->kappa, nullptr, (int)round_up(A->nx + 1, 4),
-                    nullptr, nullptr};
+                    nullptr};
   } else {
     return fail(SSTEP_ERR_INVALID, "unknown matrix kind");
   }
@@ -757,9 +758,6 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
   if (A->kind == SSTEP_MATRIX_Q1) {
     if (h->prec_kind == SSTEP_PREC_JACOBI) CKS(alloc(&h->dinv, ld));
     CKS(q1_setup(h));
-    CKS(alloc(&h->q1coef, 13 * h->n));
-    h->op.q1.coef = h->q1coef;
-    CK(launch_q1_coef(h->op.q1, h->q1coef, h->st));
     h->M.dinv = h->dinv;
     h->M.dinv_u = h->dinv ? 0.0 : 1.0;
   }
@@ -1404,7 +1402,6 @@ sstep_status sstep_update_values(sstep_handle h, const double* vals) {
   if (h->op.kind == SSTEP_MATRIX_Q1) {  // new conductivities
     CK(cudaMemcpyAsync(h->kappa, vals, sizeof(double) * h->ncell, cudaMemcpyDefault, h->st));
     CKS(q1_setup(h));
-    CK(launch_q1_coef(h->op.q1, h->q1coef, h->st));
     if (h->kappaf) CK(launch_q1_kappaf(h->op.q1, h->kappaf, h->st));
     if (h->dinvf) CK(launch_d2f(h->dinv, h->dinvf, h->n, h->st));
     CK(cudaStreamSynchronize(h->st));

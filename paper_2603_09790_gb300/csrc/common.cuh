@@ -96,7 +96,6 @@ struct Q1Op {
   const float* kappaf;    // FP32 copy for the FP32-basis path (null when unused), rows of kpitch
   int kpitch;             // row pitch of kappaf: nx+1 rounded up to a multiple of 4
   const Q1TmaMaps* tma;   // tensor maps of the basis columns and kappaf, or null
-  const double* coef;     // 13 x n FP64 vertex coefficients (launch_q1_coef), for the FP64 kernels
 };
 
 // Preconditioner: dinv == nullptr means the uniform scalar dinv_u (M = I gives dinv_u = 1).
@@ -336,9 +335,6 @@ int q1_grid_ctas(const Q1Op& A);
 int q1_setup_ctas(int64_t n);
 cudaError_t launch_q1_setup(const Q1Op& A, int jacobi, double* dinv, double* out_min, int* bad,
                             cudaStream_t st);
-// FP64 vertex coefficients (a_vv and the twelve face-diagonal entries, structure of arrays,
-// 13 x n doubles) from the conductivities, read by the FP64 operator kernels.
-cudaError_t launch_q1_coef(const Q1Op& A, double* coef, cudaStream_t st);
 // FP32 conductivities with rows padded to kpitch (the layout the tensor map needs).
 cudaError_t launch_q1_kappaf(const Q1Op& A, float* kappaf, cudaStream_t st);
 // Tensor maps for the TMA-fed FP32 MPK step: one per basis column (cols[c], n floats each) and

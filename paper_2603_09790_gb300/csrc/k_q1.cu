@@ -39,6 +39,17 @@ constexpr int KW = QX + 1, KH = QY + 1;       // staged cell plane (cells x0..x0
 constexpr int kUPer = (UW * UH + QT - 1) / QT;  // staged u values per thread
 constexpr int kKPer = (KW * KH + QT - 1) / QT;  // staged conductivities per thread
 
+// The library's Q1 operator data is one FP64 allocation: the (nx+1)(ny+1)(nz+1) conductivities,
+// then (from this offset, 256-byte aligned) 13 arrays of n vertex coefficients written by the
+// set-up pass (k_q1_setup) and read by the FP64 operator kernels: k = 0..3 the face diagonals
+// with dz = 0 at (dx, dy) = (-1,-1), (1,-1), (-1,1), (1,1); k = 4..7 those with dy = 0 at
+// (dx, dz); k = 8..11 those with dx = 0 at (dy, dz), each -1/12 of the two conductivities that
+// share the diagonal; k = 12: a_vv = (1/3) sum of the eight around v.
+__host__ __device__ __forceinline__ int64_t q1_coef_offset(const Q1Op& A) {
+  const int64_t ncell = (int64_t)(A.nx + 1) * (A.ny + 1) * (A.nz + 1);
+  return (ncell + 31) / 32 * 32;
+}
+
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -175,8 +186,8 @@ __device__ __forceinline__ void q1_march(const Q1Op& A, const T* __restrict__ ka
   }
 }
 
-// (A u)_v in FP64 from the vertex's precomputed coefficients (k_q1_coef: a_vv and the twelve
-// face-diagonal entries, -1/12 of a pair sum each) and the staged planes; the body diagonals
+// (A u)_v in FP64 from the vertex's precomputed coefficients (a_vv and the twelve face-diagonal
+// entries, -1/12 of a pair sum each, written by k_q1_setup) and the staged planes; the body diagonals
 // take the conductivities of the staged cell planes.  22 FP64 operations per vertex instead of
 // the 38 of q1_vertex: the FP64 kernels are bound by the FP64 pipe, HBM has room for the
 // 104 bytes of coefficients.
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(QT) k_q1(Q1Op A, EpiArgs e, int zc) {
   };
   auto vertex = [&](const double* Um, const double* Uc, const double* Up, const double* K0,
                     const double* K1, int tx, int ty, int64_t i, double& uc) -> double {
-    return q1_vertex_coef(A.coef, n, Um, Uc, Up, K0, K1, tx, ty, i, uc);
+    return q1_vertex_coef(A.kappa + q1_coef_offset(A), n, Um, Uc, Up, K0, K1, tx, ty, i, uc);
   };
   q1_march<double>(A, A.kappa, A.nx + 1, zc, sh, load_u, vertex, [&](int64_t i, double yv, double uc, bool in) {
     if (!in) return;
@@ -510,41 +521,6 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
   }
 }
 
-// FP64 coefficients of every vertex, structure of arrays c[k * n + v]: k = 0..3 face diagonals
-// with dz = 0 at (dx, dy) = (-1,-1), (1,-1), (-1,1), (1,1); k = 4..7 with dy = 0 at
-// (dx, dz) in the same order; k = 8..11 with dx = 0 at (dy, dz); each -1/12 of the two
-// conductivities that share the diagonal.  k = 12: a_vv = (1/3) sum of the eight around v.
-__global__ void k_q1_coef(Q1Op A, double* c) {
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int64_t n = (int64_t)nx * ny * nz;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
-    double k[2][2][2];  // k[c][b][a]: cell (x + a, y + b, z + c)
-    for (int cc = 0; cc < 2; ++cc)
-      for (int b = 0; b < 2; ++b)
-        for (int a = 0; a < 2; ++a)
-          k[cc][b][a] = A.kappa[((int64_t)(z + cc) * (ny + 1) + (y + b)) * (nx + 1) + (x + a)];
-    const double w = -1.0 / 12.0;
-    double* o = c + v;
-    o[0 * n] = w * (k[0][0][0] + k[1][0][0]);
-    o[1 * n] = w * (k[0][0][1] + k[1][0][1]);
-    o[2 * n] = w * (k[0][1][0] + k[1][1][0]);
-    o[3 * n] = w * (k[0][1][1] + k[1][1][1]);
-    o[4 * n] = w * (k[0][0][0] + k[0][1][0]);
-    o[5 * n] = w * (k[0][0][1] + k[0][1][1]);
-    o[6 * n] = w * (k[1][0][0] + k[1][1][0]);
-    o[7 * n] = w * (k[1][0][1] + k[1][1][1]);
-    o[8 * n] = w * (k[0][0][0] + k[0][0][1]);
-    o[9 * n] = w * (k[0][1][0] + k[0][1][1]);
-    o[10 * n] = w * (k[1][0][0] + k[1][0][1]);
-    o[11 * n] = w * (k[1][1][0] + k[1][1][1]);
-    const double k8 = ((k[0][0][0] + k[1][0][0]) + (k[0][0][1] + k[1][0][1])) +
-                      ((k[0][1][0] + k[1][1][0]) + (k[0][1][1] + k[1][1][1]));
-    o[12 * n] = k8 / 3.0;
-  }
-}
-
 // FP32 conductivities with rows padded to kpitch (padding zero).
 __global__ void k_q1_kappaf(Q1Op A, float* out) {
   const int64_t rows = (int64_t)(A.ny + 1) * (A.nz + 1);
@@ -615,6 +591,23 @@ __global__ void __launch_bounds__(kThreads) k_q1_setup(Q1Op A, int jacobi, doubl
     for (int c = 0; c < 2; ++c)
       for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) k8 += kap(a, b, c);
+    {  // the FP64 kernels' vertex coefficients (layout at q1_coef_offset)
+      double* o = const_cast<double*>(A.kappa) + q1_coef_offset(A) + i;
+      const double w = -1.0 / 12.0;
+      o[0 * n] = w * (kap(0, 0, 0) + kap(0, 0, 1));
+      o[1 * n] = w * (kap(1, 0, 0) + kap(1, 0, 1));
+      o[2 * n] = w * (kap(0, 1, 0) + kap(0, 1, 1));
+      o[3 * n] = w * (kap(1, 1, 0) + kap(1, 1, 1));
+      o[4 * n] = w * (kap(0, 0, 0) + kap(0, 1, 0));
+      o[5 * n] = w * (kap(1, 0, 0) + kap(1, 1, 0));
+      o[6 * n] = w * (kap(0, 0, 1) + kap(0, 1, 1));
+      o[7 * n] = w * (kap(1, 0, 1) + kap(1, 1, 1));
+      o[8 * n] = w * (kap(0, 0, 0) + kap(1, 0, 0));
+      o[9 * n] = w * (kap(0, 1, 0) + kap(1, 1, 0));
+      o[10 * n] = w * (kap(0, 0, 1) + kap(1, 0, 1));
+      o[11 * n] = w * (kap(0, 1, 1) + kap(1, 1, 1));
+      o[12 * n] = k8 / 3.0;
+    }
     // interior neighbours at offsets with two or three non-zero components
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
@@ -664,16 +657,7 @@ int q1_grid_ctas(const Q1Op& A) {
   return (int)(g.grid.x * g.grid.y * g.grid.z);
 }
 
-cudaError_t launch_q1_coef(const Q1Op& A, double* coef, cudaStream_t st) {
-  const int64_t n = (int64_t)A.nx * A.ny * A.nz;
-  const int64_t want = (n + kThreads - 1) / kThreads;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * 8));
-  k_q1_coef<<<grid, kThreads, 0, st>>>(A, coef);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st) {
-  if (!A.coef) return cudaErrorInvalidValue;  // the FP64 kernels read the set-up coefficients
   switch (e.epi) {
     case EP_SPMV: return launch_epi<EP_SPMV>(A, e, st);
     case EP_MPK: return launch_epi<EP_MPK>(A, e, st);
