@@ -72,6 +72,8 @@ enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1, SSTEP_MATRIX_Q1 = 2 };
  *      three offsets of +-1 away; 0 for the six axis neighbours (21 entries per interior row).
  *      The same matrix as assembling the Q1 element stiffness kappa_e (K1 x M1 x M1 + M1 x K1 x
  *      M1 + M1 x M1 x K1), K1 = [[1,-1],[-1,1]], M1 = [[1/3,1/6],[1/6,1/3]], over the cells.
+ *      The library keeps a copy of kappa plus 13*n doubles of vertex coefficients (FP64
+ *      kernels) and, in the FP32-basis form, an FP32 copy of kappa.
  *      points is ignored; n may be 0 or nx*ny*nz.  Preconditioners NONE and JACOBI; the
  *      FP64 and FP32-basis s-step forms and PCG.  In the FP32-basis form with nx a multiple
  *      of 4 (nx >= 72, ny >= 10) the middle MPK steps are fed by tensor-memory-accelerator
