@@ -12,8 +12,10 @@
 //   face diagonal (two offsets of +-1): -(1/12) (sum of the 2 kappa sharing that face diagonal),
 //   body diagonal (three offsets of +-1): -(1/12) (kappa of the one cell between them),
 //   axis neighbours: 0.
-// So a row holds 21 entries, and one application reads one conductivity per cell and one
-// value per vertex (8 bytes per vertex in FP32) where the assembled CSR matrix reads about 170.
+// So a row holds 21 entries.  The FP32 MPK step forms them on the fly and reads one
+// conductivity per cell and one value per vertex (8 bytes per vertex) where the assembled CSR
+// matrix reads about 170; the FP64 kernels, bound by the FP64 pipe rather than by HBM, read
+// the 13 vertex coefficients the set-up pass stored (22 FP64 operations per vertex, not 38).
 //
 // Tiling.  A CTA owns 32 x 8 vertices of the xy plane and marches through a chunk of z planes:
 // u planes z-1, z, z+1 (one-vertex xy halo) and cell planes z, z+1 are staged in shared memory
