@@ -5,9 +5,10 @@ baseline leg of the benchmark; the CUDA library and its Python binding never imp
 It shares no code with the CUDA path: the arithmetic lives in ``oracle.c`` (plain C,
 sequential loops, FP64), written from the paper:
 
-* ``mpk``      -- Algorithm 2 (Matrix Powers Kernel for the Chebyshev basis), Section 2
+* ``mpk``      -- the Chebyshev basis of Section 2 by its three-term recurrence (Algorithm 2)
 * ``fgs``      -- Eq. (fgs-iteration), Section 3.1 (forward Gauss-Seidel on W)
-* ``pcgs``     -- Algorithm 1 (PCG-S), literal form and one-reduction form
+* ``reduced_relres`` -- eta_alpha / eta_beta of Section 3.3
+* ``pcgs``     -- PCG-S (Section 2, Algorithm 1), literal form and one-reduction form
 * ``pcg``      -- classical Hestenes-Stiefel PCG (Section 1)
 * ``power``    -- power method for lambda_max, Section 2
 * ``cheb``     -- Chebyshev scalars alpha, sigma, gamma, Section 2
@@ -66,6 +67,8 @@ def _load():
         lib.or_chol_solve.argtypes = [C.c_int, P, P, P]
         lib.or_chol_solve.restype = C.c_int
         lib.or_gram.argtypes = [C.c_int64, C.c_int, P, C.c_int, P, P]
+        lib.or_reduced_relres.argtypes = [C.c_int, C.c_int, P, P, P]
+        lib.or_reduced_relres.restype = C.c_double
         lib.or_pcgs.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.c_int, C.c_double, C.c_double, P, C.c_int, C.c_double, P, P, P, P]
         lib.or_pcgs.restype = C.c_int
@@ -217,6 +220,19 @@ def gram(X, Y) -> np.ndarray:
     G = np.empty((b, a))  # column-major a x b == row-major (b, a)
     _load().or_gram(n, a, _ptr(X), b, _ptr(Y), _ptr(G))
     return G.T.copy()
+
+
+def reduced_relres(W, M, X) -> float:
+    """||M - W X|| / ||M|| (Section 3.3: eta_alpha for one column, eta_beta as the Frobenius
+    form for an s x ncol block).  M, X: (s,) or (s, ncol)."""
+    W = np.asfortranarray(W, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    ncol = 1 if M.ndim == 1 else M.shape[1]
+    Mf = np.asfortranarray(M.reshape(W.shape[0], ncol))
+    Xf = np.asfortranarray(np.asarray(X, dtype=np.float64).reshape(W.shape[0], ncol))
+    return float(_load().or_reduced_relres(W.shape[0], ncol, W.ctypes.data_as(C.c_void_p),
+                                           Mf.ctypes.data_as(C.c_void_p),
+                                           Xf.ctypes.data_as(C.c_void_p)))
 
 
 class Result:

@@ -1,11 +1,13 @@
 /*
- * oracle.c -- plain sequential FP64 restatement of PCG-S (Algorithm 1 + Algorithm 2 of
+ * oracle.c -- plain sequential FP64 restatement of PCG-S (the s-step PCG of Section 2 of
  * "Scalable s-step Preconditioned Conjugate Gradient with Chebyshev Basis and Gauss-Seidel
- * Gram Solve") and of classical PCG.
+ * Gram Solve": Chebyshev basis, reduced Gram systems, FGS of Section 3.1, block updates) and
+ * of classical PCG.
  *
  * TEST INFRASTRUCTURE ONLY: loaded by the test suite, the smoke check and the CPU-baseline
- * leg of the benchmark; never by the CUDA library.  Loops are the definitions written out,
- * in the order the paper states them; no blocking, fusion or reordering.
+ * leg of the benchmark; never by the CUDA library.  Each operation is its defining formula
+ * written out as a loop, taken in the order the method states them; no blocking, fusion or
+ * reordering.
  */
 #include "oracle.h"
 
@@ -111,40 +113,50 @@ void or_cheb_scalars(double lmin, double lmax, double* c_alpha, double* c_sigma,
   *c_gamma = 1.0;
 }
 
-/* ---------------------------------------------------------------- Algorithm 2 (MPK) */
+/* ---------------------------------------------------------------- Chebyshev basis (Section 2) */
 
+/* The s-column Chebyshev basis of Section 2, z_j = T_{j-1}(A_hat) M^{-1} r (j = 1..s) with
+ * A_hat = c_alpha M^{-1}A - c_sigma I, and its products with A.
+ *
+ * T_0 = 1, T_1(t) = t and T_{j+1}(t) = 2t T_j(t) - T_{j-1}(t) give, multiplied through by M,
+ * a recurrence on w_j = M z_j that needs one product with A and one application of M^{-1}
+ * per new column (the form of Algorithm 2, whose name for w_j is zp_j):
+ *   w_1     = r
+ *   w_2     = c_alpha (A z_1) - c_sigma w_1
+ *   w_{j+1} = 2 c_alpha (A z_j) - 2 c_sigma w_j - c_gamma w_{j-1}       (j >= 2)
+ *   z_j     = M^{-1} w_j.
+ * Outputs Z = [z_1 .. z_s] and P = [r, A z_1, .., A z_s] (n x (s+1)), as Algorithm 2 does. */
 int or_mpk(const or_csr* A, int prec, const double* dinv, const double* r, int s,
            double c_alpha, double c_sigma, double c_gamma, double* Z, double* P) {
   if (s < 1) return OR_ERR_INVALID;
   int64_t n = A->n;
-  double* zp = (double*)malloc(sizeof(double) * n * (size_t)s); /* zp_1 .. zp_s */
-#define ZC(j) (Z + (size_t)(j) * n)
-#define PC(j) (P + (size_t)(j) * n)
-#define ZPC(j) (zp + (size_t)(j) * n)
-  /* p_1 = r; zp_1 = p_1; z_1 = M^{-1} zp_1 */
-  memcpy(PC(0), r, sizeof(double) * n);
-  memcpy(ZPC(0), PC(0), sizeof(double) * n);
-  or_prec_apply(prec, n, dinv, ZPC(0), ZC(0));
-  if (s > 1) {
-    /* p_2 = A z_1; zp_2 = c_alpha p_2 - c_sigma zp_1; z_2 = M^{-1} zp_2 */
-    or_spmv(A, ZC(0), PC(1));
-    for (int64_t i = 0; i < n; ++i) ZPC(1)[i] = c_alpha * PC(1)[i] - c_sigma * ZPC(0)[i];
-    or_prec_apply(prec, n, dinv, ZPC(1), ZC(1));
-    /* q = 2 .. s-1 (1-based): three-term Chebyshev recurrence */
-    for (int q = 2; q <= s - 1; ++q) {
-      double* pq1 = PC(q);          /* p_{q+1} */
-      or_spmv(A, ZC(q - 1), pq1);   /* p_{q+1} = A z_q */
-      for (int64_t i = 0; i < n; ++i)
-        ZPC(q)[i] = 2.0 * c_alpha * pq1[i] - 2.0 * c_sigma * ZPC(q - 1)[i] - c_gamma * ZPC(q - 2)[i];
-      or_prec_apply(prec, n, dinv, ZPC(q), ZC(q));
+  double* w = (double*)malloc(sizeof(double) * n * (size_t)s); /* w_1 .. w_s */
+  /* columns are 1-based: Z_(j) = z_j, AZ_(j) = A z_j = P(:, j+1), W_(j) = w_j */
+#define Z_(j) (Z + (size_t)((j) - 1) * n)
+#define AZ_(j) (P + (size_t)(j) * n)
+#define W_(j) (w + (size_t)((j) - 1) * n)
+  memcpy(P, r, sizeof(double) * n);
+  for (int j = 1; j <= s; ++j) {
+    double* wj = W_(j);
+    if (j == 1) {
+      memcpy(wj, r, sizeof(double) * n);
+    } else if (j == 2) {  /* T_1(t) = t: no doubling, no c_gamma term */
+      const double* az = AZ_(1);
+      const double* wm1 = W_(1);
+      for (int64_t i = 0; i < n; ++i) wj[i] = c_alpha * az[i] - c_sigma * wm1[i];
+    } else {              /* three-term recurrence */
+      const double* az = AZ_(j - 1);
+      const double* wm1 = W_(j - 1);
+      const double* wm2 = W_(j - 2);
+      for (int64_t i = 0; i < n; ++i) wj[i] = 2.0 * c_alpha * az[i] - 2.0 * c_sigma * wm1[i] - c_gamma * wm2[i];
     }
+    or_prec_apply(prec, n, dinv, wj, Z_(j));  /* z_j = M^{-1} w_j */
+    or_spmv(A, Z_(j), AZ_(j));                /* A z_j            */
   }
-  /* p_{s+1} = A z_s */
-  or_spmv(A, ZC(s - 1), PC(s));
-#undef ZC
-#undef PC
-#undef ZPC
-  free(zp);
+#undef Z_
+#undef AZ_
+#undef W_
+  free(w);
   return OR_OK;
 }
 
@@ -225,9 +237,10 @@ static int reduced_solve_block(int gram, int s, const double* W, const double* R
   return OR_OK;
 }
 
-/* Relative residual ||m - W a|| / ||m|| (Section 3.3, eta_alpha); block version uses the
- * Frobenius norm over all columns (eta_beta). */
-static double reduced_relres(int s, int ncol, const double* W, const double* M, const double* X) {
+/* Relative residual of a reduced solve (Section 3.3): ||M - W X|| / ||M||, the 2-norm for one
+ * right-hand side (eta_alpha) and the Frobenius norm over the ncol columns of a block
+ * (eta_beta).  0 when M = 0. */
+double or_reduced_relres(int s, int ncol, const double* W, const double* M, const double* X) {
   double num = 0.0, den = 0.0;
   for (int c = 0; c < ncol; ++c)
     for (int i = 0; i < s; ++i) {
@@ -247,8 +260,106 @@ static int check_gram(int s, const double* W) {
   return OR_OK;
 }
 
-/* ---------------------------------------------------------------- Algorithm 1 (PCG-S) */
+/* ---------------------------------------------------------------- PCG-S (Section 2, Algorithm 1) */
 
+/* The operations of one outer iteration, each as Section 2 defines it.  Blocks are n x s,
+ * column-major; s x s matrices are column-major. */
+
+/* Reduced system for the step (Section 2): W_k = Q_k^T A Q_k, m_k = Q_k^T r^(k). */
+static void step_system(int64_t n, int s, const double* Q, const double* AQ, const double* r,
+                        double* W, double* m) {
+  or_gram(n, s, Q, s, AQ, W);
+  or_gram(n, s, Q, 1, r, m);
+}
+
+/* New iterate and residual (Section 2): x^(k+1) = x^(k) + Q_k alpha_k,
+ * r^(k+1) = r^(k) - (A Q_k) alpha_k. */
+static void advance_iterate(int64_t n, int s, const double* Q, const double* AQ,
+                            const double* alpha, double* x, double* r) {
+  for (int64_t i = 0; i < n; ++i) {
+    double dx = 0.0, dr = 0.0;
+    for (int j = 0; j < s; ++j) { dx += Q[i + (size_t)j * n] * alpha[j]; dr += AQ[i + (size_t)j * n] * alpha[j]; }
+    x[i] += dx;
+    r[i] -= dr;
+  }
+}
+
+/* Right-hand sides of the conjugation system W_k beta_k = -Q_k^T A Z_{k+1} (Section 2: the
+ * condition Q_{k+1}^T A Q_k = 0 with Q_{k+1} = Z_{k+1} + Q_k beta_k and W_k symmetric). */
+static void conjugation_rhs(int64_t n, int s, const double* Q, const double* AZ, double* B) {
+  or_gram(n, s, Q, s, AZ, B);
+  for (int i = 0; i < s * s; ++i) B[i] = -B[i];
+}
+
+/* Next direction block, Eq. (blockdirupdate), and its product with A without a new SpMV
+ * (Section 2): Q_{k+1} = Z_{k+1} + Q_k beta_k, A Q_{k+1} = A Z_{k+1} + (A Q_k) beta_k.
+ * Qn, AQn: n x s work blocks; the result is copied back into Q, AQ. */
+static void next_directions(int64_t n, int s, const double* Z, const double* AZ, const double* beta,
+                            double* Q, double* AQ, double* Qn, double* AQn) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < s; ++j) {
+      double vq = Z[i + (size_t)j * n], va = AZ[i + (size_t)j * n];
+      for (int l = 0; l < s; ++l) {
+        vq += Q[i + (size_t)l * n] * beta[l + (size_t)j * s];
+        va += AQ[i + (size_t)l * n] * beta[l + (size_t)j * s];
+      }
+      Qn[i + (size_t)j * n] = vq;
+      AQn[i + (size_t)j * n] = va;
+    }
+  memcpy(Q, Qn, sizeof(double) * n * s);
+  memcpy(AQ, AQn, sizeof(double) * n * s);
+}
+
+/* One-reduction form: every product the next step needs, taken in one pass over the current
+ * vectors Q_k, Z_{k+1}, AQ_k, AZ_{k+1}, r^(k+1):
+ *   G1 = Q_k^T AQ_k, G2 = Q_k^T AZ_{k+1}, G3 = Z_{k+1}^T AQ_k, G4 = Z_{k+1}^T AZ_{k+1},
+ *   g5 = Q_k^T r^(k+1), g6 = Z_{k+1}^T r^(k+1).
+ * With Q_{k+1} = Z_{k+1} + Q_k beta_k (Eq. blockdirupdate) the next reduced system follows on
+ * s x s data:
+ *   W_{k+1} = Q_{k+1}^T A Q_{k+1} = G4 + G3 beta + beta^T G2 + beta^T G1 beta,
+ *   m_{k+1} = Q_{k+1}^T r^(k+1)   = g6 + beta^T g5. */
+static void onesync_products(int64_t n, int s, const double* Q, const double* AQ, const double* Z,
+                             const double* AZ, const double* r, double* G1, double* G2,
+                             double* G3, double* G4, double* g5, double* g6) {
+  or_gram(n, s, Q, s, AQ, G1);
+  or_gram(n, s, Q, s, AZ, G2);
+  or_gram(n, s, Z, s, AQ, G3);
+  or_gram(n, s, Z, s, AZ, G4);
+  or_gram(n, s, Q, 1, r, g5);
+  or_gram(n, s, Z, 1, r, g6);
+}
+
+static void onesync_next_system(int s, const double* G1, const double* G2, const double* G3,
+                                const double* G4, const double* g5, const double* g6,
+                                const double* beta, double* T, double* W, double* m) {
+  for (int j = 0; j < s; ++j)       /* T = G1 beta */
+    for (int i = 0; i < s; ++i) {
+      double v = 0.0;
+      for (int l = 0; l < s; ++l) v += G1[i + (size_t)l * s] * beta[l + (size_t)j * s];
+      T[i + (size_t)j * s] = v;
+    }
+  for (int j = 0; j < s; ++j)
+    for (int i = 0; i < s; ++i) {
+      double v = G4[i + (size_t)j * s];
+      for (int l = 0; l < s; ++l) {
+        v += G3[i + (size_t)l * s] * beta[l + (size_t)j * s];
+        v += beta[l + (size_t)i * s] * G2[l + (size_t)j * s];
+        v += beta[l + (size_t)i * s] * T[l + (size_t)j * s];
+      }
+      W[i + (size_t)j * s] = v;
+    }
+  for (int i = 0; i < s; ++i) {
+    double v = g6[i];
+    for (int l = 0; l < s; ++l) v += beta[l + (size_t)i * s] * g5[l];
+    m[i] = v;
+  }
+}
+
+/* PCG-S: the outer iteration of Section 2 in the order Algorithm 1 takes it.  Per outer
+ * iteration k: the step alpha_k from the reduced system (W_k, m_k) by nu FGS sweeps or
+ * exactly; x and r advanced; the stop test ||r^(k+1)|| <= rtol ||b||; the Chebyshev basis
+ * Z_{k+1} of r^(k+1); beta_k from W_k beta_k = -Q_k^T A Z_{k+1} with the same W_k; the next
+ * direction block.  The first block is the basis itself, Q_0 = Z_0. */
 int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
             int s, int nu, double rtol, int max_outer, int algo, int gram,
             double lambda_min, double lambda_max, const double* power_v0, int power_iters,
@@ -275,10 +386,11 @@ int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
   double* B2 = (double*)malloc(sizeof(double) * s * s);
   double* beta = (double*)malloc(sizeof(double) * s * s);
   double* T = (double*)malloc(sizeof(double) * s * s);
-  double* b1 = (double*)malloc(sizeof(double) * s);
+  double* m = (double*)malloc(sizeof(double) * s);
   double* g5 = (double*)malloc(sizeof(double) * s);
   double* g6 = (double*)malloc(sizeof(double) * s);
   double* alpha = (double*)malloc(sizeof(double) * s);
+  const double* AZ = P + n;  /* A Z = P(:, 2:s+1) */
   int st = OR_OK;
 
   if (prec == OR_PREC_JACOBI) {
@@ -302,7 +414,7 @@ int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
     goto done;
   }
 
-  /* line 1: r^(0) = b - A x^(0) */
+  /* initial residual r^(0) = b - A x^(0) */
   or_spmv(A, x, t);
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
   double nr = nrm2(n, r);
@@ -310,103 +422,47 @@ int or_pcgs(const or_csr* A, int prec, const double* b, double* x,
   if (!isfinite(nr)) { st = OR_ERR_NONFINITE; goto done; }
   if (nr <= rtol * nb) { inf.iters = 0; inf.relres = nr / nb; st = OR_OK; goto finish; }
 
-  /* line 2-3: [Z, P] = MPK(r^(0)); Q = Z; AQ = P(:, 2:end) */
+  /* first block: Q_0 = Z_0, the Chebyshev basis of r^(0) */
   or_mpk(A, prec, dinv, r, s, inf.c_alpha, inf.c_sigma, inf.c_gamma, Z, P);
   memcpy(Q, Z, sizeof(double) * n * s);
-  memcpy(AQ, P + n, sizeof(double) * n * s);
-  /* one-sync form, first pass: W_0 = Z^T AZ, b1 = Z^T r */
-  if (algo == OR_ALGO_ONESYNC) {
-    or_gram(n, s, Z, s, P + n, W);
-    or_gram(n, s, Z, 1, r, b1);
-  }
+  memcpy(AQ, AZ, sizeof(double) * n * s);
+  if (algo == OR_ALGO_ONESYNC) step_system(n, s, Z, AZ, r, W, m);
 
   st = OR_NOT_CONVERGED;
   for (int k = 0; k < max_outer; ++k) {
-    if (algo == OR_ALGO_LITERAL) {
-      /* line 5: W = Q^T AQ, b1 = Q^T P(:,1), where P(:,1) = r^(k) (Algorithm 2, first line) */
-      or_gram(n, s, Q, s, AQ, W);
-      or_gram(n, s, Q, 1, r, b1);
-    }
+    /* step: alpha_k ~ W_k^{-1} m_k */
+    if (algo == OR_ALGO_LITERAL) step_system(n, s, Q, AQ, r, W, m);
     int cs = check_gram(s, W);
     if (cs != OR_OK) { st = cs; break; }
-    /* line 6: alpha = FGS(W, b1, nu) */
-    cs = reduced_solve(gram, s, W, b1, nu, alpha);
+    cs = reduced_solve(gram, s, W, m, nu, alpha);
     if (cs != OR_OK) { st = cs; break; }
-    if (eta_a) eta_a[k] = reduced_relres(s, 1, W, b1, alpha);
-    /* line 7-8: x += Q alpha; r -= AQ alpha */
-    for (int64_t i = 0; i < n; ++i) {
-      double dx = 0.0, dr = 0.0;
-      for (int j = 0; j < s; ++j) { dx += Q[i + (size_t)j * n] * alpha[j]; dr += AQ[i + (size_t)j * n] * alpha[j]; }
-      x[i] += dx;
-      r[i] -= dr;
-    }
+    if (eta_a) eta_a[k] = or_reduced_relres(s, 1, W, m, alpha);
+
+    advance_iterate(n, s, Q, AQ, alpha, x, r);
     inf.iters = k + 1;
     nr = nrm2(n, r);
     if (hist) hist[k + 1] = nr / nb;
-    /* line 9: stop test on the recursively updated residual */
+    /* stop test on the recursively updated residual */
     if (!isfinite(nr)) { st = OR_ERR_NONFINITE; break; }
     if (nr <= rtol * nb) { st = OR_OK; break; }
     if (k + 1 == max_outer) break;
 
-    /* line 10-11: [Z, P] = MPK(r^(k+1)); AQ_new = P(:, 2:end) */
+    /* Chebyshev basis of r^(k+1): Z_{k+1}, A Z_{k+1} */
     or_mpk(A, prec, dinv, r, s, inf.c_alpha, inf.c_sigma, inf.c_gamma, Z, P);
-    const double* AZ = P + n;
+
+    /* conjugation: W_k beta_k = -Q_k^T A Z_{k+1} */
     if (algo == OR_ALGO_LITERAL) {
-      /* line 12-13: b2 = -Q^T AQ_new; beta = FGS(W, b2, nu) */
-      or_gram(n, s, Q, s, AZ, B2);
-      for (int i = 0; i < s * s; ++i) B2[i] = -B2[i];
-      cs = reduced_solve_block(gram, s, W, B2, nu, beta);
-      if (cs != OR_OK) { st = cs; break; }
-      if (eta_b) eta_b[k] = reduced_relres(s, s, W, B2, beta);
+      conjugation_rhs(n, s, Q, AZ, B2);
     } else {
-      /* one reduction over [Q_k, Z_{k+1}] against [AQ_k, AZ_{k+1}, r^(k+1)] */
-      or_gram(n, s, Q, s, AQ, G1);   /* Q_k^T AQ_k       */
-      or_gram(n, s, Q, s, AZ, G2);   /* Q_k^T AZ_{k+1}   */
-      or_gram(n, s, Z, s, AQ, G3);   /* Z_{k+1}^T AQ_k   */
-      or_gram(n, s, Z, s, AZ, G4);   /* Z_{k+1}^T AZ_{k+1} */
-      or_gram(n, s, Q, 1, r, g5);    /* Q_k^T r^(k+1)    */
-      or_gram(n, s, Z, 1, r, g6);    /* Z_{k+1}^T r^(k+1) */
+      onesync_products(n, s, Q, AQ, Z, AZ, r, G1, G2, G3, G4, g5, g6);
       for (int i = 0; i < s * s; ++i) B2[i] = -G2[i];
-      cs = reduced_solve_block(gram, s, W, B2, nu, beta); /* W = W_k, as in line 13 */
-      if (cs != OR_OK) { st = cs; break; }
-      if (eta_b) eta_b[k] = reduced_relres(s, s, W, B2, beta);
-      /* W_{k+1} = (Z + Q beta)^T (AZ + AQ beta) = G4 + G3 beta + beta^T G2 + beta^T G1 beta */
-      for (int j = 0; j < s; ++j)       /* T = G1 beta */
-        for (int i = 0; i < s; ++i) {
-          double v = 0.0;
-          for (int l = 0; l < s; ++l) v += G1[i + (size_t)l * s] * beta[l + (size_t)j * s];
-          T[i + (size_t)j * s] = v;
-        }
-      for (int j = 0; j < s; ++j)
-        for (int i = 0; i < s; ++i) {
-          double v = G4[i + (size_t)j * s];
-          for (int l = 0; l < s; ++l) {
-            v += G3[i + (size_t)l * s] * beta[l + (size_t)j * s];
-            v += beta[l + (size_t)i * s] * G2[l + (size_t)j * s];
-            v += beta[l + (size_t)i * s] * T[l + (size_t)j * s];
-          }
-          W[i + (size_t)j * s] = v;
-        }
-      /* b1 = Q_{k+1}^T r^(k+1) = g6 + beta^T g5 */
-      for (int i = 0; i < s; ++i) {
-        double v = g6[i];
-        for (int l = 0; l < s; ++l) v += beta[l + (size_t)i * s] * g5[l];
-        b1[i] = v;
-      }
     }
-    /* line 15: Q = Z + Q beta; AQ = AQ_new + AQ beta */
-    for (int64_t i = 0; i < n; ++i)
-      for (int j = 0; j < s; ++j) {
-        double vq = Z[i + (size_t)j * n], va = AZ[i + (size_t)j * n];
-        for (int l = 0; l < s; ++l) {
-          vq += Q[i + (size_t)l * n] * beta[l + (size_t)j * s];
-          va += AQ[i + (size_t)l * n] * beta[l + (size_t)j * s];
-        }
-        Qn[i + (size_t)j * n] = vq;
-        AQn[i + (size_t)j * n] = va;
-      }
-    memcpy(Q, Qn, sizeof(double) * n * s);
-    memcpy(AQ, AQn, sizeof(double) * n * s);
+    cs = reduced_solve_block(gram, s, W, B2, nu, beta);
+    if (cs != OR_OK) { st = cs; break; }
+    if (eta_b) eta_b[k] = or_reduced_relres(s, s, W, B2, beta);
+    if (algo == OR_ALGO_ONESYNC) onesync_next_system(s, G1, G2, G3, G4, g5, g6, beta, T, W, m);
+
+    next_directions(n, s, Z, AZ, beta, Q, AQ, Qn, AQn);
   }
 
 finish:
@@ -422,7 +478,7 @@ done:
   if (info) *info = inf;
   free(dinv); free(r); free(t); free(Z); free(P); free(Q); free(AQ); free(Qn); free(AQn);
   free(W); free(G1); free(G2); free(G3); free(G4); free(B2); free(beta); free(T);
-  free(b1); free(g5); free(g6); free(alpha);
+  free(m); free(g5); free(g6); free(alpha);
   return st;
 }
 

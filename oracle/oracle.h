@@ -9,7 +9,8 @@
  *
  * Every routine is written as the paper states it ("Scalable s-step Preconditioned
  * Conjugate Gradient with Chebyshev Basis and Gauss-Seidel Gram Solve"):
- *   - Section 2, Algorithm 1 (PCG-S) and Algorithm 2 (MPK for the Chebyshev basis),
+ *   - Section 2: the PCG-S outer iteration (Algorithm 1) and the Chebyshev basis built by
+ *     its three-term recurrence (Algorithm 2),
  *   - Section 2, Chebyshev scalars alpha, sigma, gamma and the power method for lambda_max,
  *   - Section 3.1, Eq. (fgs-iteration): FGS on the Gram system (plain splitting of W),
  *   - Section 1 (PCG), textbook Hestenes-Stiefel preconditioned CG.
@@ -82,8 +83,15 @@ int or_chol_solve(int s, const double* W, const double* m, double* alpha);
 /* Gram products: G = X^T Y with X n x a, Y n x b (column-major), G a x b column-major. */
 void or_gram(int64_t n, int a, const double* X, int b, const double* Y, double* G);
 
-/* Algorithm 1 (PCG-S).  x holds x^(0) on entry and the solution on exit.
- * algo: OR_ALGO_LITERAL follows Algorithm 1 line by line (two reductions per outer iteration);
+/* Relative residual of a reduced solve (Section 3.3): ||M - W X|| / ||M|| over ncol columns
+ * (2-norm for ncol = 1: eta_alpha; Frobenius norm for a block: eta_beta).  W s x s, M and X
+ * s x ncol, column-major. */
+double or_reduced_relres(int s, int ncol, const double* W, const double* M, const double* X);
+
+/* PCG-S (Section 2, Algorithm 1).  x holds x^(0) on entry and the solution on exit.
+ * algo: OR_ALGO_LITERAL forms W_k = Q_k^T A Q_k and m_k = Q_k^T r^(k) after each direction
+ *       update and -Q_k^T A Z_{k+1} after each basis (two reductions per outer iteration),
+ *       as Algorithm 1 prints it;
  *       OR_ALGO_ONESYNC forms W_{k+1} from the Gram blocks of [Q_k, Z_{k+1}] and beta_k
  *       (algebraically identical; one reduction per outer iteration).
  * gram: OR_GRAM_FGS (nu sweeps) or OR_GRAM_CHOLESKY (exact reduced solves).

@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libsstep.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-Xcompiler", "-fvisibility=hidden"]
+         "-Xcompiler", "-fvisibility=hidden", "--split-compile=0"]
 
 
 def _nvcc() -> str:

@@ -233,6 +233,99 @@ def pin_fgs_prop1():
             assert np.allclose(rho, expect, atol=1e-12 * np.linalg.norm(mt)), (s, nu)
 
 
+def _prop1_residual(W, M, nu):
+    """m - W alpha^(nu) for each column m of M, from Proposition 1 alone: with
+    D = diag(W), W_c = D^{-1/2} W D^{-1/2} = I + L + L^T and m_tilde = D^{-1/2} m, the
+    normalised residual after nu sweeps from 0 is (-1)^nu (L^T (I+L)^{-1})^nu m_tilde, and
+    m - W alpha = D^{1/2} times it."""
+    s = W.shape[0]
+    d = np.sqrt(np.diag(W))
+    L = np.tril(W / np.outer(d, d), -1)
+    H = L.T @ np.linalg.inv(np.eye(s) + L)
+    Mt = np.asarray(M, dtype=np.float64).reshape(s, -1) / d[:, None]
+    return d[:, None] * (((-1) ** nu) * np.linalg.matrix_power(H, nu) @ Mt)
+
+
+def _eta_prop1(W, M, nu):
+    """Section 3.3's eta (2-norm for one column, Frobenius for a block) from Proposition 1."""
+    R = _prop1_residual(W, M, nu)
+    return np.linalg.norm(R) / np.linalg.norm(np.asarray(M, dtype=np.float64))
+
+
+def _fgs_splitting(W, m, nu):
+    """nu forward Gauss-Seidel sweeps from 0 in matrix form, (D + L_W) a_new = m - L_W^T a."""
+    DL = np.tril(W)
+    U = np.triu(W, 1)
+    a = np.zeros_like(m)
+    for _ in range(nu):
+        a = np.linalg.solve(DL, m - U @ a)
+    return a
+
+
+def pin_eta_closed_form():
+    """eta_alpha and eta_beta (Section 3.3) after nu FGS sweeps equal the closed form of
+    Proposition 1; nu = 0 gives 1; exact (Cholesky) solves give ~0."""
+    rng = np.random.default_rng(41)
+    for s in (2, 4, 7):
+        W = _spd(s, rng, cond=50.0)
+        m = rng.standard_normal(s)
+        B = rng.standard_normal((s, s))
+        for nu in (0, 1, 2, 3, 30):
+            a = O.fgs(W, m, nu)
+            e = O.reduced_relres(W, m, a)
+            assert abs(e - _eta_prop1(W, m, nu)) <= 1e-12 * max(1.0, e), (s, nu)
+            X = np.column_stack([O.fgs(W, B[:, c], nu) for c in range(s)])
+            eb = O.reduced_relres(W, B, X)
+            assert abs(eb - _eta_prop1(W, B, nu)) <= 1e-12 * max(1.0, eb), (s, nu)
+        assert O.reduced_relres(W, m, np.zeros(s)) == 1.0
+        assert O.reduced_relres(W, m, O.chol_solve(W, m)) < 1e-13
+        X = np.column_stack([O.chol_solve(W, B[:, c]) for c in range(s)])
+        assert O.reduced_relres(W, B, X) < 1e-13
+
+
+def pin_eta_in_pcgs():
+    """The eta_alpha_k, eta_beta_k that PCG-S records are Section 3.3's residuals of its own
+    reduced systems: W_k = Q_k^T A Q_k with m_k = Q_k^T r^(k), and the conjugation system
+    W_k beta_k = -Q_k^T A Z_{k+1} solved with the same W_k.  Everything on the right-hand side
+    is built here from a dense A: the Chebyshev basis by numpy on the eigendecomposition of
+    D^{-1/2} A D^{-1/2}, FGS in its matrix-splitting form, eta from Proposition 1."""
+    A = csr_of((5, 4, 3), 7, np.linspace(0.1, 1.3, 60))
+    Ad = A.dense()
+    n = A.n
+    dg = np.diag(Ad)
+    w, U = np.linalg.eigh(Ad / np.sqrt(np.outer(dg, dg)))
+    lmax = float(w.max()) * 1.01
+    ca, cs, cg = O.cheb(0.0, lmax)
+    rng = np.random.default_rng(43)
+    b = rng.standard_normal(n)
+
+    def basis(r, s):
+        y = U.T @ (r / np.sqrt(dg))
+        return np.column_stack([(U @ (cheb_T(j, ca * w - cs) * y)) / np.sqrt(dg) for j in range(s)])
+
+    for s, nu in ((3, 2), (4, 3)):
+        for algo in ("literal", "onesync"):
+            res = O.pcgs(A, b, s=s, nu=nu, rtol=0.0, max_outer=3, algo=algo, lambda_max=lmax,
+                         history=True)
+            r = b.copy()
+            Q = basis(r, s)
+            for k in range(3):
+                W = Q.T @ Ad @ Q
+                m = Q.T @ r
+                ea = _eta_prop1(W, m, nu)
+                assert abs(res.eta_a[k] - ea) <= 1e-9 * ea, (s, nu, algo, k, res.eta_a[k], ea)
+                a = _fgs_splitting(W, m, nu)
+                r = r - Ad @ (Q @ a)
+                if k == 2:
+                    break
+                Z = basis(r, s)
+                B = -(Q.T @ Ad @ Z)
+                eb = _eta_prop1(W, B, nu)
+                assert abs(res.eta_b[k] - eb) <= 1e-9 * eb, (s, nu, algo, k, res.eta_b[k], eb)
+                beta = np.column_stack([_fgs_splitting(W, B[:, c], nu) for c in range(s)])
+                Q = Z + Q @ beta
+
+
 def pin_fgs_limit_and_cholesky():
     """nu -> infinity: FGS converges to the dense solution (the Cholesky solve)."""
     rng = np.random.default_rng(19)

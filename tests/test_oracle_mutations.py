@@ -1,7 +1,8 @@
 """Plant plausible mistakes in a copy of the oracle's C source and check that a pin fails.
 
-Each mutation is a one-token slip of the kind a restatement of Algorithm 1, Algorithm 2,
-the FGS iteration or textbook PCG could contain.  The mutated copy is compiled into a
+Each mutation is a one-token slip of the kind a restatement of the PCG-S outer iteration,
+the Chebyshev basis recurrence, the FGS iteration, the reduced-solve residuals or textbook PCG
+could contain.  The mutated copy is compiled into a
 temporary directory; the committed oracle is never modified.
 """
 import os
@@ -34,12 +35,12 @@ MUTATIONS = {
     "spmv_reads_own_row": ("s += A->vals[k] * x[A->colind[k]];", "s += A->vals[k] * x[i];"),
     "jacobi_multiplies_by_diag": ("y[i] = dinv[i] * x[i];", "y[i] = x[i] / dinv[i];"),
     "cheb_sigma_inverted": ("*c_sigma = (lmax + lmin) / (lmax - lmin);", "*c_sigma = (lmax - lmin) / (lmax + lmin);"),
-    "mpk_first_step_doubled": ("ZPC(1)[i] = c_alpha * PC(1)[i] - c_sigma * ZPC(0)[i];",
-                               "ZPC(1)[i] = 2.0 * c_alpha * PC(1)[i] - c_sigma * ZPC(0)[i];"),
-    "mpk_recurrence_drops_2": ("ZPC(q)[i] = 2.0 * c_alpha * pq1[i]", "ZPC(q)[i] = c_alpha * pq1[i]"),
-    "mpk_recurrence_sign": ("- 2.0 * c_sigma * ZPC(q - 1)[i]", "+ 2.0 * c_sigma * ZPC(q - 1)[i]"),
-    "mpk_recurrence_index": ("c_gamma * ZPC(q - 2)[i]", "c_gamma * ZPC(q - 1)[i]"),
-    "mpk_missing_precond": ("or_prec_apply(prec, n, dinv, ZPC(q), ZC(q));", "memcpy(ZC(q), ZPC(q), sizeof(double) * n);"),
+    "mpk_first_step_doubled": ("wj[i] = c_alpha * az[i] - c_sigma * wm1[i];",
+                               "wj[i] = 2.0 * c_alpha * az[i] - c_sigma * wm1[i];"),
+    "mpk_recurrence_drops_2": ("wj[i] = 2.0 * c_alpha * az[i] - 2.0", "wj[i] = c_alpha * az[i] - 2.0"),
+    "mpk_recurrence_sign": ("- 2.0 * c_sigma * wm1[i] - c_gamma", "+ 2.0 * c_sigma * wm1[i] - c_gamma"),
+    "mpk_recurrence_index": ("const double* wm2 = W_(j - 2);", "const double* wm2 = W_(j - 1);"),
+    "mpk_missing_precond": ("or_prec_apply(prec, n, dinv, wj, Z_(j));", "memcpy(Z_(j), wj, sizeof(double) * n);"),
     "fgs_backward_sweep": ("for (int i = 0; i < s; ++i) {\n      double acc = m[i];",
                            "for (int i = s - 1; i >= 0; --i) {\n      double acc = m[i];"),
     "fgs_warm_start_ones": ("for (int i = 0; i < s; ++i) alpha[i] = 0.0;", "for (int i = 0; i < s; ++i) alpha[i] = 1.0;"),
@@ -52,7 +53,12 @@ MUTATIONS = {
     "onesync_quadratic_sign": ("v += beta[l + (size_t)i * s] * T[l + (size_t)j * s];",
                                "v -= beta[l + (size_t)i * s] * T[l + (size_t)j * s];"),
     "onesync_b1_drops_term": ("v += beta[l + (size_t)i * s] * g5[l];", "v += 0.0 * g5[l];"),
-    "literal_b2_sign": ("for (int i = 0; i < s * s; ++i) B2[i] = -B2[i];", "for (int i = 0; i < s * s; ++i) B2[i] = B2[i];"),
+    "literal_b2_sign": ("for (int i = 0; i < s * s; ++i) B[i] = -B[i];", "for (int i = 0; i < s * s; ++i) B[i] = B[i];"),
+    "eta_divides_by_product": ("den += M[i + (size_t)c * s] * M[i + (size_t)c * s];",
+                               "den += (M[i + (size_t)c * s] - v) * (M[i + (size_t)c * s] - v);"),
+    "eta_beta_last_column_only": ("num += v * v;", "num = v * v;"),
+    "eta_alpha_before_solve": ("if (eta_a) eta_a[k] = or_reduced_relres(s, 1, W, m, alpha);",
+                               "if (eta_a) eta_a[k] = or_reduced_relres(s, 1, W, m, m);"),
 }
 
 
