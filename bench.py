@@ -131,7 +131,7 @@ def kernel_work(s, n, points=7, sym_blocks=False):
     """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes).
 
     A multiply-add counts 2 flops.  Literal form (default): b2 = -Q^T AZ (s^2 products),
-    line 15 fused with W = Q^T AQ and b1 = Q^T r (2 s^2 + s^2 + s multiply-adds), x/r update
+    Q/AQ update fused with W = Q^T AQ and b1 = Q^T r (2 s^2 + s^2 + s multiply-adds), x/r update
     (2 s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products, or 2 s^2 + 3 s with
     the symmetric shortcut) and one update pass (2 s^2 + 2 s + 1)."""
     V = 8.0 * n

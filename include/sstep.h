@@ -113,7 +113,7 @@ enum {
   SSTEP_ALGO_ONESYNC = 0, /* Algorithm 1 with the Gram blocks of [Q_k, Z_{k+1}] formed in one
                              reduction per outer iteration (W_{k+1} assembled from them and beta) */
   SSTEP_ALGO_LITERAL = 1, /* Algorithm 1 as printed: W = Q^T AQ, b1 = Q^T r formed from the updated
-                             blocks (line 15 and lines 5-6 fused in one pass), b2 after the MPK.
+                             blocks (direction update and step system fused in one pass), b2 after the MPK.
                              Fewer FP64 products than the one-reduction form (2s^2 + s against
                              4s^2 + 2s per outer iteration); the default */
   SSTEP_ALGO_PCG = 2      /* classical preconditioned CG (Hestenes-Stiefel), the comparator */
@@ -123,7 +123,7 @@ enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1 };
 typedef struct {
   int s;              /* step size, 1 <= s <= 16 (Algorithm 1 "step size s") */
   int sweeps;         /* nu, FGS sweeps per reduced solve (Algorithm 1 "number of FGS sweeps") */
-  double rtol;        /* tau: stop when ||r|| <= tau ||b|| (Algorithm 1, line 9) */
+  double rtol;        /* tau: stop when ||r|| <= tau ||b|| (Algorithm 1's stop test) */
   int max_outer;      /* k_max (outer iterations; PCG: iterations) */
   int algo;           /* SSTEP_ALGO_* */
   int gram_solver;    /* SSTEP_GRAM_FGS, or SSTEP_GRAM_CHOLESKY (exact reduced solves, Section 3.3) */
@@ -257,7 +257,8 @@ SSTEP_API const char* sstep_last_error(void);
  * directly: z_{q+1} = 2 c_alpha M^{-1}(A z_q) - 2 c_sigma z_q - c_gamma z_{q-1}. */
 SSTEP_API sstep_status sstep_mpk(sstep_handle h, const double* r, double* Z, double* AZ, int s_override);
 
-/* Block Gram products (Algorithm 1 lines 5 and 12): for e = 0..ne-1,
+/* Block Gram products (the step system W = Q^T AQ and the conjugation right-hand sides
+ * -Q^T AZ of Section 2): for e = 0..ne-1,
  * out[e] = sum_i L[pairs[2e]][i] * R[pairs[2e+1]][i], i < n.  L: nl device pointers to n-vectors,
  * R: nr device pointers; pairs: 2*ne host ints; out: ne doubles (device).  nl, nr <= 40,
  * ne <= 512.  Deterministic: the same inputs and launch give bit-identical sums.
@@ -289,7 +290,7 @@ SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, const double*
 SSTEP_API sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu, int solver,
                        double* X, int* status_dev, void* stream);
 
-/* Algorithm 1 lines 7-8 and 15 fused: with beta (s x s) and alpha (s) in device memory,
+/* The block updates of Section 2 fused: with beta (s x s) and alpha (s) in device memory,
  * Q <- Z + Q beta, AQ <- AZ + AQ beta, x <- x + Q alpha, r <- r - AQ alpha (new Q, AQ),
  * and *rr_out = ||r||^2 (device double).  beta may be NULL (first outer iteration: Q <- Z,
  * AQ <- AZ).  Blocks have leading dimension n. */
@@ -330,7 +331,7 @@ SSTEP_API sstep_status sstep_get_history(sstep_handle h, double* relres, int max
  * stream: starting from x = 0 for right-hand side b (device or host, n doubles), runs the first
  * outer iteration and then `iters` more without a stop test, launched one by one.  ms (host,
  * 5 doubles) receives the averages per outer iteration of 4 phases and their sum:
- * literal form: [MPK (all s steps), b2 = -Q^T AZ with beta, line 15 fused with W, b1 and alpha,
+ * literal form: [MPK (all s steps), b2 = -Q^T AZ with beta, the Q/AQ update fused with W, b1 and alpha,
  * x/r update with the stop test]; one-reduction form: [MPK, Gram reduction with the reduced
  * solves, block update, 0]; PCG: [A p with p^T A p, x/r/z update, direction update, 0].
  * The handle's own x, r and basis blocks are overwritten. */

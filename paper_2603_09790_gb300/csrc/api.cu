@@ -118,7 +118,7 @@ sstep_status alloc(double** p, int64_t count) {
 // ---------------------------------------------------------------- kernel sequences
 
 // Every Gram block as computed (Algorithm 1), or the symmetric shortcut (opt-in, one-reduction
-// form only: the literal form always forms W = Q^T AQ in full, as line 5 prints it).
+// form only: the literal form always forms W = Q^T AQ in full, as Algorithm 1 prints it).
 int full_blocks(const sstep_ctx* h) {
   return (h->o.algo == SSTEP_ALGO_LITERAL || h->o.gram_solver == SSTEP_GRAM_CHOLESKY ||
           h->o.gram_blocks != SSTEP_GRAM_BLOCKS_SYM) ? 1 : 0;
@@ -264,8 +264,9 @@ sstep_status run_update(sstep_ctx* h, int mode) {
   return SSTEP_OK;
 }
 
-// Line 15 (Q <- Z + Q beta, AQ <- AZ + AQ beta; first: Q <- Z, AQ <- AZ as in line 3) followed
-// by lines 5-6 (W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)).  Fused in one pass for s <= 8.
+// Direction-block update, Eq. (blockdirupdate) (Q <- Z + Q beta, AQ <- AZ + AQ beta; first
+// block: Q <- Z, AQ <- AZ) followed by the step system of Section 2 (W = Q^T AQ, b1 = Q^T r,
+// alpha = FGS(W, b1)).  Fused in one pass for s <= 8.
 sstep_status run_upd_w(sstep_ctx* h, bool first) {
   UpdGramArgs a{h->n, h->ld, h->Z, h->AZ, h->Q, h->AQ, h->r, h->ctrl, h->partials};
   cudaError_t e = launch_upd_gram(a, h->s, first, h->st);
@@ -357,7 +358,8 @@ sstep_status run_rr(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
-// One outer iteration of the mixed literal form (lines 10-15, then 5-9).
+// One outer iteration of the mixed literal form (basis, conjugation, direction update, then
+// step system, x/r update and stop test).
 sstep_status mixed_outer(sstep_ctx* h) {
   const MixedArgs a = mixed_args(h);
   CKS(run_mpk_f32(h));
@@ -368,7 +370,7 @@ sstep_status mixed_outer(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
-// First outer iteration of the mixed form: lines 2-3 and 5-9.
+// First outer iteration of the mixed form: first block Q_0 = Z_0, step system, x/r update, stop test.
 sstep_status mixed_first(sstep_ctx* h) {
   const MixedArgs a = mixed_args(h);
   CKS(run_mpk_f32(h));
@@ -388,11 +390,11 @@ sstep_status outer_iteration(sstep_ctx* h, int algo) {
     CKS(run_gram(h, GM_ONESYNC));
     CKS(run_update(h, UM_FUSED));
   } else if (algo == SSTEP_ALGO_LITERAL) {
-    // One outer iteration of Algorithm 1 starting at line 10 (the first update ran before):
-    CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // lines 10-11
-    CKS(run_gram(h, GM_LITERAL_B2));                     // lines 12-13: b2, beta
-    CKS(run_upd_w(h, false));                            // line 15, then lines 5-6: W, b1, alpha
-    CKS(run_update(h, UM_XR));                           // lines 7-9
+    // One outer iteration of Algorithm 1 starting at the new basis (the first update ran before):
+    CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // basis of r^(k+1) (Algorithm 2)
+    CKS(run_gram(h, GM_LITERAL_B2));                     // conjugation: b2 = -Q^T AZ, beta
+    CKS(run_upd_w(h, false));                            // Q, AQ update, then W, b1, alpha
+    CKS(run_update(h, UM_XR));                           // x/r update and stop test
   } else {
     EpiArgs e = epi_base(h, EP_PCG_AP);
     e.u = h->p;
@@ -893,7 +895,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   }
   CKS(reset_ctrl(h));
   const int64_t launches0 = h->nlaunch;
-  // line 1: r^(0) = b - A x^(0); ||b||^2, ||r||^2 (mixed path: r kept as FP32 hi + lo)
+  // initial residual r^(0) = b - A x^(0); ||b||^2, ||r||^2 (mixed path: r kept as FP32 hi + lo)
   {
     EpiArgs e = epi_base(h, EP_RESID);
     e.u = h->x;
@@ -916,9 +918,9 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
     }
   } else if (algo == SSTEP_ALGO_LITERAL) {
     if (maxit > 0) {
-      CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // line 2
-      CKS(run_upd_w(h, true));                            // line 3, lines 5-6
-      CKS(run_update(h, UM_XR));                          // lines 7-9
+      CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // basis of r^(0)
+      CKS(run_upd_w(h, true));                            // Q_0 = Z_0; W, b1, alpha
+      CKS(run_update(h, UM_XR));                          // x/r update and stop test
     }
   } else {
     PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, h->hist};

@@ -3,7 +3,8 @@
 //
 // Each (system, right-hand side) pair is a "problem".  A thread-block cluster of C CTAs takes
 // the next problem from a device work queue (largest systems first) and runs Algorithm 1
-// (literal form: lines 5-6 fused with line 15, b2 after the MPK of Algorithm 2) on it to
+// (literal form: the step system fused with the direction-block update, b2 after the MPK of
+// Algorithm 2) on it to
 // convergence, then takes the next one.  The problem's unknowns are split into C contiguous
 // ranges, one per CTA; every reduction is a warp-shuffle and shared-memory sum inside each CTA,
 // then a fixed-order sum over the C CTAs' partials read through distributed shared memory
@@ -309,7 +310,7 @@ struct XR {
   float *rh, *rl, *xh, *xl;
 };
 
-// Lines 7-9: x += Q alpha, r -= AQ alpha, returns ||r||^2 (cluster sum).
+// x += Q alpha, r -= AQ alpha, returns ||r||^2 (cluster sum).
 template <int S, typename T>
 __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q, const T* AQ,
                             const XR& v, int64_t ld, Range rg) {
@@ -401,7 +402,7 @@ __device__ double update_xr(cg::cluster_group& cl, BSh<S>& sh, int& par, const T
   return sh.sums[0];
 }
 
-// Line 12-13: b2 = -Q^T AZ, beta = FGS(W, b2).  False on breakdown.
+// Conjugation: b2 = -Q^T AZ, beta = FGS(W, b2).  False on breakdown.
 template <int S, typename T>
 __device__ bool b2_beta(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q, const T* AZ,
                         int nu, int64_t ld, Range rg) {
@@ -466,8 +467,9 @@ __device__ bool b2_beta(cg::cluster_group& cl, BSh<S>& sh, int& par, const T* Q,
   return true;
 }
 
-// Line 15 (Q = Z + Q beta, AQ = AZ + AQ beta, written over Z, AZ; FIRST: Q = Z as is) fused
-// with lines 5-6 (W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)).  False on breakdown.
+// Direction-block update (Q = Z + Q beta, AQ = AZ + AQ beta, written over Z, AZ; FIRST: Q = Z
+// as is) fused with the step system (W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)).  False on
+// breakdown.
 template <int S, typename T, bool FIRST>
 __device__ bool upd_gram(cg::cluster_group& cl, BSh<S>& sh, int& par, T* Zn, T* AZn, const T* Qo,
                          const T* AQo, const XR& v, int nu, int64_t ld, Range rg) {
@@ -662,7 +664,7 @@ __device__ void solve_one(const BArgs& a, cg::cluster_group& cl, BSh<S>& sh, int
     cl.sync();
   };
 
-  // ---- line 1: r = b - A x0; ||b||^2
+  // ---- initial residual r = b - A x0; ||b||^2
   double v2[2];
   residual<2>(sy, pr.b, pr.x, v.r, v.rh, v.rl, rg, v2);
   if constexpr (kMixed)
@@ -684,13 +686,13 @@ __device__ void solve_one(const BArgs& a, cg::cluster_group& cl, BSh<S>& sh, int
   if (status < 0) {
     int qp = 0;  // the pair holding Q, AQ
     run_mpk(Zp(0), AZp(0));
-    // k = 0: Q_0 = Z_0 (line 3), W, b1, alpha (lines 5-6)
+    // k = 0: Q_0 = Z_0, W, b1, alpha
     if (!upd_gram<S, T, true>(cl, sh, par, Zp(0), AZp(0), nullptr, nullptr, v, a.nu, ld, rg))
       status = SSTEP_ERR_BREAKDOWN;
     while (status < 0) {
-      rr = update_xr<S, T>(cl, sh, par, Zp(qp), AZp(qp), v, ld, rg);  // lines 7-8
+      rr = update_xr<S, T>(cl, sh, par, Zp(qp), AZp(qp), v, ld, rg);  // x/r update
       ++iters;
-      status = stop_rule(rr, tol2, iters, a.max_outer);               // line 9
+      status = stop_rule(rr, tol2, iters, a.max_outer);               // stop test
       if constexpr (kMixed) {
         if (status < 0 && iters % a.rr_period == 0) {
           // residual replacement: x folded to FP64, then r = b - A x in FP64
@@ -706,12 +708,12 @@ __device__ void solve_one(const BArgs& a, cg::cluster_group& cl, BSh<S>& sh, int
       }
       if (status >= 0) break;
       const int zp = qp ^ 1;
-      run_mpk(Zp(zp), AZp(zp));                                         // line 10
-      if (!b2_beta<S, T>(cl, sh, par, Zp(qp), AZp(zp), a.nu, ld, rg)) {  // lines 12-13
+      run_mpk(Zp(zp), AZp(zp));                                         // basis of r
+      if (!b2_beta<S, T>(cl, sh, par, Zp(qp), AZp(zp), a.nu, ld, rg)) {  // conjugation
         status = SSTEP_ERR_BREAKDOWN;
         break;
       }
-      // line 15 then lines 5-6 of the next iteration
+      // direction update, then the step system of the next iteration
       if (!upd_gram<S, T, false>(cl, sh, par, Zp(zp), AZp(zp), Zp(qp), AZp(qp), v, a.nu, ld, rg)) {
         status = SSTEP_ERR_BREAKDOWN;
         break;

@@ -25,16 +25,16 @@ enum GramMode {
   GM_SUMS = 0,           // only write the reduced sums
   GM_ONESYNC_FIRST = 1,  // k = 0: W = Z^T AZ, b1 = Z^T r, alpha = FGS(W, b1)
   GM_ONESYNC = 2,        // beta = FGS(W_k, -Q^T AZ); W_{k+1} = ...; alpha = FGS(W_{k+1}, b1)
-  GM_LITERAL_W = 3,      // W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)          (lines 5-6)
-  GM_LITERAL_B2 = 4      // beta = FGS(W, -Q^T AZ)                              (lines 12-13)
+  GM_LITERAL_W = 3,      // W = Q^T AQ, b1 = Q^T r, alpha = FGS(W, b1)          (step system)
+  GM_LITERAL_B2 = 4      // beta = FGS(W, -Q^T AZ)                              (conjugation)
 };
 
-// Update kernel modes (Algorithm 1 lines 7-8 and 15).
+// Update kernel modes (the block updates of Section 2).
 enum UpdMode {
   UM_FIRST = 0,  // Q = Z, AQ = AZ, then x += Q alpha, r -= AQ alpha
   UM_FUSED = 1,  // Q = Z + Q beta, AQ = AZ + AQ beta, then x += Q alpha, r -= AQ alpha
-  UM_XR = 2,     // x += Q alpha, r -= AQ alpha only                  (literal lines 7-8)
-  UM_QAQ = 3     // Q = Z + Q beta, AQ = AZ + AQ beta only            (literal line 15)
+  UM_XR = 2,     // x += Q alpha, r -= AQ alpha only                  (literal form)
+  UM_QAQ = 3     // Q = Z + Q beta, AQ = AZ + AQ beta only            (literal form)
 };
 
 // Device-resident control block of one solve.  Written only by the last CTA of a reduction
@@ -244,7 +244,7 @@ __device__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* t
   return true;
 }
 
-// Stop test of Algorithm 1 line 9 on ||r||^2 (also used by PCG), executed by one thread.
+// Stop test of Algorithm 1 on ||r||^2 (also used by PCG), executed by one thread.
 __device__ __forceinline__ void stop_test(Ctrl* c, double rr) {
   c->rr = rr;
   c->iters += 1;
@@ -403,7 +403,7 @@ struct GramTiles {
   Ctrl* ctrl;
   double* partials;
 };
-// Line 15 fused with line 5 of the next outer iteration (see k_upd_gram), s <= 8.
+// Direction-block update fused with W, b1 of the next outer iteration (see k_upd_gram), s <= 8.
 struct UpdGramArgs {
   int64_t n, ld;
   const double* Z;

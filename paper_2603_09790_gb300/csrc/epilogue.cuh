@@ -111,7 +111,7 @@ __device__ void finish(const EpiArgs& e, const double* tot) {
   } else if constexpr (EPI == EP_TRUERES) {
     c->sums[0] = tot[0];
   } else if constexpr (EPI == EP_RR) {
-    // the replaced residual is the true one: the stop test of line 9 applies to it too
+    // the replaced residual is the true one: Algorithm 1's stop test applies to it too
     c->rr = tot[0];
     if (!(tot[0] == tot[0]) || tot[0] > 1.79e308) {
       c->status = SSTEP_ERR_NONFINITE;

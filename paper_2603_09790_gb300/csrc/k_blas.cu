@@ -1,14 +1,15 @@
 // k_blas.cu -- tall-skinny block kernels of PCG-S and the PCG comparator.
 //
 //  * k_gram: one pass over n rows forms every requested dot product L_a^T R_b (Algorithm 1
-//    lines 5 and 12-13; in the one-reduction form, all blocks of [Q_k Z_{k+1}]^T
+//    step system W, b1 and the conjugation right-hand sides -Q^T AZ of Section 2; in the
+//    one-reduction form, all blocks of [Q_k Z_{k+1}]^T
 //    [AQ_k AZ_{k+1} r]).  Rows are staged in shared memory in tiles of 256; each thread owns a
 //    few (entry, row-phase) slots, so every FP64 multiply-add of the product is issued once.
 //    Per-CTA partials are summed in a fixed order by the last CTA to finish (no grid barrier,
 //    bit-reproducible), and that same CTA then solves the reduced systems: FGS sweeps of
 //    Section 3.1 (Eq. fgs-iteration) for beta and alpha, and the assembly of W_{k+1}.
-//  * k_update: Algorithm 1 lines 7-8 and 15 in one pass: Q <- Z + Q beta, AQ <- AZ + AQ beta,
-//    x <- x + Q alpha, r <- r - AQ alpha, ||r||^2 and the stop test of line 9.
+//  * k_update: the block updates of Section 2 in one pass: Q <- Z + Q beta, AQ <- AZ + AQ beta
+//    (Eq. blockdirupdate), x <- x + Q alpha, r <- r - AQ alpha, ||r||^2 and Algorithm 1's stop test.
 //  * PCG vector kernels (x/r/z update with r^T z and ||r||^2; direction update).
 #include <algorithm>
 
@@ -295,7 +296,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
   const int tid = threadIdx.x;
   bool ok = true;
   if (mode == GM_ONESYNC_FIRST || mode == GM_LITERAL_W) {
-    // W = V^T AV (V = Z_0 or Q_k), b1 = V^T r;  alpha = FGS(W, b1)       (lines 5-6)
+    // W = V^T AV (V = Z_0 or Q_k), b1 = V^T r;  alpha = FGS(W, b1)       (step system)
     for (int e = tid; e < s * s; e += blockDim.x) {
       const int i = e % s, j = e / s;
       W[e] = sums[L.sym(i, j)];
@@ -309,7 +310,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
       if (tid == 0) record_alpha(c, s, W, b1, X);
     }
   } else if (mode == GM_LITERAL_B2) {
-    // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (lines 12-13)
+    // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (conjugation)
     for (int e = tid; e < s * s; e += blockDim.x) {
       W[e] = c->W[e];
       Bm[e] = -sums[e];  // entry e = i + j*s is q_i^T az_j
@@ -331,7 +332,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
       Bm[e] = -G2[e];
     }
     __syncthreads();
-    // beta_k = FGS(W_k, -Q_k^T AZ_{k+1})                                   (lines 12-13)
+    // beta_k = FGS(W_k, -Q_k^T AZ_{k+1})                                   (conjugation)
     ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
     if (ok) {
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
@@ -364,7 +365,7 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
       __syncthreads();
       for (int e = tid; e < s * s; e += blockDim.x) W[e] = Bm[e];
       __syncthreads();
-      // alpha_{k+1} = FGS(W_{k+1}, b1)                                     (lines 5-6)
+      // alpha_{k+1} = FGS(W_{k+1}, b1)                                     (step system)
       ok = reduced_solve(s, W, b1, 1, nu, solver, T, scr);
       if (ok) {
         for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = T[i];
@@ -549,13 +550,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiled(GramTiles g) {
   gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
 }
 
-// ---------------------------------------------------------------- update fused with line 5
+// ---------------------------------------------------------------- update fused with W, b1
 
-// Algorithm 1 line 15 of outer iteration k fused with line 5 of iteration k+1, in one pass:
-// Q <- Z + Q beta, AQ <- AZ + AQ beta (FIRST: Q <- Z, AQ <- AZ, Algorithm 1 line 3), then
+// The direction-block update of outer iteration k (Eq. blockdirupdate) fused with the step
+// system of iteration k+1, in one pass: Q <- Z + Q beta, AQ <- AZ + AQ beta (FIRST: the first
+// block, Q <- Z, AQ <- AZ), then
 // W = Q^T AQ and b1 = Q^T r accumulated in registers from the new columns while they are in
 // registers.  The last CTA sums the per-CTA partials in a fixed order and solves
-// alpha = FGS(W, b1) (line 6).  Entries: W_ij at i + j s, b1_i at s^2 + i.
+// alpha = FGS(W, b1).  Entries: W_ij at i + j s, b1_i at s^2 + i.
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   if (a.ctrl->done) return;
@@ -679,7 +681,7 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
   return true;
 }
 
-// b2 = -Q^T AZ (line 12) from FP32 blocks, then beta = FGS(W, b2) (line 13).
+// Conjugation system of Section 2: b2 = -Q^T AZ from FP32 blocks, then beta = FGS(W, b2).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   if (a.ctrl->done) return;
@@ -733,8 +735,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   gram_tail(GM_LITERAL_B2, a.ctrl, buf, buf + K);
 }
 
-// Line 15 in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r accumulated in
-// double-float (r = rhi + rlo), then alpha = FGS(W, b1) in the last CTA (lines 5-6).
+// Direction-block update in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r
+// accumulated in double-float (r = rhi + rlo), then alpha = FGS(W, b1) in the last CTA.
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
   if (a.ctrl->done) return;
@@ -862,7 +864,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
   gram_tail(GM_LITERAL_W, a.ctrl, buf, buf + K);
 }
 
-// Lines 7-9: x += Q alpha, r -= AQ alpha with x, r kept as FP32 (hi, lo) increments between
+// x += Q alpha, r -= AQ alpha and the stop test, with x, r kept as FP32 (hi, lo) increments between
 // residual replacements, ||r||^2 in double-float, stop test in the last CTA.
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
@@ -946,7 +948,7 @@ __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   }
 }
 
-// Line 15 alone in FP32 (FIRST: Q = Z, AQ = AZ) for step sizes whose fused form would not fit
+// Direction-block update alone in FP32 (FIRST: Q = Z, AQ = AZ) for step sizes whose fused form would not fit
 // in registers; W and b1 then come from k_gram_df.
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
@@ -1713,7 +1715,7 @@ cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
 }
 
 cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st) {
-  if (s > 4) {  // line 15 and lines 5-6 as two passes (the fused form would spill)
+  if (s > 4) {  // Q, AQ update and W, b1 as two passes (the fused form would spill)
     const int grid = update_ctas(a.n);
     switch (s) {
 #define CASE(S)                                                                   \

@@ -162,7 +162,7 @@ def test_fgs_breakdown_reported():
 
 @pytest.mark.parametrize("s,first", [(1, False), (4, True), (4, False), (7, False), (16, False)])
 def test_block_update(s, first):
-    """Algorithm 1 lines 7-8 and 15 against their definitions."""
+    """The block updates of Section 2 (x, r and Eq. blockdirupdate) against their definitions."""
     n = 50021
     rng = np.random.default_rng(s)
     Z, AZ, Q, AQ = (rng.standard_normal((s, n)) for _ in range(4))
