@@ -131,8 +131,8 @@ def kernel_work(s, n, points=7, sym_blocks=False):
     """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes).
 
     A multiply-add counts 2 flops.  Literal form (default): b2 = -Q^T AZ (s^2 products),
-    Q/AQ update fused with W = Q^T AQ and b1 = Q^T r (2 s^2 + s^2 + s multiply-adds), x/r update
-    (2 s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products, or 2 s^2 + 3 s with
+    Q/AQ update fused with W = Q^T AQ (symmetric: its upper triangle, s (s + 1) / 2 products)
+    and b1 = Q^T r (2 s^2 + s (s + 1) / 2 + s multiply-adds), x/r update (2 s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products, or 2 s^2 + 3 s with
     the symmetric shortcut) and one update pass (2 s^2 + 2 s + 1)."""
     V = 8.0 * n
     sp_flops = {5: 5, 7: 7, 27: 27}[points]  # Poisson: (points-1) adds + 1 multiply per row
@@ -142,7 +142,7 @@ def kernel_work(s, n, points=7, sym_blocks=False):
     return {
         "mpk_step": {"bytes": mpk_bytes / s, "flops": (sp_flops + rec) * n},
         "gram_b2": {"bytes": 2 * s * V, "flops": 2.0 * s * s * n},
-        "update_w": {"bytes": (6 * s + 1) * V, "flops": 2.0 * (3 * s * s + s) * n},
+        "update_w": {"bytes": (6 * s + 1) * V, "flops": 2.0 * (2 * s * s + s * (s + 1) // 2 + s) * n},
         "update_xr": {"bytes": (2 * s + 4) * V, "flops": (2.0 * (2 * s + 1) + 2) * n},
         "gram": {"bytes": (4 * s + 1) * V, "flops": 2.0 * ne * n},
         "update": {"bytes": (6 * s + 4) * V, "flops": 2.0 * (2 * s * s + 2 * s + 1) * n},

@@ -275,9 +275,11 @@ SSTEP_API sstep_status sstep_block_gram(int64_t n, int nl, const double* const* 
  * sstep_block_gram; the caller still passes L, R and out.  Scratch comes from one fixed area of
  * about 1.06 MB compiled into the library, kept on every GPU that loads it until exit.  Limits:
  * ne <= 256 (else SSTEP_ERR_INVALID with a message), devices with at most 256 SMs (else
- * SSTEP_ERR_UNSUPPORTED).  The first call on a device looks up the area's address.  All calls
- * share the area: calls that overlap on the GPU (different streams, or threads without
- * ordering) race and return wrong sums, so order them. */
+ * SSTEP_ERR_UNSUPPORTED).  The first call on a device looks up the area's address and keeps
+ * it for that device ordinal: make it before any stream capture, and do not call this entry
+ * point on a device again after cudaDeviceReset on it (the kept address belongs to the
+ * destroyed context).  All calls share the area: calls that overlap on the GPU (different
+ * streams, or threads without ordering) race and return wrong sums, so order them. */
 SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, const double* const* L, int nr,
                                                 const double* const* R, int ne, const int* pairs,
                                                 double* out, void* stream);

@@ -62,7 +62,7 @@ struct sstep_ctx {
   cudaStream_t st = nullptr;   // stream all work is ordered on (captures need a non-legacy one)
   bool own_stream = false;
   int64_t nlaunch = 0;         // kernel launches issued (graph replays count their nodes)
-  int64_t graph_nodes[4] = {0, 0, 0, 0};
+  int64_t graph_nodes[5] = {0, 0, 0, 0, 0};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int64_t n = 0, ld = 0, nnz = 0;
   int s = 4;
@@ -93,9 +93,11 @@ struct sstep_ctx {
   float *Zf = nullptr, *AZf = nullptr, *Qf = nullptr, *AQf = nullptr;
   float *rhi = nullptr, *rlo = nullptr, *xhi = nullptr, *xlo = nullptr;
   float *valsf = nullptr, *dinvf = nullptr, *kappaf = nullptr;
+  float *pf = nullptr, *Apf = nullptr;  // FP32 PCG: search direction and A p
   // graphs of one outer iteration, per algorithm (index 3: the mixed literal form, rr_period
-  // outer iterations followed by a residual replacement)
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  // outer iterations followed by a residual replacement; index 4: FP32 PCG, rr_period
+  // iterations followed by a residual replacement)
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t graph_nodes4 = 0;
   // host polling of the stop flag
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
@@ -287,7 +289,13 @@ sstep_status run_upd_w(sstep_ctx* h, bool first) {
 
 // ---------------------------------------------------------------- FP32-basis path
 
-constexpr int kAlgoMixed = 3;  // graph index of the mixed literal form
+constexpr int kAlgoMixed = 3;    // graph index of the mixed literal form
+constexpr int kAlgoPcgF32 = 4;   // graph index of FP32 PCG with FP64 residual replacement
+
+int solve_algo(const sstep_ctx* h) {
+  if (!h->mixed) return h->o.algo;
+  return h->o.algo == SSTEP_ALGO_PCG ? kAlgoPcgF32 : kAlgoMixed;
+}
 
 MixedArgs mixed_args(sstep_ctx* h) {
   MixedArgs a{};
@@ -380,11 +388,64 @@ sstep_status mixed_first(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
+PcgF32Args pcgf_args(sstep_ctx* h) {
+  PcgF32Args a{};
+  a.n = h->n;
+  a.p = h->pf;
+  a.Ap = h->Apf;
+  a.xhi = h->xhi;
+  a.xlo = h->xlo;
+  a.rhi = h->rhi;
+  a.rlo = h->rlo;
+  a.dinv = h->dinvf;
+  a.dinv_u = (float)h->M.dinv_u;
+  a.ctrl = h->ctrl;
+  a.partials = h->partials;
+  a.hist = h->hist;
+  return a;
+}
+
+// FP32 PCG: A p in FP32 with p^T A p and alpha in the operator kernel's last CTA.
+sstep_status pcgf_product(sstep_ctx* h) {
+  MpkF32Args e{};
+  e.u = h->pf;
+  e.y = h->Apf;
+  e.valsf = h->valsf;
+  e.ctrl = h->ctrl;
+  e.pap = 1;
+  e.partials = h->partials;
+  if (h->op.kind == SSTEP_MATRIX_STENCIL) {
+    for (int k = 0; k < h->op.st.points; ++k) e.w[k] = (float)h->op.st.w[k];
+    e.wc = (float)h->op.st.wc;
+  }
+  CK(launch_mpk_f32(h->op, e, h->st));
+  ++h->nlaunch;
+  return SSTEP_OK;
+}
+
+// One FP32 PCG iteration; `replace`: FP64 residual replacement before the direction update.
+sstep_status pcgf_iteration(sstep_ctx* h, bool replace) {
+  const PcgF32Args a = pcgf_args(h);
+  CKS(pcgf_product(h));
+  CK(launch_pcgf_update(a, h->st));
+  ++h->nlaunch;
+  if (replace) {
+    CKS(run_rr(h));
+    CK(launch_pcgf_rz(a, 0, h->st));
+    ++h->nlaunch;
+  }
+  CK(launch_pcgf_pdir(a, 0, h->st));
+  ++h->nlaunch;
+  return SSTEP_OK;
+}
+
 // One outer iteration k >= 1 of each algorithm (what the graph captures).
 sstep_status outer_iteration(sstep_ctx* h, int algo) {
   if (algo == kAlgoMixed) {
     for (int k = 0; k < h->rr_period; ++k) CKS(mixed_outer(h));
     CKS(run_rr(h));
+  } else if (algo == kAlgoPcgF32) {
+    for (int k = 0; k < h->rr_period; ++k) CKS(pcgf_iteration(h, k == h->rr_period - 1));
   } else if (algo == SSTEP_ALGO_ONESYNC) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_gram(h, GM_ONESYNC));
@@ -556,8 +617,9 @@ sstep_status validate_opts(const sstep_opts* o) {
   if (o->precision != SSTEP_PRECISION_FP64 && o->precision != SSTEP_PRECISION_FP32_RR)
     return fail(SSTEP_ERR_INVALID, "unknown precision");
   if (o->precision == SSTEP_PRECISION_FP32_RR) {
-    if (o->algo != SSTEP_ALGO_LITERAL)
-      return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path implements the literal form only");
+    if (o->algo != SSTEP_ALGO_LITERAL && o->algo != SSTEP_ALGO_PCG)
+      return fail(SSTEP_ERR_UNSUPPORTED,
+                  "the FP32-basis path implements the literal form and classical PCG");
     if (o->s > 8) return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path supports s <= 8");
     if (o->gram_solver != SSTEP_GRAM_FGS)
       return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path uses FGS reduced solves");
@@ -574,8 +636,8 @@ void destroy(sstep_ctx* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
-  void* fbufs[] = {h->Zf,  h->AZf, h->Qf,    h->AQf,   h->rhi,   h->rlo,
-                   h->xhi, h->xlo, h->valsf, h->dinvf, h->kappaf};
+  void* fbufs[] = {h->Zf,  h->AZf, h->Qf,    h->AQf,   h->rhi,   h->rlo, h->xhi,
+                   h->xlo, h->valsf, h->dinvf, h->kappaf, h->pf,    h->Apf};
   for (void* p : fbufs)
     if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
@@ -826,17 +888,27 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
 
   // ---- FP32-basis path: FP32 blocks and increments, FP32 copies of the operator
   if (h->o.precision == SSTEP_PRECISION_FP32_RR) {
+    const bool pcg = h->o.algo == SSTEP_ALGO_PCG;
     h->mixed = true;
-    h->rr_period = h->o.rr_period > 0 ? h->o.rr_period : h->s;
+    // PCG: one replacement per 16 iterations by default, the spacing in CG steps of the
+    // s-step form's default (every s outer iterations of s steps each, s = 4)
+    h->rr_period = h->o.rr_period > 0 ? h->o.rr_period : (pcg ? 16 : h->s);
     h->ldf = round_up(h->n, 64);
     const int64_t lf = h->ldf;
     auto fal = [&](float** p, int64_t count) -> cudaError_t {
       return cudaMalloc((void**)p, sizeof(float) * (size_t)std::max<int64_t>(count, 1));
     };
-    CK(fal(&h->Zf, lf * s));
-    CK(fal(&h->AZf, lf * s));
-    CK(fal(&h->Qf, lf * s));
-    CK(fal(&h->AQf, lf * s));
+    if (pcg) {
+      if (A->kind == SSTEP_MATRIX_Q1)
+        return fail(SSTEP_ERR_UNSUPPORTED, "FP32 PCG takes the Q1 operator as CSR");
+      CK(fal(&h->pf, lf));
+      CK(fal(&h->Apf, lf));
+    } else {
+      CK(fal(&h->Zf, lf * s));
+      CK(fal(&h->AZf, lf * s));
+      CK(fal(&h->Qf, lf * s));
+      CK(fal(&h->AQf, lf * s));
+    }
     CK(fal(&h->rhi, lf));
     CK(fal(&h->rlo, lf));
     CK(fal(&h->xhi, lf));
@@ -883,7 +955,7 @@ int auto_check_every(const sstep_ctx* h) {
 sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* info) {
   const double t0 = now_ms();
   const int64_t n = h->n;
-  const int algo = h->mixed ? kAlgoMixed : h->o.algo;
+  const int algo = solve_algo(h);
   // Order against the caller's stream: inputs produced there are complete before we read.
   CK(cudaEventRecord(h->ev_in, h->user_stream));
   CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
@@ -910,6 +982,11 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   const int maxit = h->o.max_outer;
   if (algo == kAlgoMixed) {
     if (maxit > 0) CKS(mixed_first(h));
+  } else if (algo == kAlgoPcgF32) {
+    const PcgF32Args a = pcgf_args(h);
+    CK(launch_pcgf_rz(a, 1, h->st));
+    CK(launch_pcgf_pdir(a, 1, h->st));
+    h->nlaunch += 2;
   } else if (algo == SSTEP_ALGO_ONESYNC) {
     if (maxit > 0) {
       CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
@@ -930,8 +1007,10 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   CKS(ensure_graph(h, algo));
   // Replay the captured outer iteration; poll the stop flag one batch behind.
   const int B = auto_check_every(h);
-  int launched = (algo == SSTEP_ALGO_PCG) ? 0 : 1;  // PCG-S ran its first outer iteration above
-  const int per_graph = (algo == kAlgoMixed) ? h->rr_period : 1;  // outer iterations per replay
+  // PCG-S ran its first outer iteration above
+  int launched = (algo == SSTEP_ALGO_PCG || algo == kAlgoPcgF32) ? 0 : 1;
+  // outer iterations per replay
+  const int per_graph = (algo == kAlgoMixed || algo == kAlgoPcgF32) ? h->rr_period : 1;
   bool finished = false;
   Ctrl* hc = h->hctrl;
   int* flags = h->poll_flags;
@@ -992,7 +1071,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   if (info) {
     info->status = result;
     info->outer_iters = hc->iters;
-    info->inner_equiv = algo == SSTEP_ALGO_PCG ? hc->iters : hc->iters * h->s;
+    info->inner_equiv = h->o.algo == SSTEP_ALGO_PCG ? hc->iters : hc->iters * h->s;
     const double nb = std::sqrt(hc->nb2);
     info->relres = nb > 0.0 ? std::sqrt(hc->rr) / nb : 0.0;
     info->relres_true = nb > 0.0 ? std::sqrt(true_rr) / nb : 0.0;
@@ -1119,7 +1198,7 @@ sstep_status sstep_get_diagnostics(sstep_handle h, double* eta_a, double* eta_b,
   g_err.clear();
   if (!h || h->batch) return fail(SSTEP_ERR_INVALID, "not a single-system handle");
   CK(cudaStreamSynchronize(h->st));
-  const int iters = h->o.algo == SSTEP_ALGO_PCG && !h->mixed ? 0 : h->hctrl->iters;
+  const int iters = h->o.algo == SSTEP_ALGO_PCG ? 0 : h->hctrl->iters;
   const int na = std::max(0, std::min(maxlen, iters));
   if (na > 0 && eta_a) CK(cudaMemcpy(eta_a, h->eta_a, sizeof(double) * na, cudaMemcpyDeviceToHost));
   if (na > 1 && eta_b) CK(cudaMemcpy(eta_b, h->eta_b, sizeof(double) * (na - 1), cudaMemcpyDeviceToHost));
@@ -1285,7 +1364,7 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   g_err.clear();
   if (!h || !b || !ms || iters < 1) return fail(SSTEP_ERR_INVALID, "bad profile arguments");
   if (h->batch) return fail(SSTEP_ERR_INVALID, "not available on a batched handle");
-  const int algo = h->mixed ? kAlgoMixed : h->o.algo;
+  const int algo = solve_algo(h);
   CK(cudaMemcpyAsync(h->b, b, sizeof(double) * h->n, cudaMemcpyDefault, h->st));
   CK(cudaMemsetAsync(h->x, 0, sizeof(double) * h->n, h->st));
   if (h->mixed) {
@@ -1307,6 +1386,10 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   }
   if (algo == kAlgoMixed) {
     CKS(mixed_first(h));
+  } else if (algo == kAlgoPcgF32) {
+    const PcgF32Args a = pcgf_args(h);
+    CK(launch_pcgf_rz(a, 1, h->st));
+    CK(launch_pcgf_pdir(a, 1, h->st));
   } else if (algo == SSTEP_ALGO_ONESYNC) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_gram(h, GM_ONESYNC_FIRST));
@@ -1337,6 +1420,14 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
       okc(launch_upd_gram_f32(a, h->s, false, h->st));
       cudaEventRecord(ev[3], h->st);
       okc(launch_update_xr_f32(a, h->s, h->st));
+    } else if (algo == kAlgoPcgF32) {
+      const PcgF32Args a = pcgf_args(h);
+      ok(pcgf_product(h));
+      cudaEventRecord(ev[1], h->st);
+      okc(launch_pcgf_update(a, h->st));
+      cudaEventRecord(ev[2], h->st);
+      okc(launch_pcgf_pdir(a, 0, h->st));
+      cudaEventRecord(ev[3], h->st);
     } else if (algo == SSTEP_ALGO_ONESYNC) {
       ok(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
       cudaEventRecord(ev[1], h->st);

@@ -46,6 +46,8 @@ struct Ctrl {
   double rr;         // ||r||^2 of the current residual
   double rr0;        // ||r^(0)||^2
   double rz;         // PCG: r^T z
+  double rz_prev;    // FP32 PCG: r^T z before the last update (a residual replacement
+                     // recomputes r^T z and takes beta against this value)
   double pcg_alpha, pcg_beta;
   double lam, inv_scale, power_tol;  // power method: estimate, 1/previous estimate, stop tolerance
   int power_done, power_iters, power_max;
@@ -244,6 +246,48 @@ __device__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* t
   return true;
 }
 
+// Per-thread double-float (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the
+// last CTA (no CTA waits for another).  Grids may be 1D, 2D or 3D.  buf: shared memory of at
+// least (blockDim.x / 32) * K doubles.  Returns true in the last CTA, with the K sums in
+// buf[0..K) (valid in all of its threads).
+template <int K>
+__device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
+                             double* partials, unsigned int* ticket) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
+  // warp stage in double-float on the FP32 pipe; one FP64 conversion per warp and value
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float h = hi[k], l = lo[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+      df_add(h, l, oh, ol);
+    }
+    if (lane == 0) buf[wid * K + k] = (double)h + (double)l;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
+    partials[(size_t)bid * K + k] = v;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  sum_partials(partials, nblk, K, 1, buf);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
 // Stop test of Algorithm 1 on ||r||^2 (also used by PCG), executed by one thread.
 __device__ __forceinline__ void stop_test(Ctrl* c, double rr) {
   c->rr = rr;
@@ -322,6 +366,10 @@ struct MpkF32Args {
   const float* valsf;  // CSR values in FP32
   int first;
   Ctrl* ctrl;
+  // FP32 PCG product step (first = 0, znext = null): with pap set, the kernel also forms
+  // p^T (A p) (u = p, y = A p) in double-float, and its last CTA sets alpha = r^T z / p^T A p
+  int pap;
+  double* partials;
 };
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st);
 
@@ -465,6 +513,31 @@ struct PcgArgs {
 cudaError_t launch_pcg_update(const PcgArgs& a, cudaStream_t st);   // x, r, z, rz, rr, beta
 cudaError_t launch_pcg_pdir(const PcgArgs& a, cudaStream_t st);     // p = z + beta p
 cudaError_t launch_pcg_init(const PcgArgs& a, cudaStream_t st);     // z = M^-1 r, p = z, rz
+
+// Classical PCG with the FP32-basis path's precision recipe: p and A p in FP32, x and r as
+// FP32 (hi, lo) increments over the FP64 x and a residual replaced in FP64 every rr_period
+// iterations, reductions in double-float.  z = M^{-1} r_hi is formed where it is used.
+struct PcgF32Args {
+  int64_t n;
+  float* p;
+  const float* Ap;
+  float* xhi;
+  float* xlo;
+  float* rhi;
+  float* rlo;
+  const float* dinv;  // non-uniform M^{-1} in FP32, or null
+  float dinv_u;       // uniform M^{-1}
+  Ctrl* ctrl;
+  double* partials;
+  double* hist;
+};
+// x += alpha p, r -= alpha Ap (double-float), r^T z and ||r||^2, stop test, beta
+cudaError_t launch_pcgf_update(const PcgF32Args& a, cudaStream_t st);
+// r^T z of the current r (after the initial residual or a replacement): init sets beta = 0,
+// else beta = (r^T z) / rz_prev
+cudaError_t launch_pcgf_rz(const PcgF32Args& a, int init, cudaStream_t st);
+// p = z + beta p (init: p = z)
+cudaError_t launch_pcgf_pdir(const PcgF32Args& a, int init, cudaStream_t st);
 
 cudaError_t launch_fill_splitmix(double* v, int64_t n, uint64_t seed, cudaStream_t st);
 cudaError_t launch_jacobi_csr(const CsrOp& A, double* dinv, int* bad, cudaStream_t st);

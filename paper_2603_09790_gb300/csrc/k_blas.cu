@@ -21,15 +21,23 @@ namespace {
 
 constexpr int kGramRows = 256;  // rows per shared-memory tile
 
+// SM count of the current device, cached per device ordinal.
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
+  constexpr int kDevs = 64;
+  static int sms[kDevs] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kDevs) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
   }
-  return sms;
+  if (!sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 1;
+  }
+  return sms[dev];
 }
 
 // ---------------------------------------------------------------- reduced-system tail
@@ -556,12 +564,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiled(GramTiles g) {
 // system of iteration k+1, in one pass: Q <- Z + Q beta, AQ <- AZ + AQ beta (FIRST: the first
 // block, Q <- Z, AQ <- AZ), then
 // W = Q^T AQ and b1 = Q^T r accumulated in registers from the new columns while they are in
-// registers.  The last CTA sums the per-CTA partials in a fixed order and solves
-// alpha = FGS(W, b1).  Entries: W_ij at i + j s, b1_i at s^2 + i.
+// registers.  W is symmetric by definition (A is), so only its upper triangle is accumulated
+// (entry (i, j), i <= j, at tri(i, j) = j (j + 1) / 2 + i; b1_i at S (S + 1) / 2 + i).  The last
+// CTA sums the per-CTA partials in a fixed order, mirrors the triangle into the s x s layout
+// the reduced-solve tail reads (W_ij at i + j s, b1_i at s^2 + i) and solves alpha = FGS(W, b1).
+__host__ __device__ constexpr int tri(int i, int j) { return j * (j + 1) / 2 + i; }
+
+// Mirrors the packed upper triangle of W and the S entries of b1 that follow it into the full
+// layout; executed by the whole CTA, ends with __syncthreads().
+template <int S>
+__device__ __forceinline__ void expand_sym_w(const double* packed, double* full) {
+  constexpr int NW = S * (S + 1) / 2;
+  for (int e = threadIdx.x; e < S * S + S; e += blockDim.x) {
+    if (e < S * S) {
+      const int i = e % S, j = e / S;
+      full[e] = packed[i <= j ? tri(i, j) : tri(j, i)];
+    } else {
+      full[e] = packed[NW + e - S * S];
+    }
+  }
+  __syncthreads();
+}
+
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   if (a.ctrl->done) return;
-  constexpr int K = S * S + S;
+  constexpr int NW = S * (S + 1) / 2;
+  constexpr int K = NW + S;
   __shared__ double sb[S * S];
   __shared__ double buf[kTiledSmem];
   if (!FIRST)
@@ -606,11 +635,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
     }
     const double rp = __ldg(a.r + p);
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
+    for (int j = 0; j < S; ++j)
 #pragma unroll
-      for (int j = 0; j < S; ++j) acc[i + j * S] = fma(qn[i], an[j], acc[i + j * S]);
-      acc[S * S + i] = fma(qn[i], rp, acc[S * S + i]);
-    }
+      for (int i = 0; i <= j; ++i) acc[tri(i, j)] = fma(qn[i], an[j], acc[tri(i, j)]);
+#pragma unroll
+    for (int i = 0; i < S; ++i) acc[NW + i] = fma(qn[i], rp, acc[NW + i]);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -634,52 +663,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double* sums = buf;
-  sum_partials(a.partials, gridDim.x, K, 1, sums);
+  sum_partials(a.partials, gridDim.x, K, 1, buf);
   if (threadIdx.x == 0) a.ctrl->ticket[TK_GRAM] = 0u;
-  for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = sums[e];
-  gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + K);
+  double* sums = buf + K;  // s^2 + s entries in the full layout
+  expand_sym_w<S>(buf, sums);
+  for (int e = threadIdx.x; e < S * S + S; e += blockDim.x) a.ctrl->sums[e] = sums[e];
+  gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + S * S + S);
 }
 
 // ---------------------------------------------------------------- mixed path (FP32 basis)
-
-// Per-thread (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the last CTA.
-// Returns true in the last CTA, with the K sums in buf[0..K).
-template <int K>
-__device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
-                             double* partials, unsigned int* ticket) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // warp stage in double-float on the FP32 pipe; one FP64 conversion per warp and value
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float h = hi[k], l = lo[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-      const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-      df_add(h, l, oh, ol);
-    }
-    if (lane == 0) buf[wid * K + k] = (double)h + (double)l;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
-    partials[(size_t)blockIdx.x * K + k] = v;
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  sum_partials(partials, gridDim.x, K, 1, buf);
-  if (threadIdx.x == 0) *ticket = 0u;
-  return true;
-}
 
 // Conjugation system of Section 2: b2 = -Q^T AZ from FP32 blocks, then beta = FGS(W, b2).
 template <int S>
@@ -740,7 +732,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
   if (a.ctrl->done) return;
-  constexpr int K = S * S + S;
+  constexpr int NW = S * (S + 1) / 2;  // upper triangle of W (symmetric), then b1
+  constexpr int K = NW + S;
   __shared__ float sb[S * S];
   __shared__ double buf[kTiledSmem];
   if (!FIRST)
@@ -754,11 +747,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   auto accum = [&](const float (&qn)[S], const float (&an)[S], float rh, float rl) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
+    for (int j = 0; j < S; ++j)
 #pragma unroll
-      for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
-      df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
-      lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
+      for (int i = 0; i <= j; ++i) df_acc_prod(hi[tri(i, j)], lo[tri(i, j)], qn[i], an[j]);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      df_acc_prod(hi[NW + i], lo[NW + i], qn[i], rh);
+      lo[NW + i] = fmaf(qn[i], rl, lo[NW + i]);
     }
   };
   // four consecutive points per thread and trip: 16-byte loads and stores
@@ -850,18 +845,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
       a.Q[j * ld + p] = qn[j];
       a.AQ[j * ld + p] = an[j];
     }
-    const float rh = __ldg(a.rhi + p), rl = __ldg(a.rlo + p);
-#pragma unroll
-    for (int i = 0; i < S; ++i) {
-#pragma unroll
-      for (int j = 0; j < S; ++j) df_acc_prod(hi[i + j * S], lo[i + j * S], qn[i], an[j]);
-      df_acc_prod(hi[S * S + i], lo[S * S + i], qn[i], rh);
-      lo[S * S + i] = fmaf(qn[i], rl, lo[S * S + i]);
-    }
+    accum(qn, an, __ldg(a.rhi + p), __ldg(a.rlo + p));
   }
   if (!df_grid_sums<K>(hi, lo, buf, a.partials, &a.ctrl->ticket[TK_GRAM])) return;
-  for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = buf[e];
-  gram_tail(GM_LITERAL_W, a.ctrl, buf, buf + K);
+  double* sums = buf + K;  // s^2 + s entries in the full layout
+  expand_sym_w<S>(buf, sums);
+  for (int e = threadIdx.x; e < S * S + S; e += blockDim.x) a.ctrl->sums[e] = sums[e];
+  gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + S * S + S);
 }
 
 // x += Q alpha, r -= AQ alpha and the stop test, with x, r kept as FP32 (hi, lo) increments between
@@ -1801,11 +1791,15 @@ cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* 
   return cudaGetLastError();
 }
 
+// Raises k_gram's dynamic shared-memory limit on the current device (a per-device function
+// attribute), once per device ordinal.
 cudaError_t gram_init() {
-  static int done = 0;
-  if (done) return cudaSuccess;
+  constexpr int kDevs = 64;
+  static int done_dev[kDevs] = {};
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
+  int* done = (dev >= 0 && dev < kDevs) ? &done_dev[dev] : nullptr;
+  if (done && *done) return cudaSuccess;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (optin <= 0) optin = 48 * 1024;
   cudaError_t e = cudaSuccess;
@@ -1820,7 +1814,7 @@ cudaError_t gram_init() {
   }
   SET(1) SET(2) SET(3) SET(4) SET(5) SET(6) SET(7) SET(8)
 #undef SET
-  if (e == cudaSuccess) done = 1;
+  if (e == cudaSuccess && done) *done = 1;
   return e;
 }
 

@@ -270,6 +270,24 @@ __global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
 
 // ---------------------------------------------------------------- FP32 MPK step (mixed path)
 
+// FP32 PCG product step: the last CTA turns the grid's double-float sum p^T (A p) into
+// alpha = r^T z / p^T A p (breakdown when p^T A p is not positive and finite).
+__device__ __forceinline__ void pap_finish(const MpkF32Args& e, const float (&hi)[1],
+                                           const float (&lo)[1]) {
+  __shared__ double buf[32];
+  if (!df_grid_sums<1>(hi, lo, buf, e.partials, &e.ctrl->ticket[TK_PCG1])) return;
+  if (threadIdx.x == 0) {
+    Ctrl* c = e.ctrl;
+    const double pap = buf[0];
+    if (!(pap > 0.0) || pap > 1.79e308) {
+      c->status = SSTEP_ERR_BREAKDOWN;
+      c->done = 1;
+    } else {
+      c->pcg_alpha = c->rz / pap;
+    }
+  }
+}
+
 template <int PTS, bool POISSON>
 __device__ __forceinline__ float stencil7_point_f(const MpkF32Args& e, const float (*p)[TX + 2],
                                                   int tx, int ty, float ub, float uc, float ua) {
@@ -296,9 +314,10 @@ __device__ __forceinline__ float stencil7_point_f(const MpkF32Args& e, const flo
 
 // The 2.5D body of k_stencil7 with FP32 values: half the bytes per point, and the FP32 pipe
 // (64x the FP64 one on this part) does the arithmetic, so the step is bound by HBM.
-template <int PTS, bool POISSON, bool FIRST, bool SCALE>
+template <int PTS, bool POISSON, bool FIRST, bool SCALE, bool PAP = false>
 __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args e, int zc) {
   if (e.ctrl && e.ctrl->done) return;
+  float ph[1] = {0.0f}, pl[1] = {0.0f};  // PAP: p^T (A p)
   __shared__ float t[2][2][TY + 2][TX + 2];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
@@ -348,6 +367,7 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args 
         c0 *= e.dinv_u;
       }
       mpk_f32_epilogue(e, (int64_t)z * pxy + col, a0, c0, FIRST);
+      if constexpr (PAP) df_acc_prod(ph[0], pl[0], c0, a0);
       if (z + 1 < z1) {
         float a1 = stencil7_point_f<PTS, POISSON>(e, P1, tx, ty, uc, ua, ua2), c1 = ua;
         if constexpr (FIRST && !SCALE) {
@@ -355,6 +375,7 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args 
           c1 *= e.dinv_u;
         }
         mpk_f32_epilogue(e, (int64_t)(z + 1) * pxy + col, a1, c1, FIRST);
+        if constexpr (PAP) df_acc_prod(ph[0], pl[0], c1, a1);
       }
     }
     ub = ua;
@@ -367,6 +388,7 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args 
     hy1 = nhy1;
     set ^= 1;
   }
+  if constexpr (PAP) pap_finish(e, ph, pl);
 }
 
 // FP32 MPK step for 7-point stencils with nx a multiple of 4 and a uniform M^{-1}: each thread
@@ -377,9 +399,10 @@ __global__ void __launch_bounds__(TX * TY) k_stencil7f(StencilOp op, MpkF32Args 
 constexpr int TX4 = 16, TY4 = 16;  // threads: 16 float4 columns x 16 rows
 constexpr int kRow4 = 4 * TX4 + 8;  // floats per staged row: 4 pad | 64 values | 4 pad
 
-template <bool POISSON, bool FIRST>
+template <bool POISSON, bool FIRST, bool PAP = false>
 __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Args e, int zc) {
   if (e.ctrl && e.ctrl->done) return;
+  float ph[1] = {0.0f}, pl[1] = {0.0f};  // PAP: p^T (A p)
   __shared__ __align__(16) float sm[2][TY4 + 2][kRow4];
   const int tx = threadIdx.x % TX4, ty = threadIdx.x / TX4;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
@@ -454,6 +477,10 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
         cv[l] = cc;
       }
       const int64_t i = (int64_t)z * pxy + col;
+      if constexpr (PAP) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) df_acc_prod(ph[0], pl[0], cv[l], av[l]);
+      }
       if constexpr (FIRST) *reinterpret_cast<float4*>(e.z1 + i) = make_float4(cv[0], cv[1], cv[2], cv[3]);
       *reinterpret_cast<float4*>(e.y + i) = make_float4(av[0], av[1], av[2], av[3]);
       if (e.znext) {
@@ -473,11 +500,13 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
     hxv = nhx;
     set ^= 1;
   }
+  if constexpr (PAP) pap_finish(e, ph, pl);
 }
 
-template <bool FIRST, bool SCALE>
+template <bool FIRST, bool SCALE, bool PAP = false>
 __global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
   if (e.ctrl && e.ctrl->done) return;
+  float ph[1] = {0.0f}, pl[1] = {0.0f};  // PAP: p^T (A p)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
@@ -495,7 +524,9 @@ __global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
       uc *= e.dinv_u;
     }
     mpk_f32_epilogue(e, i, a, uc, FIRST);
+    if constexpr (PAP) df_acc_prod(ph[0], pl[0], uc, a);
   }
+  if constexpr (PAP) pap_finish(e, ph, pl);
 }
 
 int num_sms() {
@@ -710,6 +741,38 @@ cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st) 
 }
 
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st) {
+  if (e.pap) {  // FP32 PCG product step: y = A p with p^T A p (no recurrence)
+    if (e.first || e.znext || !e.ctrl || !e.partials) return cudaErrorInvalidValue;
+    if (A.kind == SSTEP_MATRIX_STENCIL) {
+      const StencilOp& op = A.st;
+      if (op.points == 27) return cudaErrorNotSupported;
+      if (op.points == 7 && op.nx % 4 == 0) {
+        const int gx = (op.nx + 4 * TX4 - 1) / (4 * TX4), gy = (op.ny + TY4 - 1) / TY4;
+        int64_t gz = std::max<int64_t>(1, (int64_t)num_sms() * 4 / std::max(1, gx * gy));
+        gz = std::min<int64_t>(gz, std::max(1, op.nz / 8));
+        const int zc = (int)((op.nz + gz - 1) / gz);
+        const dim3 grid(gx, gy, (op.nz + zc - 1) / zc);
+        if (op.poisson) k_stencil7f4<true, false, true><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+        else k_stencil7f4<false, false, true><<<grid, TX4 * TY4, 0, st>>>(op, e, zc);
+        return cudaGetLastError();
+      }
+      StencilGrid g = stencil_grid(op);
+      const int threads = TX * TY;
+      if (op.points == 7) {
+        if (op.poisson) k_stencil7f<7, true, false, false, true><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+        else k_stencil7f<7, false, false, false, true><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+      } else {
+        if (op.poisson) k_stencil7f<5, true, false, false, true><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+        else k_stencil7f<5, false, false, false, true><<<g.grid, threads, 0, st>>>(op, e, g.zc);
+      }
+      return cudaGetLastError();
+    }
+    if (A.kind == SSTEP_MATRIX_CSR) {
+      k_csrf<false, false, true><<<csr_ctas(A.csr.n), kThreads, 0, st>>>(A.csr, e);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;  // Q1: the FP32 PCG comparator takes the CSR form
+  }
   if (A.kind == SSTEP_MATRIX_Q1) return launch_q1_mpk_f32(A.q1, e, st);
   const bool scale = e.first && e.dinv != nullptr;
   if (A.kind == SSTEP_MATRIX_STENCIL) {

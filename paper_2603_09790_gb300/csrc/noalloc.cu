@@ -10,10 +10,17 @@
 // (about 1.06 MB), present on every GPU that loads the library until the process exits.
 //
 // Limits: ne <= kNoAllocMaxEntries (256) products per call, and devices with at most
-// kNoAllocMaxCtas / 2 SMs (the Gram grid is two CTAs per SM).  All calls share the one array
-// and it keeps the previous call's contents, so each call first zeroes the ticket and flags
-// it relies on.  Calls that run concurrently on the GPU (on different streams, or from
-// different threads without ordering) race on the array and give wrong sums; order them.
+// kNoAllocMaxCtas / 2 SMs (the Gram grid is two CTAs per SM of the current device).  All calls
+// share the one array and it keeps the previous call's contents, so each call first zeroes the
+// ticket and flags it relies on.  Calls that run concurrently on the GPU (on different streams,
+// or from different threads without ordering) race on the array and give wrong sums; order
+// them.
+//
+// Set-up: the first call on a device, with that device current, looks up the array's device
+// address (cudaGetSymbolAddress) and keeps it for later calls on that device ordinal; make that
+// first call before any stream capture.  The address belongs to the device's primary context:
+// after cudaDeviceReset on a device the kept address is stale, so do not call this entry point
+// on that device again in the same process.
 #include <mutex>
 #include <string>
 
@@ -37,7 +44,8 @@ std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device.  In host code the array's name is only
-// a host-side stand-in, so the address is looked up once per device, with that device current.
+// a host-side stand-in, so the address is looked up once per device, with that device current,
+// and kept per device ordinal.
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_scratch_addr[dev]) {
@@ -66,6 +74,7 @@ extern "C" SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, co
   if (ne > kNoAllocMaxEntries)
     return fail(SSTEP_ERR_INVALID, "block_gram_noalloc: at most 256 products per call (ne = " +
                                        std::to_string(ne) + ")");
+  // the grid launch_gram uses on the current device must fit the partial-sum table
   if (gram_ctas() > kNoAllocMaxCtas)
     return fail(SSTEP_ERR_UNSUPPORTED, "block_gram_noalloc: the device has more SMs than the "
                                        "fixed scratch area serves (at most 256)");

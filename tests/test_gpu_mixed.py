@@ -36,6 +36,20 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def poisson_kappa(dims, points):
+    """kappa(A) of the Dirichlet Poisson matrix from its closed-form spectrum: with
+    theta = k pi / (N + 1), k = 1..N per axis, lambda = sum_d (2 - 2 cos theta_d) (5/7 points)
+    or 27 - prod_d (1 + 2 cos theta_d) (27 points); the extremes sit at k = 1 or k = N."""
+    ends = [np.cos(np.array([1, N]) * np.pi / (N + 1)) for N in dims]
+    if points in (5, 7):
+        lmin = sum(2 - 2 * c[0] for c in ends)
+        lmax = sum(2 - 2 * c[1] for c in ends)
+    else:
+        prods = [a * b * c for a in 1 + 2 * ends[0] for b in 1 + 2 * ends[1] for c in 1 + 2 * ends[2]]
+        lmin, lmax = 27 - max(prods), 27 - min(prods)
+    return lmax / lmin
+
+
 @pytest.mark.parametrize("form,dims,points,s,nu", [
     ("stencil", (40, 36, 28), 7, 4, 30), ("stencil", (40, 36, 28), 7, 4, 3),
     ("csr", (64, 64), 5, 4, 30), ("stencil", (64, 64), 5, 2, 3), ("csr", (30, 26, 22), 27, 8, 30)])
@@ -51,9 +65,7 @@ def test_mixed_reaches_fp64_true_residual(form, dims, points, s, nu):
     assert info.relres_true <= 2e-8
     ref = O.pcgs(csr, b, s=s, nu=nu, rtol=1e-8, algo="literal", lambda_max=bi["lambda_max"])
     assert ref.status == O.OK
-    lam = np.linalg.eigvalsh(csr.dense()) if csr.n <= 5000 else None
-    kappa = lam[-1] / lam[0] if lam is not None else 1e4
-    assert relerr(x, ref.x) <= 2e-8 * kappa + 1e-10
+    assert relerr(x, ref.x) <= 2e-8 * poisson_kappa((nx, ny, nz)[:len(dims)], points) + 1e-10
 
 
 def test_mixed_q1_lognormal_s8():
@@ -95,3 +107,52 @@ def test_mixed_rejects_unsupported():
         assert e.value.status == sstep.ERR_UNSUPPORTED
     with pytest.raises(sstep.SstepError):
         sstep.Solver(sstep.Stencil(10, 10, 10, 27), precision="fp32_rr", lambda_max=2.0)
+
+
+# ---------------------------------------------------------------- FP32 PCG comparator
+# Classical PCG in the same precision recipe: p and A p in FP32, x and r as double-float
+# increments between FP64 residual replacements, reductions in double-float.  Tolerances as
+# above: the FP64 true residual at rtol, the solution within rtol * kappa(A) of the oracle's,
+# the iteration count within a few percent of the FP64 oracle's (FP32 directions perturb
+# the Krylov recurrence at the 1e-7 level).
+
+
+@pytest.mark.parametrize("form,dims,points,rrp", [
+    ("stencil", (40, 36, 28), 7, 0), ("stencil", (37, 31, 23), 7, 5), ("stencil", (64, 64), 5, 0),
+    ("csr", (64, 64), 5, 1), ("csr", (30, 26, 22), 27, 0)])
+def test_pcg_fp32_reaches_fp64_true_residual(form, dims, points, rrp):
+    csr = O.CSR(*I.poisson_csr(dims, points))
+    nx, ny, nz = (tuple(dims) + (1,))[:3]
+    A = sstep.Stencil(nx, ny, nz, points) if form == "stencil" else \
+        sstep.CSR(dev(csr.rowptr), dev(csr.colind), dev(csr.vals))
+    xt, b = I.poisson_problem(dims, points)
+    x, info, _ = solve(A, b, algo="pcg", rtol=1e-8, precision="fp32_rr", rr_period=rrp,
+                       lambda_max=2.0)
+    assert info.status == sstep.OK
+    assert info.relres_true <= 2e-8
+    ref = O.pcg(csr, b, rtol=1e-8)
+    assert ref.status == O.OK
+    assert relerr(x, ref.x) <= 2e-8 * poisson_kappa(dims, points) + 1e-10
+    assert abs(info.outer_iters - ref.iters) <= max(3, 0.05 * ref.iters), (info.outer_iters, ref.iters)
+
+
+@pytest.mark.parametrize("dims", [(30, 26, 22), (33, 17, 9)])
+def test_pcg_fp32_fixed_count_close_to_fp64(dims):
+    A = sstep.Stencil(*dims, points=7)
+    xt, b = I.poisson_problem(dims, 7)
+    K = 40
+    kw = dict(algo="pcg", rtol=0.0, max_outer=K, lambda_max=2.0)
+    xm, im, _ = solve(A, b, precision="fp32_rr", **kw)
+    xd, idd, _ = solve(A, b, **kw)
+    assert im.outer_iters == K and idd.outer_iters == K
+    assert relerr(xm, xd) <= 1e-4
+
+
+def test_pcg_fp32_zero_rhs_and_q1_rejected():
+    A = sstep.Stencil(12, 10, 8, 7)
+    x, info, _ = solve(A, np.zeros(960), algo="pcg", precision="fp32_rr", lambda_max=2.0)
+    assert info.status == sstep.OK and info.outer_iters == 0 and not x.any()
+    (rp, ci, v), kappa, xt, b = I.q1_lognormal_problem((8, 8, 8))
+    with pytest.raises(sstep.SstepError) as e:
+        sstep.Solver(sstep.Q1(8, 8, 8, dev(kappa)), algo="pcg", precision="fp32_rr", lambda_max=2.0)
+    assert e.value.status == sstep.ERR_UNSUPPORTED
