@@ -129,18 +129,24 @@ __host__ __device__ __forceinline__ double splitmix_pm1(uint64_t seed, int64_t i
   return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
 }
 
-// Error-free transformations on the FP32 pipe: TwoProd via FMA (a*b = p + e exactly) and
-// Knuth's TwoSum.  A (hi, lo) pair accumulates products of FP32 numbers with about 48 bits,
+// Error-free transformations on the FP32 pipe (Knuth's TwoSum; Dekker/Ogita-Rump-Oishi
+// products by FMA).  A (hi, lo) pair accumulates products of FP32 numbers with about 48 bits,
 // so Gram sums of FP32 vectors carry FP64-class accuracy while the narrow FP64 pipe of this
 // part stays idle.  Intrinsics keep the compiler from contracting the sequences.
+//
+// (hi, lo) += a b in 8 operations: p = fl(a b); TwoSum(hi, p) = s + (t1 + (p - bb)) exactly,
+// with bb = s - hi, t1 = hi - (s - bb) exact; the product's own error e = a b - p joins the
+// low-order part p - bb in one FMA, fma(a, b, -bb) = fl(a b - bb) = fl((p - bb) + e).  That
+// one rounding of a quantity of size <= u (|s| + |p|) costs u^2 (|s| + |p|): the same order as
+// the separate TwoProd + TwoSum + two low-order adds (10 operations), which round (err + e).
 __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float b) {
   const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);
   const float s = __fadd_rn(hi, p);
   const float bb = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float t1 = __fsub_rn(hi, __fsub_rn(s, bb));
+  const float t2 = __fmaf_rn(a, b, -bb);
   hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  lo = __fadd_rn(lo, __fadd_rn(t1, t2));
 }
 
 // (ah, al) += (bh, bl), renormalised.
@@ -423,6 +429,15 @@ cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStrea
 cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st);
 cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st);
 // g[k] (+)= -scale * lam[row(k)] * x[col(k)] over the CSR pattern
+// Differentiated Q1 solve (k_adjoint.cu): kappa = exp(theta); assembled CSR values of the Q1
+// operator; dL/dkappa (or dL/dtheta) = -lambda_c^T K_ref x_c per cell.
+cudaError_t launch_q1_exp(int64_t ncell, const double* theta, double* kappa, cudaStream_t st);
+cudaError_t launch_q1_assemble(int nx, int ny, int nz, const double* kappa, int64_t n,
+                               const int64_t* rowptr, const int32_t* colind, double* vals,
+                               int* bad, cudaStream_t st);
+cudaError_t launch_q1_grad(int nx, int ny, int nz, const double* kappa, const double* lam,
+                           const double* x, double* grad, int wrt_log, int accumulate,
+                           cudaStream_t st);
 cudaError_t launch_pattern_grad(const CsrOp& A, const double* lam, const double* x, double* g,
                                 double scale, int accumulate, cudaStream_t st);
 // x64 += xhi + xlo; xhi = xlo = 0 (before a residual replacement and at the end)

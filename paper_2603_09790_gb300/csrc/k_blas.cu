@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
 // Direction-block update in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r
 // accumulated in double-float (r = rhi + rlo), then alpha = FGS(W, b1) in the last CTA.
 template <int S, bool FIRST>
-__global__ void __launch_bounds__(kThreads, 1) k_upd_gramf(MixedArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_upd_gramf(MixedArgs a) {
   if (a.ctrl->done) return;
   constexpr int NW = S * (S + 1) / 2;  // upper triangle of W (symmetric), then b1
   constexpr int K = NW + S;
