@@ -63,6 +63,16 @@ def parse():
                         "(s in 4..10, eta diagnostics); 0 skips")
     p.add_argument("--q1", type=int, default=192,
                    help="edge of the Q1 log-normal diffusion workload (FP32 basis, s = 8); 0 skips")
+    p.add_argument("--grid", default="2,4,8:2,3",
+                   help="s values:nu values of the FP64 configuration grid timed once each at the "
+                        "headline size, stencil and CSR forms; empty skips")
+    p.add_argument("--oracle-full", default="",
+                   help="run the FP64 oracle to completion on the n^3 7-point workload for one "
+                        "configuration ('pcg' or '<literal|onesync>_s<S>nu<NU>') on one host "
+                        "thread, print its time as one JSON line and exit (no GPU work)")
+    p.add_argument("--small", type=int, default=64,
+                   help="edge of the 2D 5-point CSR workload (s = 4, nu = 2; GPU and oracle times); "
+                        "0 skips")
     return p.parse_args()
 
 
@@ -266,6 +276,103 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
+def run_grid(spec, N, dev, sstep, I, torch, b, v0d):
+    """The FP64 configuration grid at N^3: stencil and CSR forms x s x nu (literal form), plus
+    classical PCG per form.  One solve per configuration (its graph capture included, about a
+    millisecond); set-up (operator copy, Jacobi, Gershgorin bound, 20 power iterations) timed
+    separately and added into the total."""
+    s_list, nu_list = ([int(v) for v in part.split(",")] for part in spec.split(":"))
+    dims = (N, N, N)
+    rp, ci, vv = I.poisson_csr(dims, 7)
+    ops = {"stencil": lambda: sstep.Stencil(N, N, N, 7),
+           "csr": lambda: sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                                    torch.from_numpy(vv).to(dev))}
+    bd = torch.from_numpy(b).to(dev)
+    common = dict(rtol=1e-8, power_iters=20, power_tol=0.0, power_v0=v0d, lambda_min=-1.0)
+    out = {"workload": f"poisson7_{N}^3_jacobi_literal", "rtol": 1e-8,
+           "timing": "setup_s: host wall time of sstep_setup (power method included); solve_s: "
+                     "sstep_info.ms_solve of one solve (device buffers; first solve of the handle, "
+                     "graph capture included); total_s = setup_s + solve_s"}
+    for form, mk in ops.items():
+        A = mk()
+        cases = [(f"s{s_}_nu{nu_}", dict(s=s_, sweeps=nu_)) for s_ in s_list for nu_ in nu_list]
+        cases.append(("pcg", dict(algo="pcg")))
+        for label, kw in cases:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S = sstep.Solver(A, **common, **kw)
+            t_setup = time.perf_counter() - t0
+            x = torch.zeros_like(bd)
+            info = S.solve(bd, x)
+            S.free()
+            out[f"{form}_{label}"] = {
+                "setup_s": t_setup, "solve_s": info.ms_solve / 1e3,
+                "total_s": t_setup + info.ms_solve / 1e3, "outer_iters": info.outer_iters,
+                "inner_equiv": info.inner_equiv, "status": info.status,
+                "relres_true": info.relres_true}
+        del A
+        torch.cuda.empty_cache()
+    for form in ops:
+        pcg = out[f"{form}_pcg"]["solve_s"]
+        for k in list(out):
+            if k.startswith(form + "_s") and isinstance(out[k], dict):
+                out[k]["solve_over_pcg"] = out[k]["solve_s"] / pcg
+    return out
+
+
+def run_small(N, dev, sstep, I, torch, with_oracle):
+    """2D 5-point Poisson on an N x N grid, FP64 CSR, Jacobi, s = 4, nu = 2, Chebyshev interval
+    from 20 power iterations and the Gershgorin lower bound, rtol 1e-8; against classical PCG
+    of the library; the FP64 oracle run to completion on the same input (one host thread)."""
+    dims = (N, N)
+    rp, ci, vv = I.poisson_csr(dims, 5)
+    xt, b = I.poisson_problem(dims, 5)
+    v0 = I.power_start(N * N)
+    A = sstep.CSR(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(vv).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    common = dict(rtol=1e-8, power_iters=20, power_tol=0.0, power_v0=torch.from_numpy(v0).to(dev),
+                  lambda_min=-1.0)
+    out = {"workload": f"poisson5_{N}x{N}_csr_jacobi_literal_s4_nu2", "n": N * N, "nnz": int(rp[-1]),
+           "timing": "median of 5 solves (sstep_info.ms_solve, device buffers) after a warm-up; "
+                     "setup_s: host wall time of sstep_setup"}
+    lam = None
+    for label, kw in (("sstep", dict(s=4, sweeps=2)), ("pcg", dict(algo="pcg"))):
+        t0 = time.perf_counter()
+        S = sstep.Solver(A, **common, **kw)
+        t_setup = time.perf_counter() - t0
+        x = torch.zeros_like(bd)
+        S.solve(bd, x)
+        ts, info = [], None
+        for _ in range(5):
+            x.zero_()
+            info = S.solve(bd, x)
+            ts.append(info.ms_solve / 1e3)
+        if label == "sstep":
+            lam = S.get_basis_info()["lambda_max"]
+        S.free()
+        out[label] = {"setup_s": t_setup, "solve_s": float(np.median(ts)),
+                      "outer_iters": info.outer_iters, "relres_true": info.relres_true,
+                      "x_rel_error_vs_true": float(np.linalg.norm(x.cpu().numpy() - xt) / np.linalg.norm(xt))}
+    out["sstep_over_pcg"] = out["sstep"]["solve_s"] / out["pcg"]["solve_s"]
+    if with_oracle:
+        import oracle as O
+        Ac = O.CSR(rp, ci, vv)
+        t0 = time.perf_counter()
+        lam_o, _ = O.power(Ac, "jacobi", v0, 20, 0.0)
+        ref = O.pcgs(Ac, b, s=4, nu=2, rtol=1e-8, algo="literal",
+                     lambda_min=O.gershgorin_lower(Ac, "jacobi"), lambda_max=lam_o)
+        t_or = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        refp = O.pcg(Ac, b, rtol=1e-8)
+        t_orp = time.perf_counter() - t0
+        out["oracle"] = {"sstep_s": t_or, "sstep_outer_iters": ref.iters, "pcg_s": t_orp,
+                         "pcg_iters": refp.iters, "cores": 1,
+                         "what": "the FP64 C oracle (plain sequential loops) run to completion, "
+                                 "power method included, one host thread"}
+        out["lambda_max_gpu_vs_oracle"] = [lam, lam_o]
+    return out
+
+
 def run_batch(spec, dev, sstep, I, torch, shape="0:0"):
     """Batched workload: nsys 7-point Poisson systems with edges drawn uniformly in 32..96
     (seed 0), nrhs right-hand sides each (U[-1,1), seed 1 + system), Jacobi, nu = 3, rtol 1e-8,
@@ -444,24 +551,26 @@ def run_hpcg27(N, dev, sstep, torch):
 def run_adjoint(N, dev, sstep, I, torch):
     """Differentiated solve: Q1 diffusion on N^3 interior vertices with kappa = exp(theta),
     theta ~ N(0, 0.5^2) iid per cell (seed 0), b = 1, loss = ||x - x_target||^2 with x_target
-    the solution for theta = 0.  Forward + backward (x recomputed, adjoint s-step solve, pattern
-    gradient, assembly transpose) against one plain FP64 solve of the same system; the gradient
-    is checked by central differences on 4 random cells."""
+    the solution for theta = 0.  Forward + backward through autograd.q1_solve (kappa = exp(theta),
+    device assembly of the CSR values for the AMG preconditioner, x recomputed in backward,
+    adjoint s-step solve, per-cell gradient kernel) against one plain FP64 set-up + solve of the
+    same system; the gradient is checked by central differences on 32 random cells (seed 2,
+    h = 1e-3, solves at rtol 1e-12 with the matrix-free operator and Jacobi)."""
     from paper_2603_09790_gb300 import autograd as AG
     dims = (N, N, N)
     t0 = time.perf_counter()
-    asm = AG.Q1Assembly(dims, dev)
-    t_asm = time.perf_counter() - t0
+    patt = AG.Q1Pattern(dims, dev)
+    t_pat = time.perf_counter() - t0
     ncell = (N + 1) ** 3
     theta0 = torch.from_numpy(0.5 * I.normal_pm(0, ncell)).to(dev)
     b = torch.ones(N ** 3, dtype=torch.float64, device=dev)
     opts = dict(s=4, sweeps=30, rtol=1e-8, power_iters=20, power_tol=0.0, precond="amg",
                 amg_coarse_max=512)
     with torch.no_grad():
-        x_target = AG.solve(asm.values(torch.ones_like(theta0)), b, asm.pattern, **opts)
+        x_target = AG.q1_solve(torch.zeros_like(theta0), b, patt, **dict(opts, precond="jacobi"))
 
     def loss_of(th, o):
-        x = AG.solve(asm.values(torch.exp(th)), b, asm.pattern, **o)
+        x = AG.q1_solve(th, b, patt, **o)
         return torch.sum((x - x_target) ** 2)
 
     th = theta0.clone().requires_grad_(True)
@@ -476,52 +585,96 @@ def run_adjoint(N, dev, sstep, I, torch):
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t0
     g = th.grad
-    # the plain FP64 form: set-up and solve of the same system, no gradient
-    vals = asm.values(torch.exp(theta0)).contiguous()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A = sstep.CSR(asm.pattern.rowptr, asm.pattern.colind, vals)
-    with sstep.Solver(A, **opts) as S:
+    # plain FP64 set-up + solve of the same system, AMG and Jacobi, set-up and solve apart
+    kappa = torch.empty_like(theta0)
+    sstep.q1_exp(theta0, kappa)
+    vals = patt.values(kappa)
+    A = sstep.CSR(patt.pattern.rowptr, patt.pattern.colind, vals)
+    plain = {}
+    for label, op, kw in (("amg_csr", A, opts), ("jacobi_csr", A, dict(opts, precond="jacobi")),
+                          ("jacobi_matrix_free", sstep.Q1(N, N, N, kappa), dict(opts, precond="jacobi"))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = sstep.Solver(op, **kw)
+        t_setup = time.perf_counter() - t0
         x = torch.zeros_like(b)
+        S.solve(b, x)  # graph capture
+        x.zero_()
         info = S.solve(b, x)
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    # central differences on 4 random cells, solves at rtol 1e-12
-    o12 = dict(opts, rtol=1e-12)
+        S.free()
+        plain[label] = {"setup_s": t_setup, "solve_s": info.ms_solve / 1e3,
+                        "outer_iters": info.outer_iters, "relres_true": info.relres_true}
+    # central differences on 32 random cells, solves at rtol 1e-12 (matrix-free, Jacobi)
+    o12 = dict(opts, rtol=1e-12, precond="jacobi")
     rng = np.random.default_rng(2)
-    cells = rng.choice(ncell, 4, replace=False)
+    cells = rng.choice(ncell, 32, replace=False)
     h = 1e-3
     fd_err = []
+    t0 = time.perf_counter()
+    gmax = max(abs(g).max().item(), 1e-300)
     with torch.no_grad():
         for c in cells:
             tp, tm = theta0.clone(), theta0.clone()
             tp[c] += h
             tm[c] -= h
             fd = (loss_of(tp, o12).item() - loss_of(tm, o12).item()) / (2 * h)
-            fd_err.append(abs(fd - g[c].item()) / max(abs(g).max().item(), 1e-300))
-    # the same solve with Jacobi instead of the V-cycle
-    t0 = time.perf_counter()
-    with sstep.Solver(A, **dict(opts, precond="jacobi")) as S:
-        xj = torch.zeros_like(b)
-        info_j = S.solve(b, xj)
-    torch.cuda.synchronize()
-    t_jac = time.perf_counter() - t0
-    return {"workload": f"q1_theta_{N}^3_csr_amg_literal_s4_nu30_adjoint", "n": N ** 3,
-            "amg": "double pairwise aggregation, l1-Jacobi V-cycle, dense coarse solve at <= 512",
-            "plain_fp64_jacobi_setup_solve_s": t_jac, "plain_jacobi_outer_iters": info_j.outer_iters,
-            "cells": ncell, "assembly_map_s": t_asm, "loss": float(loss.item()),
-            "forward_s": t_fwd, "forward_backward_s": t_all, "plain_fp64_setup_solve_s": t_plain,
-            "plain_outer_iters": info.outer_iters,
-            "forward_backward_over_plain": t_all / t_plain,
+            fd_err.append(abs(fd - g[c].item()) / gmax)
+    t_fd = time.perf_counter() - t0
+    return {"workload": f"q1_theta_{N}^3_amg_literal_s4_nu30_adjoint", "n": N ** 3,
+            "amg": "double pairwise aggregation, l1-Jacobi V-cycle, dense coarse solve at <= 512; "
+                   "hierarchy set up on the host, V-cycle on the device",
+            "cells": ncell, "pattern_s": t_pat, "loss": float(loss.item()),
+            "forward_s": t_fwd, "forward_backward_s": t_all,
+            "plain_fp64": plain,
+            "forward_backward_over_plain_amg": t_all / (plain["amg_csr"]["setup_s"] + plain["amg_csr"]["solve_s"]),
             "fd_cells": [int(c) for c in cells], "fd_step": h,
-            "fd_max_err_rel_to_max_grad": float(max(fd_err)),
-            "timing": "host wall time (synchronised), set-up of every solver handle included"}
+            "fd_max_err_rel_to_max_grad": float(max(fd_err)), "fd_s": t_fd,
+            "timing": "host wall time (synchronised); forward/backward include every handle set-up "
+                      "(AMG hierarchy included); plain_fp64 splits set-up and solve"}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = dict(l.split(":", 1) for l in out.splitlines() if ":" in l)
+        return {k: info.get(k, "").strip() for k in ("Architecture", "Model name", "CPU(s)", "Vendor ID")}
+    except Exception:
+        return {}
+
+
+def run_oracle_full(args):
+    """The FP64 oracle run to completion (rtol 1e-8) on the n^3 7-point workload, one host
+    thread: power method (20 iterations, start vector seed 1) + PCG-S or PCG."""
+    import oracle as O
+    from paper_2603_09790_gb300 import inputs as I
+    dims = (args.n,) * 3
+    A = O.CSR(*I.poisson_csr(dims, 7))
+    xt, b = I.poisson_problem(dims, 7)
+    cfg = args.oracle_full
+    t0 = time.perf_counter()
+    lam, _ = O.power(A, "jacobi", I.power_start(A.n), 20, 0.0)
+    t_power = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if cfg == "pcg":
+        r = O.pcg(A, b, rtol=1e-8)
+    else:
+        algo, rest = cfg.split("_")
+        s_, nu_ = rest[1:].split("nu")
+        r = O.pcgs(A, b, s=int(s_), nu=int(nu_), rtol=1e-8, algo=algo,
+                   lambda_min=O.gershgorin_lower(A, "jacobi"), lambda_max=lam)
+    t_solve = time.perf_counter() - t0
+    print(json.dumps({"oracle_full": cfg, "n": A.n, "power_s": t_power, "solve_s": t_solve,
+                      "total_s": t_power + t_solve, "iters": r.iters, "status": r.status,
+                      "relres_true": r.relres_true, "cores": 1, "cpu": cpu_model()}))
+    return 0
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.oracle_full:
+        return run_oracle_full(args)
 
     import torch
     import torch.distributed as dist
@@ -629,6 +782,15 @@ def main():
     pph = P.profile(bd, iters=5)
     P.free()
 
+    # ---- classical PCG in the FP32-basis precision recipe (FP32 p, A p; double-float x, r;
+    # FP64 residual replacement every 16 iterations), the comparator of the FP32 s-step forms
+    PF = sstep.Solver(A, algo="pcg", precision="fp32_rr", **common)
+    xpf = torch.zeros(n, dtype=torch.float64, device=dev)
+    pfms, pfinfos = timed_solves(PF, xpf, args.steps, args.warmup)
+    PF.profile(bd, iters=2)
+    pfph = PF.profile(bd, iters=5)
+    PF.free()
+
     # ---- optional extra s-step configurations
     extra = {}
     x_fp64 = torch.from_numpy(x_host).to(dev)  # the headline FP64 solution
@@ -646,6 +808,8 @@ def main():
             "s": ems[0] / 1e3, "outer_iters": einfos[0].outer_iters,
             "relres_true": einfos[0].relres_true, "rel_diff_vs_fp64_solution": err,
             "time_over_fp64_pcg": ems[0] / float(np.mean(pms))}
+        if prec == "fp32_rr":
+            extra[key]["time_over_fp32_pcg"] = ems[0] / float(np.mean(pfms))
         if prec == "fp32_rr":  # the FP32 kernels are HBM-bound: GB/s per launch
             E.profile(bd, iters=2)
             fph = E.profile(bd, iters=5)
@@ -662,6 +826,9 @@ def main():
                                                      for k in fb) / (sum(fph[:4]) * 1e-3) / 1e9 / hbm_
         E.free()
 
+    grid = run_grid(args.grid, N, dev, sstep, I, torch, b, v0d) if args.grid else None
+    small = run_small(args.small, dev, sstep, I, torch,
+                      rank == 0 and not args.no_cpu_baseline) if args.small > 0 else None
     batch = run_batch(args.batch, dev, sstep, I, torch, args.batch_shape) if args.batch else None
     q1 = run_q1(args.q1, dev, sstep, I, torch) if args.q1 > 0 else None
     adjoint = run_adjoint(args.adjoint, dev, sstep, I, torch) if args.adjoint > 0 else None
@@ -721,6 +888,12 @@ def main():
         "pcg": {"s": float(np.mean(pms)) / 1e3, "iters": pinfos[-1].outer_iters,
                 "relres_true": pinfos[-1].relres_true},
         "sstep_over_pcg_time": ms_step / float(np.mean(pms)),
+        "pcg_fp32_rr": {"s": float(np.mean(pfms)) / 1e3, "iters": pfinfos[-1].outer_iters,
+                        "relres_true": pfinfos[-1].relres_true, "rr_period": 16,
+                        "phase_ms": {"spmv_pap": pfph[0], "update": pfph[1], "pdir": pfph[2]}},
+        "setup_s": {"headline_sstep": info.ms_setup / 1e3},
+        "configs_fp64_256": grid,
+        "poisson5_64x64_csr": small,
         "extra_configs": extra,
         "batched": batch,
         "q1_diffusion": q1,
@@ -742,7 +915,8 @@ def main():
             "value": v, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": f"2 power + 2 outer iterations + 8 PCG iterations of the FP64 C oracle at {N}^3 "
                       f"(single thread), extrapolated to 20 power and {n_outer} outer iterations",
-            "pcg_value": t_pcg * (oracle_counts().get("pcg", {}).get("iters") or pinfos[-1].outer_iters)}
+            "pcg_value": t_pcg * (oracle_counts().get("pcg", {}).get("iters") or pinfos[-1].outer_iters),
+            "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

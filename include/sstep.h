@@ -318,6 +318,49 @@ SSTEP_API sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, cons
                                           const double* lam, const double* x, double* grad_vals,
                                           double scale, int accumulate, void* stream);
 
+/* The differentiated Q1 diffusion solve (the paper has no counterpart; this is the adjoint of a
+ * linear solve).  Q1 finite elements on the unit cells of an (nx+1) x (ny+1) x (nz+1) cell grid,
+ * one conductivity per cell (cell cx + (nx+1)(cy + (ny+1) cz)), unknowns at the nx*ny*nz
+ * interior vertices (vertex i + nx (j + ny k) at grid point (i+1, j+1, k+1)), Dirichlet
+ * boundary eliminated: A = sum_c kappa_c P_c^T K_ref P_c with the trilinear element stiffness
+ * K_ref (local vertex lx + 2 ly + 4 lz).  All pointers are device pointers; stream is a
+ * cudaStream_t as void*; the calls are stream-ordered and allocate nothing but the 4-byte flag
+ * of sstep_q1_assemble. */
+
+/* kappa[c] = exp(theta[c]) for c < ncell (conductivity from log-conductivity). */
+SSTEP_API sstep_status sstep_q1_exp(int64_t ncell, const double* theta, double* kappa, void* stream);
+
+/* Assembled CSR values of the Q1 operator for conductivities kappa on the pattern (rowptr
+ * int64 n+1, colind int32) of an n = nx*ny*nz vertex grid: vals[k] for entry (i, j) = sum
+ * over the cells c shared by vertices i and j of kappa_c K_ref[l_i(c), l_j(c)].  A column that
+ * is not one of the 27 neighbours of its row: SSTEP_ERR_INVALID (the stream is synchronised to
+ * read the flag). */
+SSTEP_API sstep_status sstep_q1_assemble(int nx, int ny, int nz, const double* kappa,
+                                         const int64_t* rowptr, const int32_t* colind,
+                                         double* vals, void* stream);
+
+/* Gradient of a loss L(x), x = A(kappa)^{-1} b, with respect to the cell conductivities, from
+ * x and the adjoint lambda (A lambda = dL/dx): grad[c] (+)= -lambda_c^T K_ref x_c, where
+ * lambda_c, x_c hold the cell's 8 vertex values (0 at boundary vertices).  wrt_log = 1 gives
+ * dL/dtheta_c = kappa_c dL/dkappa_c for kappa = exp(theta).  grad: (nx+1)(ny+1)(nz+1)
+ * doubles. */
+SSTEP_API sstep_status sstep_q1_grad(int nx, int ny, int nz, const double* kappa, const double* lam,
+                                     const double* x, double* grad, int wrt_log, int accumulate,
+                                     void* stream);
+
+/* Gradient of a loss with respect to the weights of a batch of 7-point stencil systems
+ * A_i = wc_i I + wo_i N (N: the sum of the six axis neighbours inside the grid; the form the
+ * batched solver takes), each with `nrhs` right-hand sides, from the solutions x and the adjoint
+ * solutions lambda (A_i lambda = dL/dx): grad[2 i] = dL/dwc_i = -sum_r lambda_ir^T x_ir and
+ * grad[2 i + 1] = dL/dwo_i = -sum_r lambda_ir^T N x_ir, the right-hand sides r summed in
+ * increasing order.  dims: host int[3 nsys] (nx, ny, nz per system); lam, x: host arrays of
+ * nsys * nrhs device pointers, system-major; grad: device double[2 nsys].  Allocates a
+ * stream-ordered table of the problems.  The paper has no counterpart. */
+SSTEP_API sstep_status sstep_stencil7_weight_grad(int nsys, int nrhs, const int* dims,
+                                                  const double* const* lam,
+                                                  const double* const* x, double* grad,
+                                                  void* stream);
+
 /* Replace the values of the handle's operator, device or host: CSR vals[nnz] (same pattern), or
  * the Q1 cell conductivities ((nx+1)(ny+1)(nz+1) doubles, checked like at set-up).  M^{-1}
  * (Jacobi), the AMG hierarchy and the FP32 copies are refreshed; the Chebyshev interval is

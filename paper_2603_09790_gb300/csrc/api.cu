@@ -1488,6 +1488,73 @@ sstep_status sstep_pattern_grad(int64_t n, const int64_t* rowptr, const int32_t*
   return SSTEP_OK;
 }
 
+sstep_status sstep_q1_exp(int64_t ncell, const double* theta, double* kappa, void* stream) {
+  g_err.clear();
+  if (ncell < 1 || !theta || !kappa) return fail(SSTEP_ERR_INVALID, "bad q1_exp arguments");
+  CK(launch_q1_exp(ncell, theta, kappa, (cudaStream_t)stream));
+  return SSTEP_OK;
+}
+
+sstep_status sstep_q1_assemble(int nx, int ny, int nz, const double* kappa, const int64_t* rowptr,
+                               const int32_t* colind, double* vals, void* stream) {
+  g_err.clear();
+  if (nx < 1 || ny < 1 || nz < 1 || !kappa || !rowptr || !colind || !vals)
+    return fail(SSTEP_ERR_INVALID, "bad q1_assemble arguments");
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = (int64_t)nx * ny * nz;
+  int* bad = nullptr;
+  CK(cudaMallocAsync((void**)&bad, sizeof(int), st));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  CK(launch_q1_assemble(nx, ny, nz, kappa, n, rowptr, colind, vals, bad, st));
+  int hbad = 0;
+  CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaFreeAsync(bad, st));
+  CK(cudaStreamSynchronize(st));
+  if (hbad) return fail(SSTEP_ERR_INVALID, "q1_assemble: a column is not a neighbour of its row");
+  return SSTEP_OK;
+}
+
+sstep_status sstep_q1_grad(int nx, int ny, int nz, const double* kappa, const double* lam,
+                           const double* x, double* grad, int wrt_log, int accumulate,
+                           void* stream) {
+  g_err.clear();
+  if (nx < 1 || ny < 1 || nz < 1 || !lam || !x || !grad || (wrt_log && !kappa))
+    return fail(SSTEP_ERR_INVALID, "bad q1_grad arguments");
+  CK(launch_q1_grad(nx, ny, nz, kappa, lam, x, grad, wrt_log, accumulate, (cudaStream_t)stream));
+  return SSTEP_OK;
+}
+
+sstep_status sstep_stencil7_weight_grad(int nsys, int nrhs, const int* dims, const double* const* lam,
+                                        const double* const* x, double* grad, void* stream) {
+  g_err.clear();
+  if (nsys < 1 || nrhs < 1 || !dims || !lam || !x || !grad)
+    return fail(SSTEP_ERR_INVALID, "bad stencil7_weight_grad arguments");
+  const int np = nsys * nrhs;
+  std::vector<Bil7Prob> tab(np);
+  for (int i = 0; i < nsys; ++i) {
+    const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SSTEP_ERR_INVALID, "grid dimensions must be >= 1");
+    for (int r = 0; r < nrhs; ++r) {
+      const int p = i * nrhs + r;
+      if (!lam[p] || !x[p]) return fail(SSTEP_ERR_INVALID, "null vector pointer");
+      tab[p] = Bil7Prob{nx, ny, nz, lam[p], x[p]};
+    }
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  Bil7Prob* dtab = nullptr;
+  double* part = nullptr;
+  CK(cudaMallocAsync((void**)&dtab, sizeof(Bil7Prob) * np, st));
+  CK(cudaMallocAsync((void**)&part, sizeof(double) * 2 * np, st));
+  CK(cudaMemcpyAsync(dtab, tab.data(), sizeof(Bil7Prob) * np, cudaMemcpyHostToDevice, st));
+  CK(launch_stencil7_bilinear(dtab, np, part, st));
+  CK(launch_sum_groups(part, nsys, nrhs, 2, -1.0, grad, st));
+  CK(cudaFreeAsync(dtab, st));
+  CK(cudaFreeAsync(part, st));
+  // the host table must outlive the copy
+  CK(cudaStreamSynchronize(st));
+  return SSTEP_OK;
+}
+
 sstep_status sstep_update_values(sstep_handle h, const double* vals) {
   g_err.clear();
   if (!h || !vals) return fail(SSTEP_ERR_INVALID, "null argument");

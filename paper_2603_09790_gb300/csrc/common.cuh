@@ -149,6 +149,24 @@ __device__ __forceinline__ void df_acc_prod(float& hi, float& lo, float a, float
   lo = __fadd_rn(lo, __fadd_rn(t1, t2));
 }
 
+// (hi, lo) += a.x b.x + a.y b.y + a.z b.z + a.w b.w: the four TwoSum steps of df_acc_prod on
+// hi, their low-order parts (each t1 + fl(a b - bb)) summed pairwise and added to lo once:
+// 7 instead of 8 operations per product, the same u^2 error class per product.
+__device__ __forceinline__ float df_step(float& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float s1 = __fadd_rn(s, p);
+  const float bb = __fsub_rn(s1, s);
+  const float t1 = __fsub_rn(s, __fsub_rn(s1, bb));
+  const float t2 = __fmaf_rn(a, b, -bb);
+  s = s1;
+  return __fadd_rn(t1, t2);
+}
+__device__ __forceinline__ void df_acc_dot4(float& hi, float& lo, float4 a, float4 b) {
+  const float l0 = df_step(hi, a.x, b.x), l1 = df_step(hi, a.y, b.y);
+  const float l2 = df_step(hi, a.z, b.z), l3 = df_step(hi, a.w, b.w);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(l0, l1), __fadd_rn(l2, l3)));
+}
+
 // (ah, al) += (bh, bl), renormalised.
 __device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
   const float s = __fadd_rn(ah, bh);
@@ -262,7 +280,11 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
-  // warp stage in double-float on the FP32 pipe; one FP64 conversion per warp and value
+  // warp stage in double-float on the FP32 pipe (every lane ends with the warp's sums); lane k
+  // then keeps value k, so that each warp converts its K values to FP64 with one instruction
+  // sequence per 32 values: an FP64 instruction costs a sub-partition tens of cycles however
+  // few of its lanes are active
+  float kh = 0.0f, kl = 0.0f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     float h = hi[k], l = lo[k];
@@ -272,7 +294,14 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
       const float ol = __shfl_xor_sync(0xffffffffu, l, o);
       df_add(h, l, oh, ol);
     }
-    if (lane == 0) buf[wid * K + k] = (double)h + (double)l;
+    if ((k & 31) == lane) {
+      kh = h;
+      kl = l;
+    }
+    if ((k & 31) == 31 || k == K - 1) {
+      const int k0 = k & ~31;
+      if (lane <= k - k0) buf[wid * K + k0 + lane] = (double)kh + (double)kl;
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -438,6 +467,17 @@ cudaError_t launch_q1_assemble(int nx, int ny, int nz, const double* kappa, int6
 cudaError_t launch_q1_grad(int nx, int ny, int nz, const double* kappa, const double* lam,
                            const double* x, double* grad, int wrt_log, int accumulate,
                            cudaStream_t st);
+// Bilinear forms of a batch of 7-point problems (k_adjoint.cu): per problem lam^T x and
+// lam^T (N x), N the six-neighbour sum; then per-group sums with a scale.
+struct Bil7Prob {
+  int nx, ny, nz;
+  const double* lam;
+  const double* x;
+};
+cudaError_t launch_stencil7_bilinear(const Bil7Prob* probs_dev, int nprob, double* out,
+                                     cudaStream_t st);
+cudaError_t launch_sum_groups(const double* in, int groups, int per, int w, double scale,
+                              double* out, cudaStream_t st);
 cudaError_t launch_pattern_grad(const CsrOp& A, const double* lam, const double* x, double* g,
                                 double scale, int accumulate, cudaStream_t st);
 // x64 += xhi + xlo; xhi = xlo = 0 (before a residual replacement and at the end)

@@ -42,73 +42,14 @@ int sm_count() {
 
 // ---------------------------------------------------------------- reduced-system tail
 
-// nu forward Gauss-Seidel sweeps from x = 0 on W x = b (W: s x s column-major in shared
-// memory), Eq. (fgs-iteration) in its plain form on W.  One thread per right-hand side.
-__device__ void fgs_column(int s, const double* W, const double* rinv, const double* b, int nu,
-                           double* x, int stride) {
-  for (int i = 0; i < s; ++i) x[i * stride] = 0.0;
-  for (int sw = 0; sw < nu; ++sw) {
-    for (int i = 0; i < s; ++i) {
-      double a0 = b[i], a1 = 0.0;
-      int j = 0;
-      for (; j + 1 < s; j += 2) {
-        if (j != i) a0 = fma(-W[i + j * s], x[j * stride], a0);
-        if (j + 1 != i) a1 = fma(-W[i + (j + 1) * s], x[(j + 1) * stride], a1);
-      }
-      if (j < s && j != i) a0 = fma(-W[i + j * s], x[j * stride], a0);
-      x[i * stride] = (a0 + a1) * rinv[i];
-    }
-  }
-}
-
-// fgs_column for a compile-time s <= 4: the same operations in the same order (bit-identical
-// results), with the row loops unrolled so that the W loads leave the dependent chain and x
-// stays in registers.
-template <int S>
-__device__ void fgs_column_s(const double* Wp, const double* rinv, const double* b, int nu,
-                             double* x, int stride) {
-  // W is re-read from shared memory every sweep (volatile): hoisting all s^2 entries into
-  // registers would raise the register count of every kernel that carries this tail
-  const volatile double* W = Wp;
-  double xv[S];
-#pragma unroll
-  for (int i = 0; i < S; ++i) xv[i] = 0.0;
-  for (int sw = 0; sw < nu; ++sw) {
-#pragma unroll
-    for (int i = 0; i < S; ++i) {
-      double a0 = b[i], a1 = 0.0;
-#pragma unroll
-      for (int j = 0; j + 1 < S; j += 2) {
-        if (j != i) a0 = fma(-W[i + j * S], xv[j], a0);
-        if (j + 1 != i) a1 = fma(-W[i + (j + 1) * S], xv[j + 1], a1);
-      }
-      if constexpr (S % 2 == 1) {
-        if (S - 1 != i) a0 = fma(-W[i + (S - 1) * S], xv[S - 1], a0);
-      }
-      xv[i] = (a0 + a1) * rinv[i];
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < S; ++i) x[i * stride] = xv[i];
-}
-
-__device__ void fgs_dispatch(int s, const double* W, const double* rinv, const double* b, int nu,
-                             double* x, int stride) {
-  switch (s) {
-    case 1: fgs_column_s<1>(W, rinv, b, nu, x, stride); return;
-    case 2: fgs_column_s<2>(W, rinv, b, nu, x, stride); return;
-    case 3: fgs_column_s<3>(W, rinv, b, nu, x, stride); return;
-    case 4: fgs_column_s<4>(W, rinv, b, nu, x, stride); return;
-    default: fgs_column(s, W, rinv, b, nu, x, stride); return;
-  }
-}
-
-// Forward Gauss-Seidel for s >= 5 with one warp per right-hand side, lane i owning row i.  The
-// part of row i above the diagonal uses the previous sweep's x and is formed by all lanes at
-// once; each new x_k is then passed down the warp, so the sequential chain per row is one
-// multiply, one shuffle and one FMA instead of a dot product of s terms (the reduced solves of
-// s = 8, nu = 30 were latency-bound on the FP64 pipe).  The same sums as fgs_column, added in
-// another order: the terms above the diagonal first.  Executed by the whole CTA.
+// nu forward Gauss-Seidel sweeps from x = 0 on W x = b (W: s x s column-major in shared memory),
+// Eq. (fgs-iteration) in its plain form on W: x_i <- (b_i - sum_{j != i} W_ij x_j) / W_ii, rows
+// in increasing order, the rows above i taking this sweep's values.  One warp per right-hand
+// side, lane i owning row i.  The part of row i above the diagonal uses the previous sweep's x
+// and is formed by all lanes at once; each new x_k is then passed down the warp, so the
+// sequential chain per row is one multiply, one shuffle and one FMA instead of a dot product of
+// s terms.  The terms above the diagonal are added first, then those below it in increasing
+// order.  Executed by the whole CTA.
 __device__ void fgs_warp(int s, const double* W, const double* rinv, const double* B, int nrhs,
                          int nu, double* X) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -139,6 +80,54 @@ __device__ void fgs_warp(int s, const double* W, const double* rinv, const doubl
       x = xn;
     }
     if (row) X[lane + c * s] = x;
+  }
+}
+
+// fgs_warp with the step size known at compile time: the same operations in the same order
+// (bit-identical results), with every loop over the rows exactly s long, so that the chain of
+// dependent FP64 operations per sweep is s - 1 multiply-adds (above the diagonal) and s
+// (multiply, shuffle, multiply-add) steps, not kMaxS of each.
+template <int S>
+__device__ void fgs_warp_s(const double* W, const double* rinv, const double* B, int nrhs, int nu,
+                           double* X) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool row = lane < S;
+  double wr[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) wr[j] = row ? W[lane + j * S] : 0.0;
+  const double ri = row ? rinv[lane] : 0.0;
+  for (int c = warp; c < nrhs; c += nw) {
+    const double bi = row ? B[lane + c * S] : 0.0;
+    double x = 0.0;
+    for (int sw = 0; sw < nu; ++sw) {
+      double up = 0.0;
+#pragma unroll
+      for (int j = 1; j < S; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j);
+        if (j > lane) up = fma(-wr[j], xj, up);
+      }
+      double acc = bi + up, xn = x;
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        if (lane == k) xn = acc * ri;
+        const double xk = __shfl_sync(0xffffffffu, xn, k);
+        if (lane > k && row) acc = fma(-wr[k], xk, acc);
+      }
+      x = xn;
+    }
+    if (row) X[lane + c * S] = x;
+  }
+}
+
+__device__ void fgs_warp_dispatch(int s, const double* W, const double* rinv, const double* B,
+                                  int nrhs, int nu, double* X) {
+  switch (s) {
+    case 1: fgs_warp_s<1>(W, rinv, B, nrhs, nu, X); return;
+    case 2: fgs_warp_s<2>(W, rinv, B, nrhs, nu, X); return;
+    case 3: fgs_warp_s<3>(W, rinv, B, nrhs, nu, X); return;
+    case 4: fgs_warp_s<4>(W, rinv, B, nrhs, nu, X); return;
+    case 8: fgs_warp_s<8>(W, rinv, B, nrhs, nu, X); return;
+    default: fgs_warp(s, W, rinv, B, nrhs, nu, X); return;
   }
 }
 
@@ -175,33 +164,46 @@ __device__ void chol_column(int s, const double* L, const double* b, double* x, 
 
 // Solve W X = B for nrhs columns (B, X column-major s x nrhs in shared memory) with nu FGS
 // sweeps or exactly (Cholesky).  Executed by the whole CTA; returns false on breakdown.
+//
+// The FP64 pipe of this part is narrow: a warp's FP64 instruction occupies its SM sub-partition
+// for tens of cycles whether one lane or thirty-two are active, so this serial tail is written
+// lane-parallel.  Warp 0 checks the entries and forms the s reciprocals of the diagonal with one
+// instruction sequence (lane i: row i); the FGS sweeps run one warp per right-hand side
+// (fgs_warp: lane i owns row i, successive right-hand sides on successive warps, which the SM
+// schedules on different sub-partitions).
 __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs, int nu,
                               int solver, double* X, double* scratch /* s*s + s */) {
   __shared__ int ok;
-  if (threadIdx.x == 0) {
-    ok = 1;
-    for (int i = 0; i < s; ++i) {
-      const double d = W[i + i * s];
-      if (!(d > 0.0) || d > 1.79e308) ok = 0;
-    }
-    for (int i = 0; i < s * s; ++i)
-      if (!(W[i] == W[i]) || fabs(W[i]) > 1.79e308) ok = 0;
-    if (ok) {
-      if (solver == SSTEP_GRAM_CHOLESKY) {
-        if (!chol_factor(s, W, scratch)) ok = 0;
-      } else {
-        for (int i = 0; i < s; ++i) scratch[s * s + i] = 1.0 / W[i + i * s];
+  const int tid = threadIdx.x;
+  if (solver == SSTEP_GRAM_CHOLESKY) {
+    if (tid == 0) {
+      ok = 1;
+      for (int i = 0; i < s; ++i) {
+        const double d = W[i + i * s];
+        if (!(d > 0.0) || d > 1.79e308) ok = 0;
       }
+      for (int i = 0; i < s * s; ++i)
+        if (!(W[i] == W[i]) || fabs(W[i]) > 1.79e308) ok = 0;
+      if (ok && !chol_factor(s, W, scratch)) ok = 0;
     }
+  } else if (tid < 32) {
+    bool good = true;
+    for (int e = tid; e < s * s; e += 32)
+      if (!(W[e] == W[e]) || fabs(W[e]) > 1.79e308) good = false;
+    if (tid < s) {
+      const double d = W[tid + tid * s];
+      if (!(d > 0.0) || d > 1.79e308) good = false;
+      else scratch[s * s + tid] = 1.0 / d;
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (tid == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
   if (!ok) return false;
-  if (solver != SSTEP_GRAM_CHOLESKY && s >= 5) {
-    fgs_warp(s, W, scratch + s * s, B, nrhs, nu, X);
-  } else if ((int)threadIdx.x < nrhs) {
-    const int c = threadIdx.x;
-    if (solver == SSTEP_GRAM_CHOLESKY) chol_column(s, scratch, B + c * s, X + c * s, 1);
-    else fgs_dispatch(s, W, scratch + s * s, B + c * s, nu, X + c * s, 1);
+  if (solver != SSTEP_GRAM_CHOLESKY) {
+    fgs_warp_dispatch(s, W, scratch + s * s, B, nrhs, nu, X);
+  } else if (tid < nrhs) {
+    chol_column(s, scratch, B + tid * s, X + tid * s, 1);
   }
   __syncthreads();
   return true;
@@ -674,8 +676,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
 // ---------------------------------------------------------------- mixed path (FP32 basis)
 
 // Conjugation system of Section 2: b2 = -Q^T AZ from FP32 blocks, then beta = FGS(W, b2).
+// Four consecutive points per thread and trip (16-byte loads); the next trip's eight vectors are
+// loaded before this trip's products, so every thread keeps 256 bytes in flight while it
+// computes (two CTAs of 256 threads per SM, 128 registers).
 template <int S>
-__global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_gram_b2f(MixedArgs a) {
   if (a.ctrl->done) return;
   constexpr int K = S * S;
   __shared__ double buf[kTiledSmem];
@@ -685,7 +690,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
   const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // four consecutive points per thread and trip (16-byte loads: more bytes in flight)
   const int64_t n4 = a.n >> 2;
   // column pointers formed once: the loop body indexes them with v alone
   const float4* qc[S];
@@ -695,21 +699,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_gram_b2f(MixedArgs a) {
     qc[i] = reinterpret_cast<const float4*>(a.Q + i * ld);
     zc[i] = reinterpret_cast<const float4*>(a.AZ + i * ld);
   }
-  for (int64_t v = gid; v < n4; v += stride) {
-    float4 q[S], z[S];
+  float4 q[S], z[S];
+  int64_t v = gid;
+  if (v < n4) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) q[i] = __ldg(qc[i] + v);
+    for (int i = 0; i < S; ++i) {
+      q[i] = __ldg(qc[i] + v);
+      z[i] = __ldg(zc[i] + v);
+    }
+  }
+  for (; v < n4; v += stride) {
+    float4 qn[S], zn[S];
+    const int64_t vn = v + stride;
+    if (vn < n4) {
 #pragma unroll
-    for (int j = 0; j < S; ++j) z[j] = __ldg(zc[j] + v);
+      for (int i = 0; i < S; ++i) {
+        qn[i] = __ldg(qc[i] + vn);
+        zn[i] = __ldg(zc[i] + vn);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < S; ++i)
 #pragma unroll
-      for (int j = 0; j < S; ++j) {
-        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].x, z[j].x);
-        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].y, z[j].y);
-        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].z, z[j].z);
-        df_acc_prod(hi[i + j * S], lo[i + j * S], q[i].w, z[j].w);
-      }
+      for (int j = 0; j < S; ++j) df_acc_dot4(hi[i + j * S], lo[i + j * S], q[i], z[j]);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      q[i] = qn[i];
+      z[i] = zn[i];
+    }
   }
   for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
     float q[S], z[S];

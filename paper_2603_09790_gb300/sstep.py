@@ -98,6 +98,10 @@ def load():
         "sstep_amg_level": (I, [P, I, P, P, P, P, P, P]),
         "sstep_amg_apply": (I, [P, P, P]),
         "sstep_get_diagnostics": (I, [P, P, P, I, P, P, I, P]),
+        "sstep_q1_exp": (I, [I64, P, P, P]),
+        "sstep_q1_assemble": (I, [I, I, I, P, P, P, P, P]),
+        "sstep_q1_grad": (I, [I, I, I, P, P, P, P, I, I, P]),
+        "sstep_stencil7_weight_grad": (I, [I, I, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -427,6 +431,38 @@ def pattern_grad(rowptr, colind, lam, x, grad_vals, scale=1.0, accumulate=False,
     n = int(rowptr.numel()) - 1
     _check(load().sstep_pattern_grad(n, _ptr(rowptr), _ptr(colind), _ptr(lam), _ptr(x), _ptr(grad_vals),
                                      float(scale), int(bool(accumulate)), _stream_ptr(stream)))
+
+
+def q1_exp(theta, kappa, stream=None):
+    """sstep_q1_exp: kappa = exp(theta) (device tensors of the cell count)."""
+    _check(load().sstep_q1_exp(int(theta.numel()), _ptr(theta), _ptr(kappa), _stream_ptr(stream)))
+
+
+def q1_assemble(dims, kappa, rowptr, colind, vals, stream=None):
+    """sstep_q1_assemble: CSR values of the Q1 operator for cell conductivities kappa on the
+    pattern (rowptr int64, colind int32) of the nx x ny x nz interior vertex grid."""
+    nx, ny, nz = (int(d) for d in dims)
+    _check(load().sstep_q1_assemble(nx, ny, nz, _ptr(kappa), _ptr(rowptr), _ptr(colind), _ptr(vals),
+                                    _stream_ptr(stream)))
+
+
+def q1_grad(dims, kappa, lam, x, grad, wrt_log=True, accumulate=False, stream=None):
+    """sstep_q1_grad: grad[c] (+)= -lambda_c^T K_ref x_c per cell, times kappa_c when wrt_log."""
+    nx, ny, nz = (int(d) for d in dims)
+    _check(load().sstep_q1_grad(nx, ny, nz, _ptr(kappa), _ptr(lam), _ptr(x), _ptr(grad),
+                                int(bool(wrt_log)), int(bool(accumulate)), _stream_ptr(stream)))
+
+
+def stencil7_weight_grad(grids, nrhs, lam, x, grad, stream=None):
+    """sstep_stencil7_weight_grad: grad[2 i] = -sum_r lam_ir^T x_ir, grad[2 i + 1] =
+    -sum_r lam_ir^T N x_ir for systems with grids[i] = (nx, ny, nz) and nrhs right-hand sides
+    each (lam, x: lists of device vectors, system-major; grad: device tensor of 2 nsys)."""
+    nsys = len(grids)
+    dims = np.ascontiguousarray(np.asarray(grids, dtype=np.int32).reshape(-1))
+    L = (C.c_void_p * len(lam))(*[_ptr(v) for v in lam])
+    X = (C.c_void_p * len(x))(*[_ptr(v) for v in x])
+    _check(load().sstep_stencil7_weight_grad(nsys, int(nrhs), dims.ctypes.data, L, X, _ptr(grad),
+                                             _stream_ptr(stream)))
 
 
 def fgs(W, B, nu, X, solver="fgs", status=None, stream=None):

@@ -11,8 +11,8 @@ iterations (rtol = 0), so that the CUDA path can be compared with it at the full
 Calls only the oracle (and the seeded input module).  Slow: about 3 s of one CPU core per
 PCG-S outer iteration, 0.4 s per PCG iteration.  Usage:
     python tests/golden/make_oracle_fixed_256.py [config ...]
-config: "pcg_K<k>" or "<literal|onesync>_s<S>nu<NU>_K<k>" (default: literal_s4nu3_K48
-literal_s4nu30_K131 pcg_K520).
+config: "pcg_K<k>" or "<literal|onesync>_s<S>nu<NU>_K<k>" (default: literal_s4nu3_K32
+literal_s4nu3_K40 literal_s4nu30_K131 pcg_K520).
 """
 import json
 import os
@@ -76,4 +76,4 @@ def main(configs):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["literal_s4nu3_K48", "literal_s4nu30_K131", "pcg_K520"])
+    main(sys.argv[1:] or ["literal_s4nu3_K32", "literal_s4nu3_K40", "literal_s4nu30_K131", "pcg_K520"])
