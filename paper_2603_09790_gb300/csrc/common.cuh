@@ -202,10 +202,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* NV * 32
 // Final step of a "last CTA to arrive" reduction with per-entry partials: for E = T * K entries
 // (T tiles of K values; entry e = tt * K + k), out[e] = sum over b < nblk of
 // partials[(tt * nblk + b) * K + k].  Every thread of the CTA works: thread idx takes entry
-// idx % E and the partials b = idx / E, idx / E + G, ... (G = blockDim / E groups); then one
-// thread per entry adds the G group sums in increasing order.  A fixed order for a given launch
-// shape, so deterministic; with a few entries it keeps many loads in flight instead of a
-// serial chain over the CTAs per entry.  E <= 1024.  Ends with __syncthreads().
+// idx % E and the partials b = idx / E, idx / E + G, ... (G = blockDim / E groups), eight L2
+// loads in flight at a time; then the G group sums of each entry are added: in order by one
+// thread when G <= 32, else by one warp (lane l taking groups l, l + 32, ... in order, then a
+// fixed butterfly over the lanes).  On this part an FP64 warp instruction occupies its
+// sub-partition for tens of cycles however few lanes are active, so a chain of G dependent
+// additions (G = 256 for a single entry) becomes G / 32 + 5.  A fixed order for a given launch
+// shape, so deterministic.  E <= 1024.  Ends with __syncthreads().
 __device__ __forceinline__ void sum_partials(const double* partials, unsigned int nblk, int K,
                                              int T, double* out) {
   constexpr int kScratch = 1024;
@@ -216,14 +219,32 @@ __device__ __forceinline__ void sum_partials(const double* partials, unsigned in
     const int e = idx % E, g = idx / E;
     const double* p = partials + (size_t)(e / K) * nblk * K + (e % K);
     double v = 0.0;
-    for (unsigned int b = g; b < nblk; b += G) v += __ldcg(p + (size_t)b * K);
+    unsigned int b = g;
+    for (; b + 7u * G < nblk; b += 8u * G) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = __ldcg(p + (size_t)(b + u * G) * K);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v += t[u];
+    }
+    for (; b < nblk; b += G) v += __ldcg(p + (size_t)b * K);
     scratch[idx] = v;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    double v = 0.0;
-    for (int g = 0; g < G; ++g) v += scratch[g * E + e];
-    out[e] = v;
+  if (G <= 32) {  // a short chain: one thread per entry adds the group sums in order
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      double v = 0.0;
+      for (int g = 0; g < G; ++g) v += scratch[g * E + e];
+      out[e] = v;
+    }
+  } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = w; e < E; e += nw) {
+      double v = 0.0;
+      for (int g = lane; g < G; g += 32) v += scratch[g * E + e];
+      v = warp_sum(v);
+      if (lane == 0) out[e] = v;
+    }
   }
   __syncthreads();
 }

@@ -459,7 +459,8 @@ __global__ void __launch_bounds__(kThreads) k_gram(GramArgs g, int nch, int rp) 
   if (!last) return;
   __threadfence();
   // Fixed-order sum over CTAs: entry e is summed by threads e, e+ne, ... over CTA slices,
-  // then the slices are added in slice order.
+  // then the slices are added: in slice order by one thread when there are at most 32, else by
+  // one warp per entry (lane l: slices l, l + 32, ... in order, then a fixed butterfly).
   const int per = max(1, (int)blockDim.x / g.ne);  // threads per entry
   double* part = sm;                                // per * ne
   double* sums = sm + per * g.ne;                   // ne
@@ -472,10 +473,20 @@ __global__ void __launch_bounds__(kThreads) k_gram(GramArgs g, int nch, int rp) 
     part[sl * g.ne + e] = v;
   }
   __syncthreads();
-  for (int e = tid; e < g.ne; e += blockDim.x) {
-    double v = 0.0;
-    for (int sl = 0; sl < per; ++sl) v += part[sl * g.ne + e];
-    sums[e] = v;
+  if (per <= 32) {
+    for (int e = tid; e < g.ne; e += blockDim.x) {
+      double v = 0.0;
+      for (int sl = 0; sl < per; ++sl) v += part[sl * g.ne + e];
+      sums[e] = v;
+    }
+  } else {
+    const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    for (int e = w; e < g.ne; e += nw) {
+      double v = 0.0;
+      for (int sl = lane; sl < per; sl += 32) v += part[sl * g.ne + e];
+      v = warp_sum(v);
+      if (lane == 0) sums[e] = v;
+    }
   }
   __syncthreads();
   if (tid == 0) g.ctrl->ticket[TK_GRAM] = 0u;

@@ -428,9 +428,14 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
     return __ldg(e.u + c + (int64_t)zz * pxy);
   };
   float4 ub = ld4(col, z0 - 1, in), uc = ld4(col, z0, in), ua = ld4(col, z0 + 1, in);
+  float4 ua2 = ld4(col, z0 + 2, in);
   float4 hyv = ld4(hycol, z0, hyok);
   float hxv = ld1(hxcol, z0, hxok);
   const float wc = e.wc, a1 = e.c1 * e.dinv_u, c2 = e.c2;
+  // z_{q-1} at this thread's points of the current plane, requested a plane ahead
+  const bool zpv_on = in && e.znext && e.zprev;
+  float4 zp = zpv_on ? __ldg(reinterpret_cast<const float4*>(e.zprev + (int64_t)z0 * pxy + col))
+                     : zero4;
   int set = 0;
   for (int z = z0; z < z1; ++z) {
     float (*P)[kRow4] = sm[set];
@@ -438,10 +443,14 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
     if (hy) *reinterpret_cast<float4*>(&P[ty + 1 + hy][4 + 4 * tx]) = hyv;
     if (hx < 0) P[ty + 1][3] = hxv;
     if (hx > 0) P[ty + 1][4 + 4 * TX4] = hxv;
-    // next plane's values in flight during the barrier and the arithmetic
-    const float4 nz4 = ld4(col, z + 2, in);
+    // values of the planes ahead in flight during the barrier and the arithmetic: u two planes
+    // ahead (z + 3), its halo and z_{q-1} one plane ahead
+    const float4 nz4 = ld4(col, z + 3, in);
     const float4 nhy = ld4(hycol, z + 1, hyok);
     const float nhx = ld1(hxcol, z + 1, hxok);
+    const float4 nzp = (zpv_on && z + 1 < z1)
+                           ? __ldg(reinterpret_cast<const float4*>(e.zprev + (int64_t)(z + 1) * pxy + col))
+                           : zero4;
     __syncthreads();
     if (in) {
       const float4 ym = *reinterpret_cast<const float4*>(&P[ty][4 + 4 * tx]);
@@ -484,8 +493,6 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
       if constexpr (FIRST) *reinterpret_cast<float4*>(e.z1 + i) = make_float4(cv[0], cv[1], cv[2], cv[3]);
       *reinterpret_cast<float4*>(e.y + i) = make_float4(av[0], av[1], av[2], av[3]);
       if (e.znext) {
-        float4 zp = zero4;
-        if (e.zprev) zp = __ldg(reinterpret_cast<const float4*>(e.zprev + i));
         const float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
         float zn[4];
 #pragma unroll
@@ -495,9 +502,11 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
     }
     ub = uc;
     uc = ua;
-    ua = nz4;
+    ua = ua2;
+    ua2 = nz4;
     hyv = nhy;
     hxv = nhx;
+    zp = nzp;
     set ^= 1;
   }
   if constexpr (PAP) pap_finish(e, ph, pl);
