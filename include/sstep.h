@@ -118,7 +118,14 @@ enum {
                              4s^2 + 2s per outer iteration); the default */
   SSTEP_ALGO_PCG = 2      /* classical preconditioned CG (Hestenes-Stiefel), the comparator */
 };
-enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1 };
+/* Reduced solves.  FGS: nu forward Gauss-Seidel sweeps from 0 (Section 3.1, Eq. fgs-iteration).
+ * FGS_OPERATOR: the same nu sweeps applied as one s x s matrix, x = P_nu b with
+ * P_nu = (I + M + ... + M^{nu-1}) (D + L)^{-1}, M = I - (D + L)^{-1} W, formed by repeated
+ * doubling in O(log nu) small products (s <= 5); equal to FGS in exact arithmetic, different
+ * in rounding; formed once per W_k and applied to both systems that share it (alpha_k,
+ * beta_k).  The FP32-basis path uses it whenever FGS is asked for and s <= 5.
+ * CHOLESKY: exact solves (Section 3.3). */
+enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1, SSTEP_GRAM_FGS_OPERATOR = 2 };
 
 typedef struct {
   int s;              /* step size, 1 <= s <= 16 (Algorithm 1 "step size s") */
@@ -126,7 +133,7 @@ typedef struct {
   double rtol;        /* tau: stop when ||r|| <= tau ||b|| (Algorithm 1's stop test) */
   int max_outer;      /* k_max (outer iterations; PCG: iterations) */
   int algo;           /* SSTEP_ALGO_* */
-  int gram_solver;    /* SSTEP_GRAM_FGS, or SSTEP_GRAM_CHOLESKY (exact reduced solves, Section 3.3) */
+  int gram_solver;    /* SSTEP_GRAM_FGS (default), SSTEP_GRAM_FGS_OPERATOR or SSTEP_GRAM_CHOLESKY */
   int power_iters;    /* power-method cap (Section 2: 50) */
   double power_tol;   /* power-method relative-change stop (Section 2: 1e-3); <= 0 runs power_iters */
   double lambda_min;  /* lower end of the Chebyshev interval (Section 2 uses 0); < 0 = Gershgorin bound */
@@ -230,9 +237,10 @@ SSTEP_API sstep_status sstep_amg_apply(sstep_handle h, const double* b, double* 
  * iteration k < *count, eta_a[k] = ||Q_k^T r^(k) - W_k alpha_k||_2 / ||Q_k^T r^(k)||_2 and, for
  * k < *count - 1, eta_b[k] = ||-Q_k^T AZ_{k+1} - W_k beta_k||_F / ||Q_k^T AZ_{k+1}||_F; W receives
  * W_k (s x s column-major, one after another) for k < *countw <= min(maxw, 64).  HOST arrays
- * of maxlen (eta_a, eta_b) and maxw * s * s (W) doubles; any output may be NULL.  Recorded on
- * the device by the reduced-solve step at no extra pass over the vectors.  *count = 0 for
- * classical PCG. */
+ * of maxlen (eta_a, eta_b) and maxw * s * s (W) doubles; any output may be NULL.  The device
+ * keeps each outer iteration's reduced systems (W_k, Q_k^T r, alpha_k, -Q_k^T AZ_{k+1}, beta_k:
+ * plain stores in the reduced-solve step, no arithmetic on the solve's path); this call forms
+ * the eta values from them in FP64 on the host.  *count = 0 for classical PCG. */
 SSTEP_API sstep_status sstep_get_diagnostics(sstep_handle h, double* eta_a, double* eta_b,
                                              int maxlen, int* count, double* W, int maxw,
                                              int* countw);
@@ -288,7 +296,9 @@ SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, const double*
  * W itself: W = D + L_W + L_W^T).  W: s x s column-major, B and X: s x nrhs column-major, all
  * device pointers; 1 <= s <= 16, 1 <= nrhs <= 16.  Breakdown (W_ii <= 0 or non-finite) is
  * written to *status_dev (device int, may be NULL) as SSTEP_ERR_BREAKDOWN, else SSTEP_OK.
- * solver = SSTEP_GRAM_CHOLESKY solves exactly instead.  stream: cudaStream_t as void*. */
+ * solver = SSTEP_GRAM_CHOLESKY solves exactly instead; SSTEP_GRAM_FGS_OPERATOR (s <= 5,
+ * else SSTEP_ERR_UNSUPPORTED) forms P_nu and returns X = P_nu B, the products in increasing
+ * order of the summed index.  stream: cudaStream_t as void*. */
 SSTEP_API sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu, int solver,
                        double* X, int* status_dev, void* stream);
 

@@ -79,7 +79,7 @@ struct sstep_ctx {
   double *x = nullptr, *r = nullptr, *b = nullptr, *p = nullptr, *Ap = nullptr;
   double* partials = nullptr;
   double* hist = nullptr;
-  double *eta_a = nullptr, *eta_b = nullptr, *whist = nullptr;  // reduced-solve diagnostics
+  double* red = nullptr;  // the reduced systems of every outer iteration (diagnostics)
   Ctrl* ctrl = nullptr;
   Ctrl* hctrl = nullptr;  // pinned host mirror
   // basis info
@@ -501,13 +501,16 @@ sstep_status reset_ctrl(sstep_ctx* h) {
   c->s = h->s;
   c->nu = h->o.sweeps;
   c->solver = h->o.gram_solver;
+  // the FP32-basis path applies the FGS sweeps in operator form where it can (s <= 5): one
+  // P_nu(W_k) serves alpha_k and beta_k, and the chain of the reduced solve is O(log nu)
+  if (h->o.precision == SSTEP_PRECISION_FP32_RR && c->solver == SSTEP_GRAM_FGS && h->s <= 5)
+    c->solver = SSTEP_GRAM_FGS_OPERATOR;
   c->full_gram = full_blocks(h);
   c->power_tol = h->o.power_tol;
   c->power_max = h->o.power_iters;
-  c->eta_a = h->eta_a;
-  c->eta_b = h->eta_b;
-  c->whist = h->whist;
-  c->whist_max = h->whist ? kDiagW : 0;
+  c->red = h->red;
+  c->red_max = h->o.max_outer + 1;
+  c->red_stride = red_stride_for(h->s);
   CK(cudaMemcpyAsync(h->ctrl, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->st));
   return SSTEP_OK;
 }
@@ -611,7 +614,9 @@ sstep_status validate_opts(const sstep_opts* o) {
   if (!(o->rtol >= 0.0)) return fail(SSTEP_ERR_INVALID, "rtol must be >= 0");
   if (o->max_outer < 0) return fail(SSTEP_ERR_INVALID, "max_outer must be >= 0");
   if (o->algo < 0 || o->algo > 2) return fail(SSTEP_ERR_INVALID, "unknown algo");
-  if (o->gram_solver < 0 || o->gram_solver > 1) return fail(SSTEP_ERR_INVALID, "unknown gram_solver");
+  if (o->gram_solver < 0 || o->gram_solver > 2) return fail(SSTEP_ERR_INVALID, "unknown gram_solver");
+  if (o->gram_solver == SSTEP_GRAM_FGS_OPERATOR && o->s > 5)
+    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 5");
   if (o->power_iters < 1 && !(o->lambda_max > 0.0))
     return fail(SSTEP_ERR_INVALID, "power_iters must be >= 1 when lambda_max is not given");
   if (o->precision != SSTEP_PRECISION_FP64 && o->precision != SSTEP_PRECISION_FP32_RR)
@@ -621,7 +626,7 @@ sstep_status validate_opts(const sstep_opts* o) {
       return fail(SSTEP_ERR_UNSUPPORTED,
                   "the FP32-basis path implements the literal form and classical PCG");
     if (o->s > 8) return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path supports s <= 8");
-    if (o->gram_solver != SSTEP_GRAM_FGS)
+    if (o->gram_solver == SSTEP_GRAM_CHOLESKY)
       return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path uses FGS reduced solves");
   }
   return SSTEP_OK;
@@ -641,8 +646,8 @@ void destroy(sstep_ctx* h) {
   for (void* p : fbufs)
     if (p) cudaFree(p);
   void* bufs[] = {h->rowptr, h->colind, h->vals, h->dinv, h->Z, h->AZ, h->Q, h->AQ, h->x, h->r,
-                  h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl, h->eta_a, h->eta_b,
-                  h->whist, h->kappa};
+                  h->b, h->p, h->Ap, h->partials, h->hist, h->ctrl, h->red,
+                  h->kappa};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -806,9 +811,7 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
        (int64_t)4096});
   CKS(alloc(&h->partials, part));
   CKS(alloc(&h->hist, (int64_t)h->o.max_outer + 2));
-  CKS(alloc(&h->eta_a, (int64_t)h->o.max_outer + 2));
-  CKS(alloc(&h->eta_b, (int64_t)h->o.max_outer + 2));
-  CKS(alloc(&h->whist, (int64_t)kDiagW * s * s));
+  CKS(alloc(&h->red, ((int64_t)h->o.max_outer + 2) * red_stride_for(s)));
   CK(cudaMalloc(&h->ctrl, sizeof(Ctrl)));
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
   CK(cudaMallocHost(&h->hctrl, sizeof(Ctrl)));
@@ -1200,12 +1203,33 @@ sstep_status sstep_get_diagnostics(sstep_handle h, double* eta_a, double* eta_b,
   CK(cudaStreamSynchronize(h->st));
   const int iters = h->o.algo == SSTEP_ALGO_PCG ? 0 : h->hctrl->iters;
   const int na = std::max(0, std::min(maxlen, iters));
-  if (na > 0 && eta_a) CK(cudaMemcpy(eta_a, h->eta_a, sizeof(double) * na, cudaMemcpyDeviceToHost));
-  if (na > 1 && eta_b) CK(cudaMemcpy(eta_b, h->eta_b, sizeof(double) * (na - 1), cudaMemcpyDeviceToHost));
-  if (count) *count = na;
   const int nw = std::max(0, std::min({maxw, iters, kDiagW}));
-  if (nw > 0 && W)
-    CK(cudaMemcpy(W, h->whist, sizeof(double) * (size_t)nw * h->s * h->s, cudaMemcpyDeviceToHost));
+  const int s = h->s, st = red_stride_for(s);
+  const int nrec = std::max(na, nw);
+  std::vector<double> rec((size_t)nrec * st);
+  if (nrec > 0)
+    CK(cudaMemcpy(rec.data(), h->red, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
+  // eta = ||B - W X||_F / ||B||_F of the kept systems (Section 3.3), in FP64 on the host
+  auto eta = [s](const double* Wk, const double* B, const double* X, int nrhs) {
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < nrhs; ++c)
+      for (int i = 0; i < s; ++i) {
+        double v = B[i + c * s];
+        for (int j = 0; j < s; ++j) v -= Wk[i + j * s] * X[j + c * s];
+        num += v * v;
+        den += B[i + c * s] * B[i + c * s];
+      }
+    return den > 0.0 ? std::sqrt(num / den) : 0.0;
+  };
+  for (int k = 0; k < na; ++k) {
+    const double* r = rec.data() + (size_t)k * st;
+    if (eta_a) eta_a[k] = eta(r, r + s * s, r + s * s + s, 1);
+    if (eta_b && k + 1 < na) eta_b[k] = eta(r, r + s * s + 2 * s, r + 2 * s * s + 2 * s, s);
+  }
+  if (count) *count = na;
+  if (W)
+    for (int k = 0; k < nw; ++k)
+      std::memcpy(W + (size_t)k * s * s, rec.data() + (size_t)k * st, sizeof(double) * s * s);
   if (countw) *countw = nw;
   return SSTEP_OK;
 }
@@ -1296,8 +1320,11 @@ sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu
                        double* X, int* status_dev, void* stream) {
   g_err.clear();
   if (s < 1 || s > kMaxS || nrhs < 1 || nrhs > kMaxS || nu < 0 || !W || !B || !X ||
-      (solver != SSTEP_GRAM_FGS && solver != SSTEP_GRAM_CHOLESKY))
+      (solver != SSTEP_GRAM_FGS && solver != SSTEP_GRAM_CHOLESKY &&
+       solver != SSTEP_GRAM_FGS_OPERATOR))
     return fail(SSTEP_ERR_INVALID, "bad fgs arguments");
+  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > 5)
+    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 5");
   CK(launch_fgs_standalone(s, W, nrhs, B, nu, solver, X, status_dev, (cudaStream_t)stream));
   return SSTEP_OK;
 }

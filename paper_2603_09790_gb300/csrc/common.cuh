@@ -60,17 +60,19 @@ struct Ctrl {
   double alpha[kMaxS];
   double beta[kMaxS * kMaxS];    // column-major s x s
   double W[kMaxS * kMaxS];       // W_k used for alpha_k (and for beta_k)
+  double P[32];                  // FGS operator P_nu(W_k) (solver SSTEP_GRAM_FGS_OPERATOR, s <= 5)
+  int p_valid;                   // 1 once P holds the operator of the current W
   double sums[kMaxEntries];      // reduced Gram sums of the last reduction
   unsigned int ticket[kNumTickets];
-  // diagnostics of the reduced solves (Section 3.3 experiments), written by the Gram tails:
-  // eta_a[k] = ||b1 - W_k alpha_k|| / ||b1||, eta_b[k] = ||B2 - W_k beta_k||_F / ||B2||_F,
-  // whist[k] = W_k for k < whist_max (s x s column-major each)
-  double* eta_a;
-  double* eta_b;
-  double* whist;
-  int whist_max;
+  // the reduced systems of every outer iteration k <= red_max (Section 3.3 experiments), kept
+  // by the Gram tails for the host to form eta_alpha and eta_beta: record k (red_stride
+  // doubles at red + k red_stride) holds W_k (s x s), b1_k (s), alpha_k (s), B2_k = -Q_k^T
+  // AZ_{k+1} (s x s) and beta_k (s x s), each column-major; plain stores, no arithmetic.
+  double* red;
+  int red_max, red_stride;
 };
-constexpr int kDiagW = 64;  // outer iterations whose W_k is kept
+constexpr int kDiagW = 64;  // outer iterations whose W_k the diagnostics return
+__host__ __device__ constexpr int red_stride_for(int s) { return 3 * s * s + 2 * s; }
 
 // ---------------------------------------------------------------- operator descriptors
 
@@ -291,44 +293,125 @@ __device__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* t
   return true;
 }
 
+// Warp stage of df_grid_sums for K <= 32 values per lane, a reduce-scatter: with KP the next
+// power of two >= K (missing values 0) and L = log2 KP, level t < L pairs lanes at distance
+// 16 >> t; the lane whose bit (4 - t) is set keeps the upper half of its current values and
+// sends the lower half, its partner the reverse, and each adds what it receives.  After the L
+// levels a lane holds the sum of value index lane >> (5 - L) over the 2^L lanes that share its
+// other bits; plain butterfly levels over the remaining 5 - L lane bits finish the warp sum.
+// KP - 1 + 5 - L double-float additions per lane instead of 5 K.
+template <int K>
+__device__ __forceinline__ void df_warp_scatter(const float (&hi)[K], const float (&lo)[K],
+                                                float& vh, float& vl) {
+  constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  constexpr int L = KP == 1 ? 0 : KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : KP == 16 ? 4 : 5;
+  const int lane = threadIdx.x & 31;
+  float h[KP], l[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    h[k] = k < K ? hi[k] : 0.0f;
+    l[k] = k < K ? lo[k] : 0.0f;
+  }
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const int half = KP >> (t + 1), o = 16 >> t;
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float sh = upper ? h[k] : h[k + half], sl = upper ? l[k] : l[k + half];
+      const float kh = upper ? h[k + half] : h[k], kl = upper ? l[k + half] : l[k];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      h[k] = kh;
+      l[k] = kl;
+      df_add(h[k], l[k], rh, rl);
+    }
+  }
+  float a = h[0], b = l[0];
+#pragma unroll
+  for (int o = 16 >> L; o > 0; o >>= 1) {
+    const float rh = __shfl_xor_sync(0xffffffffu, a, o), rl = __shfl_xor_sync(0xffffffffu, b, o);
+    df_add(a, b, rh, rl);
+  }
+  vh = a;
+  vl = b;
+}
+
+// Last step of df_grid_sums: out[e] = sum over b < nblk of partials[b * K + e] (K <= 32).
+// G = the largest power of two with G K <= blockDim groups; thread g K + e loads the partials
+// b = g, g + G, ..., up to 24 at a time (one round trip to L2 for up to 24 G CTAs) and adds them
+// by a pairwise tree; the G group sums of an entry are then added by a tree over g in shared
+// memory.  A fixed order for a given launch shape.  Ends with __syncthreads().
+__device__ __forceinline__ void sum_partials_df(const double* partials, unsigned int nblk, int K,
+                                                double* out) {
+  __shared__ double scr[kThreads];
+  int G = 1;
+  while (2 * G * K <= (int)blockDim.x && 2 * G * K <= kThreads) G *= 2;
+  const int idx = threadIdx.x;
+  if (idx < G * K) {
+    const int e = idx % K, g = idx / K;
+    double v = 0.0;
+    for (unsigned int b0 = g; b0 < nblk; b0 += 24u * G) {
+      double t[24];
+#pragma unroll
+      for (int u = 0; u < 24; ++u) {
+        const unsigned int b = b0 + u * G;
+        t[u] = b < nblk ? __ldcg(partials + (size_t)b * K + e) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 12; ++u) t[u] += t[u + 12];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) t[u] += t[u + 6];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) t[u] += t[u + 3];
+      v += (t[0] + t[1]) + t[2];
+    }
+    scr[idx] = v;
+  }
+  __syncthreads();
+  for (int h = G / 2; h >= 1; h /= 2) {
+    if (idx < h * K) scr[idx] += scr[idx + h * K];
+    __syncthreads();
+  }
+  if (idx < K) out[idx] = scr[idx];
+  __syncthreads();
+}
+
 // Per-thread double-float (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the
-// last CTA (no CTA waits for another).  Grids may be 1D, 2D or 3D.  buf: shared memory of at
-// least (blockDim.x / 32) * K doubles.  Returns true in the last CTA, with the K sums in
-// buf[0..K) (valid in all of its threads).
+// last CTA (no CTA waits for another).  Grids may be 1D, 2D or 3D; K <= 32, blockDim a multiple
+// of 32 up to kThreads.  buf: shared memory of at least (blockDim.x / 32) * K doubles.  Returns
+// true in the last CTA, with the K sums in buf[0..K) (valid in all of its threads).
 template <int K>
 __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
                              double* partials, unsigned int* ticket) {
+  static_assert(K >= 1 && K <= 32, "K <= 32 values per thread");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
-  // warp stage in double-float on the FP32 pipe (every lane ends with the warp's sums); lane k
-  // then keeps value k, so that each warp converts its K values to FP64 with one instruction
-  // sequence per 32 values: an FP64 instruction costs a sub-partition tens of cycles however
-  // few of its lanes are active
-  float kh = 0.0f, kl = 0.0f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float h = hi[k], l = lo[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, h, o);
-      const float ol = __shfl_xor_sync(0xffffffffu, l, o);
-      df_add(h, l, oh, ol);
-    }
-    if ((k & 31) == lane) {
-      kh = h;
-      kl = l;
-    }
-    if ((k & 31) == 31 || k == K - 1) {
-      const int k0 = k & ~31;
-      if (lane <= k - k0) buf[wid * K + k0 + lane] = (double)kh + (double)kl;
-    }
+  // the warp stage on the FP32 pipe; each lane then holds the warp sum of one value, so that a
+  // warp converts its K values to FP64 in one instruction sequence (an FP64 instruction costs a
+  // sub-partition tens of cycles however few of its lanes are active)
+  float vh, vl;
+  df_warp_scatter<K>(hi, lo, vh, vl);
+  {
+    constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    constexpr int R = 32 / KP;  // lanes per value
+    const int v = lane / R;
+    if (lane % R == 0 && v < K) buf[wid * K + v] = (double)vh + (double)vl;
   }
   __syncthreads();
+  // the warps' sums of a value in four interleaved chains
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v += buf[w * K + k];
-    partials[(size_t)bid * K + k] = v;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int w = 0;
+    for (; w + 3 < nw; w += 4) {
+      a0 += buf[w * K + k];
+      a1 += buf[(w + 1) * K + k];
+      a2 += buf[(w + 2) * K + k];
+      a3 += buf[(w + 3) * K + k];
+    }
+    for (; w < nw; ++w) a0 += buf[w * K + k];
+    partials[(size_t)bid * K + k] = (a0 + a1) + (a2 + a3);
   }
   __shared__ bool last;
   __syncthreads();
@@ -339,7 +422,7 @@ __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double*
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  sum_partials(partials, nblk, K, 1, buf);
+  sum_partials_df(partials, nblk, K, buf);
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }

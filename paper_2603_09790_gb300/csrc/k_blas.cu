@@ -131,6 +131,113 @@ __device__ void fgs_warp_dispatch(int s, const double* W, const double* rinv, co
   }
 }
 
+// ---- the FGS operator (solver SSTEP_GRAM_FGS_OPERATOR)
+//
+// nu sweeps from x = 0 are linear in the right-hand side: with W = D + L + U (diagonal, strictly
+// lower, strictly upper), one sweep is x <- T (b - U x), T = (D + L)^{-1}, so
+//   x_nu = P_nu b,   P_nu = (I + M + ... + M^{nu-1}) T,   M = -T U = I - T W.
+// For s^2 <= 32 one warp holds an s x s matrix one entry per lane (lane i + j s: entry (i, j),
+// the column-major index), and P_nu is formed from the binary digits of nu by doubling,
+// S_{2m} = S_m + M^m S_m, M^{2m} = M^m M^m, and stepping, S_{m+1} = I + M S_m,
+// M^{m+1} = M^m M (S_m = I + ... + M^{m-1}): about 2 log2(nu) + 3 products, each a chain of s
+// FP64 multiply-adds, where nu sequential sweeps chain about 3 s dependent operations each.
+
+// (A B)_ij for the s x s matrices held one entry per lane (a = A_ij, b = B_ij in lane i + j s);
+// the s products are summed in increasing k by a chain of multiply-adds from 0.
+template <int S>
+__device__ __forceinline__ double lane_mm(double a, double b, int i, int j) {
+  double ak[S], bk[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    ak[k] = __shfl_sync(0xffffffffu, a, i + k * S);
+    bk[k] = __shfl_sync(0xffffffffu, b, k + j * S);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) acc = fma(ak[k], bk[k], acc);
+  return acc;
+}
+
+// P = P_nu(W) into P (s x s column-major, shared memory); rinv[i] = 1 / W_ii.  Executed by all
+// 32 lanes of one warp.
+template <int S>
+__device__ void fgs_operator_s(const double* W, const double* rinv, int nu, double* P) {
+  static_assert(S * S <= 32, "one entry per lane");
+  const int lane = threadIdx.x & 31;
+  const bool in = lane < S * S;
+  const int i = in ? lane % S : 0, j = in ? lane / S : 0;
+  const double eye = (in && i == j) ? 1.0 : 0.0;
+  // T = (D + L)^{-1}, column j by forward substitution: row r is final after step r
+  double wl[S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) wl[r] = W[i + r * S];
+  const double ri = rinv[i];
+  double t = 0.0, acc = eye;
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    if (i == r) t = acc * ri;
+    const double tr = __shfl_sync(0xffffffffu, t, r + j * S);
+    if (i > r) acc = fma(-wl[r], tr, acc);
+  }
+  if (nu <= 0) {
+    if (in) P[lane] = 0.0;
+    return;
+  }
+  const double m1 = eye - lane_mm<S>(t, in ? W[lane] : 0.0, i, j);  // M = I - T W
+  double sum = eye, pw = m1;                                        // S_1 = I, M^1
+  for (int bit = 30 - __clz(nu); bit >= 0; --bit) {
+    const double ps = lane_mm<S>(pw, sum, i, j);
+    const double pp = lane_mm<S>(pw, pw, i, j);
+    sum += ps;
+    pw = pp;
+    if ((nu >> bit) & 1) {
+      const double ms = lane_mm<S>(m1, sum, i, j);
+      const double pm = lane_mm<S>(pw, m1, i, j);
+      sum = eye + ms;
+      pw = pm;
+    }
+  }
+  const double p = lane_mm<S>(sum, t, i, j);
+  if (in) P[lane] = p;
+}
+
+// Returns false when s is too large for the one-warp layout.
+__device__ bool fgs_operator(int s, const double* W, const double* rinv, int nu, double* P) {
+  switch (s) {
+    case 1: fgs_operator_s<1>(W, rinv, nu, P); return true;
+    case 2: fgs_operator_s<2>(W, rinv, nu, P); return true;
+    case 3: fgs_operator_s<3>(W, rinv, nu, P); return true;
+    case 4: fgs_operator_s<4>(W, rinv, nu, P); return true;
+    case 5: fgs_operator_s<5>(W, rinv, nu, P); return true;
+    default: return false;
+  }
+}
+
+// X = P B (P: s x s, B and X: s x nrhs, column-major), one entry per thread, the products
+// summed in increasing k by a chain of multiply-adds from 0 (the order of lane_mm).
+__device__ __forceinline__ void apply_operator(int s, const double* P, const double* B, int nrhs,
+                                               double* X) {
+  for (int e = threadIdx.x; e < s * nrhs; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    double acc = 0.0;
+    for (int k = 0; k < s; ++k) acc = fma(P[i + k * s], B[k + j * s], acc);
+    X[e] = acc;
+  }
+}
+
+// Bit tests equivalent to the floating-point checks of the reduced solve, on the integer pipe:
+// finite_ok(w) <=> !(w != w) && |w| <= 1.79e308;  diag_ok(d) <=> d > 0 && d <= 1.79e308.
+// (Non-negative doubles order like their bit patterns; NaN patterns lie above infinity's.)
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v));
+}
+__device__ __forceinline__ bool finite_ok(double w) {
+  return (dbits(w) & 0x7FFFFFFFFFFFFFFFull) <= dbits(1.79e308);
+}
+__device__ __forceinline__ bool diag_ok(double d) {
+  return dbits(d) != 0ull && dbits(d) <= dbits(1.79e308);  // sign clear, not +0, not too large
+}
+
 // Dense Cholesky factorisation in place (lower triangle of L, column-major), one thread.
 __device__ bool chol_factor(int s, const double* W, double* L) {
   for (int j = 0; j < s; ++j) {
@@ -171,10 +278,15 @@ __device__ void chol_column(int s, const double* L, const double* b, double* x, 
 // instruction sequence (lane i: row i); the FGS sweeps run one warp per right-hand side
 // (fgs_warp: lane i owns row i, successive right-hand sides on successive warps, which the SM
 // schedules on different sub-partitions).
+//
+// solver SSTEP_GRAM_FGS_OPERATOR (s <= 5; larger s take the sweeps): warp 0 forms P_nu(W) into
+// scratch[0 .. s*s) (fgs_operator) and X = P_nu B; the caller may keep P for a later system
+// with the same W.
 __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs, int nu,
                               int solver, double* X, double* scratch /* s*s + s */) {
   __shared__ int ok;
   const int tid = threadIdx.x;
+  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > 5) solver = SSTEP_GRAM_FGS;
   if (solver == SSTEP_GRAM_CHOLESKY) {
     if (tid == 0) {
       ok = 1;
@@ -187,12 +299,13 @@ __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs,
       if (ok && !chol_factor(s, W, scratch)) ok = 0;
     }
   } else if (tid < 32) {
+    // the same predicates as the Cholesky branch's, on the integer pipe
     bool good = true;
     for (int e = tid; e < s * s; e += 32)
-      if (!(W[e] == W[e]) || fabs(W[e]) > 1.79e308) good = false;
+      if (!finite_ok(W[e])) good = false;
     if (tid < s) {
       const double d = W[tid + tid * s];
-      if (!(d > 0.0) || d > 1.79e308) good = false;
+      if (!diag_ok(d)) good = false;
       else scratch[s * s + tid] = 1.0 / d;
     }
     good = __all_sync(0xffffffffu, good);
@@ -200,7 +313,11 @@ __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs,
   }
   __syncthreads();
   if (!ok) return false;
-  if (solver != SSTEP_GRAM_CHOLESKY) {
+  if (solver == SSTEP_GRAM_FGS_OPERATOR) {
+    if (tid < 32) fgs_operator(s, W, scratch + s * s, nu, scratch);
+    __syncthreads();
+    apply_operator(s, scratch, B, nrhs, X);
+  } else if (solver != SSTEP_GRAM_CHOLESKY) {
     fgs_warp_dispatch(s, W, scratch + s * s, B, nrhs, nu, X);
   } else if (tid < nrhs) {
     chol_column(s, scratch, B + tid * s, X + tid * s, 1);
@@ -238,60 +355,68 @@ struct OneSyncIdx {
   __host__ __device__ int count() const { return g6(L.s); }
 };
 
-// Relative residual of a reduced solve, ||B - W X|| / ||B|| (Frobenius over nrhs columns),
-// one thread (Section 3.3: eta_alpha, eta_beta).
-__device__ double reduced_relres(int s, const double* W, const double* B, const double* X, int nrhs) {
-  double num = 0.0, den = 0.0;
-  for (int c = 0; c < nrhs; ++c)
-    for (int i = 0; i < s; ++i) {
-      double v = B[i + c * s];
-      for (int j = 0; j < s; ++j) v = fma(-W[i + j * s], X[j + c * s], v);
-      num = fma(v, v, num);
-      den = fma(B[i + c * s], B[i + c * s], den);
-    }
-  return den > 0.0 ? sqrt(num / den) : 0.0;
-}
-
-// Records eta_alpha for alpha_k (k = updates so far) and W_k.
+// Keeps W_k, b1_k and alpha_k of outer iteration k = updates so far (executed by the whole CTA;
+// plain stores).
 __device__ void record_alpha(Ctrl* c, int s, const double* W, const double* b1, const double* a) {
   const int k = c->iters;
-  if (c->eta_a && k <= c->max_iters) c->eta_a[k] = reduced_relres(s, W, b1, a, 1);
-  if (c->whist && k < c->whist_max)
-    for (int e = 0; e < s * s; ++e) c->whist[(size_t)k * s * s + e] = W[e];
+  if (!c->red || k > c->red_max) return;
+  double* r = c->red + (size_t)k * c->red_stride;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) r[e] = W[e];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    r[s * s + i] = b1[i];
+    r[s * s + s + i] = a[i];
+  }
 }
 
-// Records eta_beta for beta_k, computed after update k + 1.  Called by the whole CTA: thread c
-// forms column c's sums, thread 0 adds the columns in order.
-__device__ void record_beta(Ctrl* c, int s, const double* W, const double* B, const double* X) {
-  __shared__ double part[2 * kMaxS];
+// Keeps B2_k and beta_k, formed after update k + 1 (executed by the whole CTA; plain stores).
+__device__ void record_beta(Ctrl* c, int s, const double* B, const double* X) {
   const int k = c->iters - 1;
-  const bool rec = c->eta_b && k >= 0 && k <= c->max_iters;
-  const int col = threadIdx.x;
-  if (rec && col < s) {
-    double num = 0.0, den = 0.0;
-    for (int i = 0; i < s; ++i) {
-      double v = B[i + col * s];
-      for (int j = 0; j < s; ++j) v = fma(-W[i + j * s], X[j + col * s], v);
-      num = fma(v, v, num);
-      den = fma(B[i + col * s], B[i + col * s], den);
-    }
-    part[col] = num;
-    part[kMaxS + col] = den;
+  if (!c->red || k < 0 || k > c->red_max) return;
+  double* r = c->red + (size_t)k * c->red_stride + s * s + 2 * s;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    r[e] = B[e];
+    r[s * s + e] = X[e];
   }
-  __syncthreads();
-  if (rec && threadIdx.x == 0) {
-    double num = 0.0, den = 0.0;
-    for (int j = 0; j < s; ++j) {
-      num += part[j];
-      den += part[kMaxS + j];
-    }
-    c->eta_b[k] = den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+// Operator form: keeps P_nu(W) (left in scr[0 .. s*s) by reduced_solve) for the next system
+// with the same W.
+__device__ __forceinline__ void keep_operator(Ctrl* c, int s, const double* scr) {
+  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || s > 5) return;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) c->P[e] = scr[e];
+  if (threadIdx.x == 0) c->p_valid = 1;
+}
+
+// Operator form: whether a kept P_nu(W) can serve the next system with the same W.
+__device__ __forceinline__ bool can_reuse_operator(const Ctrl* c, int s) {
+  return c->solver == SSTEP_GRAM_FGS_OPERATOR && s <= 5 && c->p_valid;
+}
+
+// X = P B with the kept P for the s right-hand sides of the conjugation system (no new checks:
+// W passed them when P was formed).  pre: a copy of c->P the kernel loaded into shared memory
+// at its start, or null.  Executed by the whole CTA.
+__device__ __forceinline__ void reuse_operator(const Ctrl* c, int s, const double* B, double* X,
+                                               double* scr, const double* pre) {
+  if (!pre) {
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) scr[e] = c->P[e];
+    __syncthreads();
+    pre = scr;
   }
+  apply_operator(s, pre, B, s, X);
   __syncthreads();
+}
+
+// Loads c->P into shared memory (all CTAs of a conjugation-system kernel, at its start: the
+// last CTA then finds it there).  Executed by the whole CTA; the caller synchronises.
+__device__ __forceinline__ void preload_operator(const Ctrl* c, double* pre) {
+  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || c->s > 5 || !c->p_valid) return;
+  for (int e = threadIdx.x; e < c->s * c->s; e += blockDim.x) pre[e] = c->P[e];
 }
 
 // The tail: executed by the last CTA after the reduction, with the sums in shared memory.
-__device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
+// pre: c->P loaded into shared memory by the kernel (GM_LITERAL_B2 with a kept operator), or null.
+__device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh,
+                          const double* pre = nullptr) {
   const int s = c->s, nu = c->nu, solver = c->solver;
   const Layout L{s, c->full_gram};
   double* W = sh;               // s*s
@@ -317,19 +442,22 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
     if (ok) {
       for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = X[i];
       for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
-      if (tid == 0) record_alpha(c, s, W, b1, X);
+      keep_operator(c, s, scr);
+      record_alpha(c, s, W, b1, X);
     }
   } else if (mode == GM_LITERAL_B2) {
     // b2 = -Q^T AQ_new; beta = FGS(W, b2)                                    (conjugation)
+    const bool reuse = can_reuse_operator(c, s);
     for (int e = tid; e < s * s; e += blockDim.x) {
-      W[e] = c->W[e];
+      if (!reuse) W[e] = c->W[e];
       Bm[e] = -sums[e];  // entry e = i + j*s is q_i^T az_j
     }
     __syncthreads();
-    ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
+    if (reuse) reuse_operator(c, s, Bm, X, scr, pre);
+    else ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
     if (ok) {
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
-      record_beta(c, s, W, Bm, X);
+      record_beta(c, s, Bm, X);
     }
   } else if (mode == GM_ONESYNC) {
     const OneSyncIdx I{L};
@@ -343,10 +471,12 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
     }
     __syncthreads();
     // beta_k = FGS(W_k, -Q_k^T AZ_{k+1})                                   (conjugation)
-    ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
+    if (can_reuse_operator(c, s)) reuse_operator(c, s, Bm, X, scr, nullptr);
+    else ok = reduced_solve(s, W, Bm, s, nu, solver, X, scr);
     if (ok) {
       for (int e = tid; e < s * s; e += blockDim.x) c->beta[e] = X[e];
-      record_beta(c, s, W, Bm, X);
+      record_beta(c, s, Bm, X);
+      __syncthreads();
       // T = G1 beta
       for (int e = tid; e < s * s; e += blockDim.x) {
         const int i = e % s, j = e / s;
@@ -380,7 +510,8 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh) {
       if (ok) {
         for (int i = tid; i < s; i += blockDim.x) c->alpha[i] = T[i];
         for (int e = tid; e < s * s; e += blockDim.x) c->W[e] = W[e];
-        if (tid == 0) record_alpha(c, s, W, b1, T);
+        keep_operator(c, s, scr);
+        record_alpha(c, s, W, b1, T);
       }
     }
   }
@@ -695,6 +826,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_b2f(MixedArgs a) {
   if (a.ctrl->done) return;
   constexpr int K = S * S;
   __shared__ double buf[kTiledSmem];
+  __shared__ double pre[S * S];  // the kept FGS operator, for the last CTA's tail
+  preload_operator(a.ctrl, pre);  // (visible to the tail after the reduction's barriers)
   float hi[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
@@ -752,7 +885,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_b2f(MixedArgs a) {
   }
   if (!df_grid_sums<K>(hi, lo, buf, a.partials, &a.ctrl->ticket[TK_GRAM])) return;
   for (int e = threadIdx.x; e < K; e += blockDim.x) a.ctrl->sums[e] = buf[e];
-  gram_tail(GM_LITERAL_B2, a.ctrl, buf, buf + K);
+  gram_tail(GM_LITERAL_B2, a.ctrl, buf, buf + K, pre);
 }
 
 // Direction-block update in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libsstep.so")
 MATRIX_CSR, MATRIX_STENCIL, MATRIX_Q1 = 0, 1, 2
 PREC = {"none": 0, "jacobi": 1, "amg": 2}
 ALGO = {"onesync": 0, "literal": 1, "pcg": 2}
-GRAM = {"fgs": 0, "cholesky": 1}
+GRAM = {"fgs": 0, "cholesky": 1, "fgs_operator": 2}
 
 
 class SstepError(RuntimeError):

@@ -26,14 +26,16 @@ def run(A, b, **kw):
     return info, d, bi
 
 
-@pytest.mark.parametrize("dims,points,algo,s,nu,K", [
-    ((24, 22, 20), 27, "literal", 4, 30, 10), ((24, 22, 20), 27, "onesync", 6, 30, 6),
-    ((30, 26, 22), 7, "literal", 8, 60, 4), ((30, 26, 22), 7, "literal", 10, 30, 3)])
-def test_eta_matches_oracle(dims, points, algo, s, nu, K):
+@pytest.mark.parametrize("dims,points,algo,s,nu,K,gram", [
+    ((24, 22, 20), 27, "literal", 4, 30, 10, "fgs"), ((24, 22, 20), 27, "onesync", 6, 30, 6, "fgs"),
+    ((30, 26, 22), 7, "literal", 8, 60, 4, "fgs"), ((30, 26, 22), 7, "literal", 10, 30, 3, "fgs"),
+    ((24, 22, 20), 27, "literal", 4, 3, 10, "fgs_operator"),
+    ((24, 22, 20), 27, "onesync", 5, 4, 8, "fgs_operator")])
+def test_eta_matches_oracle(dims, points, algo, s, nu, K, gram):
     csr = O.CSR(*I.poisson_csr(dims, points))
     b = np.ones(csr.n)  # the unit right-hand side of the paper's 27-point benchmark
     info, d, bi = run(sstep.Stencil(*dims, points=points), b, s=s, sweeps=nu, rtol=0.0,
-                      max_outer=K, algo=algo, power_iters=20, power_tol=0.0)
+                      max_outer=K, algo=algo, gram=gram, power_iters=20, power_tol=0.0)
     assert info.outer_iters == K
     ref = O.pcgs(csr, b, s=s, nu=nu, rtol=0.0, max_outer=K, algo=algo,
                  lambda_min=bi["lambda_min"], lambda_max=bi["lambda_max"], history=True)

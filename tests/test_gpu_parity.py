@@ -152,6 +152,47 @@ def test_fgs(s, nrhs, nu, solver):
         assert np.max(np.abs(Xg[c] - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("s,nrhs,nu", [(1, 1, 1), (2, 3, 2), (3, 2, 3), (4, 4, 3), (4, 1, 30),
+                                       (4, 2, 1), (5, 5, 7), (5, 2, 0), (4, 4, 64)])
+def test_fgs_operator(s, nrhs, nu):
+    """The operator form of the nu sweeps (P_nu by doubling, then X = P_nu B) against the oracle's
+    sweeps: equal up to rounding, bounded by the magnitudes the products involve."""
+    rng = np.random.default_rng(1000 + s * 10 + nu)
+    G = rng.standard_normal((s, s))
+    Qm, _ = np.linalg.qr(G)
+    W = Qm @ np.diag(np.geomspace(1, 50, s)) @ Qm.T
+    d = rng.uniform(0.3, 3.0, s)
+    W = W * np.outer(d, d)
+    W = (W + W.T) / 2
+    B = rng.standard_normal((nrhs, s))
+    X = torch.zeros((nrhs, s), dtype=torch.float64, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    sstep.fgs(dev(W.T.copy()), dev(B), nu, X, solver="fgs_operator", status=st)
+    Xg = host(X)
+    assert int(host(st)[0]) == 0
+    Pref = np.column_stack([O.fgs(W, np.eye(s)[:, j], nu) for j in range(s)])
+    for c in range(nrhs):
+        ref = O.fgs(W, B[c], nu)
+        bound = 1e-13 * (2 + np.log2(nu + 1)) * (np.abs(Pref) @ np.abs(B[c])).max() + 1e-300
+        assert np.max(np.abs(Xg[c] - ref)) <= bound, (np.max(np.abs(Xg[c] - ref)), bound)
+
+
+def test_fgs_operator_rejects_large_s():
+    W = np.eye(6)
+    X = torch.zeros((1, 6), dtype=torch.float64, device=DEV)
+    with pytest.raises(sstep.SstepError) as e:
+        sstep.fgs(dev(W), dev(np.ones((1, 6))), 2, X, solver="fgs_operator")
+    assert e.value.status == sstep.ERR_UNSUPPORTED
+
+
+def test_fgs_operator_breakdown_reported():
+    W = np.array([[1.0, 0.2], [0.2, -1.0]])
+    X = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    sstep.fgs(dev(W), dev(np.ones((1, 2))), 2, X, solver="fgs_operator", status=st)
+    assert int(host(st)[0]) == sstep.ERR_BREAKDOWN
+
+
 def test_fgs_breakdown_reported():
     W = np.array([[1.0, 0.2], [0.2, -1.0]])
     X = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
@@ -244,7 +285,11 @@ def gpu_solve(A, b, x0=None, **kw):
     ((30, 26, 22), 7, "stencil", 4, 30, "literal", "fgs", 25),
     ((19, 17, 15), 27, "stencil", 4, 30, "onesync", "fgs", 10),
     ((30, 26, 22), 7, "stencil", 4, 0, "onesync", "cholesky", 20),
-    ((30, 26, 22), 7, "stencil", 1, 1, "onesync", "fgs", 60)])
+    ((30, 26, 22), 7, "stencil", 1, 1, "onesync", "fgs", 60),
+    # the operator form of the sweeps (equal to the oracle's sweeps up to rounding)
+    ((64, 64), 5, "csr", 4, 2, "literal", "fgs_operator", 40),
+    ((30, 26, 22), 7, "stencil", 4, 30, "literal", "fgs_operator", 25),
+    ((30, 26, 22), 7, "stencil", 5, 3, "onesync", "fgs_operator", 12)])
 def test_solve_fixed_count(dims, points, form, s, nu, algo, gram, K):
     A, csr = operators(dims, points, form)
     xt, b = I.poisson_problem(dims, points)
@@ -252,7 +297,8 @@ def test_solve_fixed_count(dims, points, form, s, nu, algo, gram, K):
     x, info, hist, bi = gpu_solve(A, b, s=s, sweeps=nu, rtol=0.0, max_outer=K, algo=algo, gram=gram,
                                   power_iters=20, power_tol=0.0, power_v0=dev(v0), lambda_min=-1.0)
     assert info.status == sstep.NOT_CONVERGED and info.outer_iters == K
-    ref = O.pcgs(csr, b, s=s, nu=nu, rtol=0.0, max_outer=K, algo=algo, gram=gram,
+    ref = O.pcgs(csr, b, s=s, nu=nu, rtol=0.0, max_outer=K, algo=algo,
+                 gram="fgs" if gram == "fgs_operator" else gram,
                  lambda_min=bi["lambda_min"], lambda_max=bi["lambda_max"], history=True)
     assert relerr(x, ref.x) <= 1e-9
     assert np.allclose(hist[1:K + 1], ref.hist[1:K + 1], rtol=1e-8)
@@ -260,13 +306,15 @@ def test_solve_fixed_count(dims, points, form, s, nu, algo, gram, K):
 
 @pytest.mark.parametrize("dims,points,form,s,nu,gram", [
     ((48, 40, 32), 7, "stencil", 4, 30, "fgs"), ((64, 64), 5, "csr", 4, 30, "fgs"),
-    ((40, 36, 28), 7, "csr", 2, 0, "cholesky"), ((24, 22, 20), 27, "stencil", 4, 30, "fgs")])
+    ((40, 36, 28), 7, "csr", 2, 0, "cholesky"), ((24, 22, 20), 27, "stencil", 4, 30, "fgs"),
+    ((48, 40, 32), 7, "stencil", 4, 30, "fgs_operator")])
 def test_solve_free_running(dims, points, form, s, nu, gram):
     A, csr = operators(dims, points, form)
     xt, b = I.poisson_problem(dims, points)
     x, info, hist, bi = gpu_solve(A, b, s=s, sweeps=nu, rtol=1e-8, gram=gram,
                                   power_v0=dev(I.power_start(csr.n)))
-    ref = O.pcgs(csr, b, s=s, nu=nu, rtol=1e-8, algo="onesync", gram=gram,
+    ref = O.pcgs(csr, b, s=s, nu=nu, rtol=1e-8, algo="onesync",
+                 gram="fgs" if gram == "fgs_operator" else gram,
                  lambda_min=bi["lambda_min"], lambda_max=bi["lambda_max"])
     assert info.status == sstep.OK and ref.status == O.OK
     assert abs(info.outer_iters - ref.iters) <= 1
