@@ -467,10 +467,9 @@ def run_q1(N, dev, sstep, I, torch):
         for label, kw in (("fp64_s8_nu30", dict(s=8, sweeps=30)),
                           ("fp32_rr_s8_nu30", dict(s=8, sweeps=30, precision="fp32_rr", rr_period=8)),
                           ("fp32_rr_s8_nu3", dict(s=8, sweeps=3, precision="fp32_rr", rr_period=8)),
+                          ("fp32_rr_s4_nu30", dict(s=4, sweeps=30, precision="fp32_rr", rr_period=4)),
                           ("fp64_pcg", dict(algo="pcg")),
                           ("fp32_rr_pcg", dict(algo="pcg", precision="fp32_rr"))):
-            if pre == "mf_" and label == "fp32_rr_pcg":
-                continue  # the FP32 PCG comparator takes the Q1 operator as CSR
             S = sstep.Solver(A, rtol=1e-8, power_iters=20, power_tol=0.0, lambda_min=-1.0, **kw)
             x = torch.zeros_like(bd)
             S.solve(bd, x)  # warm-up (graph instantiation)

@@ -902,8 +902,6 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
       return cudaMalloc((void**)p, sizeof(float) * (size_t)std::max<int64_t>(count, 1));
     };
     if (pcg) {
-      if (A->kind == SSTEP_MATRIX_Q1)
-        return fail(SSTEP_ERR_UNSUPPORTED, "FP32 PCG takes the Q1 operator as CSR");
       CK(fal(&h->pf, lf));
       CK(fal(&h->Apf, lf));
     } else {
@@ -927,11 +925,15 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
       CK(fal(&h->kappaf, (int64_t)h->op.q1.kpitch * (A->ny + 1) * (A->nz + 1)));
       h->op.q1.kappaf = h->kappaf;
       CK(launch_q1_kappaf(h->op.q1, h->kappaf, h->st));
-      std::vector<const float*> cols(s);
-      for (int c = 0; c < s; ++c) cols[c] = h->Zf + c * lf;
+      // the vectors the TMA-fed kernel reads: the basis columns, or PCG's direction p
+      std::vector<const float*> cols;
+      if (pcg) cols.push_back(h->pf);
+      else
+        for (int c = 0; c < s; ++c) cols.push_back(h->Zf + c * lf);
       // null (or SSTEP_Q1_TMA=0 in the environment): the plain-load kernel serves every step
       const char* tma_env = std::getenv("SSTEP_Q1_TMA");
-      if (!(tma_env && tma_env[0] == '0')) h->q1tma = q1_tma_build(h->op.q1, cols.data(), s);
+      if (!(tma_env && tma_env[0] == '0'))
+        h->q1tma = q1_tma_build(h->op.q1, cols.data(), (int)cols.size());
       h->op.q1.tma = h->q1tma;
       if (h->dinv) {
         CK(fal(&h->dinvf, lf));

@@ -512,6 +512,26 @@ struct MpkF32Args {
 };
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st);
 
+// FP32 PCG product step: the last CTA turns the grid's double-float sum p^T (A p) into
+// alpha = r^T z / p^T A p (breakdown when p^T A p is not positive and finite).  Reached by every
+// thread of every CTA; nothing is changed when an earlier failure already stopped the solve.
+__device__ __forceinline__ void pap_finish(const MpkF32Args& e, const float (&hi)[1],
+                                           const float (&lo)[1]) {
+  __shared__ double buf[32];
+  if (!df_grid_sums<1>(hi, lo, buf, e.partials, &e.ctrl->ticket[TK_PCG1])) return;
+  if (threadIdx.x == 0) {
+    Ctrl* c = e.ctrl;
+    const double pap = buf[0];
+    if (c->done) return;
+    if (!(pap > 0.0) || pap > 1.79e308) {
+      c->status = SSTEP_ERR_BREAKDOWN;
+      c->done = 1;
+    } else {
+      c->pcg_alpha = c->rz / pap;
+    }
+  }
+}
+
 // Q1 operator kernels (k_q1.cu), reached through launch_operator / launch_mpk_f32.
 cudaError_t launch_q1_operator(const Q1Op& A, const EpiArgs& e, cudaStream_t st);
 cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t st);

@@ -270,24 +270,6 @@ __global__ void __launch_bounds__(kThreads) k_csr(CsrOp A, EpiArgs e) {
 
 // ---------------------------------------------------------------- FP32 MPK step (mixed path)
 
-// FP32 PCG product step: the last CTA turns the grid's double-float sum p^T (A p) into
-// alpha = r^T z / p^T A p (breakdown when p^T A p is not positive and finite).
-__device__ __forceinline__ void pap_finish(const MpkF32Args& e, const float (&hi)[1],
-                                           const float (&lo)[1]) {
-  __shared__ double buf[32];
-  if (!df_grid_sums<1>(hi, lo, buf, e.partials, &e.ctrl->ticket[TK_PCG1])) return;
-  if (threadIdx.x == 0) {
-    Ctrl* c = e.ctrl;
-    const double pap = buf[0];
-    if (!(pap > 0.0) || pap > 1.79e308) {
-      c->status = SSTEP_ERR_BREAKDOWN;
-      c->done = 1;
-    } else {
-      c->pcg_alpha = c->rz / pap;
-    }
-  }
-}
-
 template <int PTS, bool POISSON>
 __device__ __forceinline__ float stencil7_point_f(const MpkF32Args& e, const float (*p)[TX + 2],
                                                   int tx, int ty, float ub, float uc, float ua) {
@@ -780,7 +762,8 @@ cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st
       k_csrf<false, false, true><<<csr_ctas(A.csr.n), kThreads, 0, st>>>(A.csr, e);
       return cudaGetLastError();
     }
-    return cudaErrorNotSupported;  // Q1: the FP32 PCG comparator takes the CSR form
+    if (A.kind == SSTEP_MATRIX_Q1) return launch_q1_mpk_f32(A.q1, e, st);
+    return cudaErrorNotSupported;
   }
   if (A.kind == SSTEP_MATRIX_Q1) return launch_q1_mpk_f32(A.q1, e, st);
   const bool scale = e.first && e.dinv != nullptr;

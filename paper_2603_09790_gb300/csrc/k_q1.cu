@@ -257,10 +257,13 @@ __global__ void __launch_bounds__(QT) k_q1(Q1Op A, EpiArgs e, int zc) {
   reduce_and_finish<EPI>(e, red);
 }
 
-template <bool FIRST, bool SCALE>
+// PAP: the FP32 PCG product step (u = p, y = A p, no recurrence): p^T (A p) is accumulated in
+// double-float and the last CTA forms alpha (pap_finish).
+template <bool FIRST, bool SCALE, bool PAP = false>
 __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
   if (e.ctrl && e.ctrl->done) return;
   __shared__ Q1Smem<float> sh;
+  float ph[1] = {0.0f}, pl[1] = {0.0f};
   const float* __restrict__ u = e.u;
   auto load_u = [&](int64_t idx) -> float {
     float v = __ldg(u + idx);
@@ -278,7 +281,9 @@ __global__ void __launch_bounds__(QT) k_q1f(Q1Op A, MpkF32Args e, int zc) {
       uc *= e.dinv_u;
     }
     mpk_f32_epilogue(e, i, yv, uc, FIRST);
+    if constexpr (PAP) df_acc_prod(ph[0], pl[0], uc, yv);
   });
+  if constexpr (PAP) pap_finish(e, ph, pl);
 }
 
 // ---------------------------------------------------------------- TMA-fed FP32 MPK step
@@ -418,11 +423,14 @@ __device__ __forceinline__ float q1_vertex_win(const UWin2& m, const UWin2& c, c
   return fmaf(k8 * (1.0f / 3.0f), uc, -(s * (1.0f / 12.0f)));
 }
 
+// PAP: the FP32 PCG product step, as in k_q1f.
+template <bool PAP = false>
 __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUtensorMap mu,
                                                  const __grid_constant__ CUtensorMap mk, Q1Op A,
                                                  MpkF32Args e, int zc) {
   if (e.ctrl && e.ctrl->done) return;
   __shared__ TmaSmem sh;
+  float pah[1] = {0.0f}, pal[1] = {0.0f};  // PAP: p^T (A p)
   const int tid = threadIdx.x, tx = tid % QX, ty = tid / QX;
   const int nx = A.nx, ny = A.ny, nz = A.nz;
   const int x0 = blockIdx.x * TBX, y0 = blockIdx.y * QY;
@@ -499,6 +507,10 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
         yv.y = q1_vertex_win<1>(uw[j % 3], uw[(j + 1) % 3], uw[(j + 2) % 3], kw[(j + 1) % 2],
                                 kw[j % 2], uc.y);
         *reinterpret_cast<float2*>(e.y + idx) = yv;  // A z_q
+        if constexpr (PAP) {
+          df_acc_prod(pah[0], pal[0], uc.x, yv.x);
+          df_acc_prod(pah[0], pal[0], uc.y, yv.y);
+        }
         if (e.znext) {
           const float2 t = e.zprev ? make_float2(-zp.x, -zp.y) : make_float2(0.0f, 0.0f);
           float2 zn;
@@ -521,6 +533,7 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
       e.ctrl->done = 1;
     }
   }
+  if constexpr (PAP) pap_finish(e, pah, pal);  // every thread: stop is uniform over the CTA
 }
 
 // FP32 conductivities with rows padded to kpitch (padding zero).
@@ -683,7 +696,7 @@ cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t s
         // first two planes' latency) is paid once per CTA
         static int per_sm = 0;
         if (!per_sm) {
-          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1f_tma, QT, 0) !=
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_q1f_tma<false>, QT, 0) !=
                   cudaSuccess ||
               per_sm < 1)
             per_sm = 1;
@@ -693,9 +706,15 @@ cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t s
         gz = std::min<int64_t>(gz, std::max(1, A.nz / 8));
         const int zc = (int)((A.nz + gz - 1) / gz);
         const dim3 grid(gx, gy, (A.nz + zc - 1) / zc);
-        k_q1f_tma<<<grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, zc);
+        if (e.pap) k_q1f_tma<true><<<grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, zc);
+        else k_q1f_tma<false><<<grid, QT, 0, st>>>(A.tma->mu[c], A.tma->mk, A, e, zc);
         return cudaGetLastError();
       }
+  }
+  if (e.pap) {
+    if (e.first) return cudaErrorInvalidValue;
+    k_q1f<false, false, true><<<g.grid, QT, 0, st>>>(A, e, g.zc);
+    return cudaGetLastError();
   }
   if (e.first) {
     if (e.dinv) k_q1f<true, true><<<g.grid, QT, 0, st>>>(A, e, g.zc);

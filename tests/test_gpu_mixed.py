@@ -148,11 +148,7 @@ def test_pcg_fp32_fixed_count_close_to_fp64(dims):
     assert relerr(xm, xd) <= 1e-4
 
 
-def test_pcg_fp32_zero_rhs_and_q1_rejected():
+def test_pcg_fp32_zero_rhs():
     A = sstep.Stencil(12, 10, 8, 7)
     x, info, _ = solve(A, np.zeros(960), algo="pcg", precision="fp32_rr", lambda_max=2.0)
     assert info.status == sstep.OK and info.outer_iters == 0 and not x.any()
-    (rp, ci, v), kappa, xt, b = I.q1_lognormal_problem((8, 8, 8))
-    with pytest.raises(sstep.SstepError) as e:
-        sstep.Solver(sstep.Q1(8, 8, 8, dev(kappa)), algo="pcg", precision="fp32_rr", lambda_max=2.0)
-    assert e.value.status == sstep.ERR_UNSUPPORTED

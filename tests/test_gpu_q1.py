@@ -193,3 +193,33 @@ def test_fp32_tma_steps_equal_plain_loads(dims, monkeypatch):
     (i1, x1), (i0, x0) = out
     assert i1.status == sstep.OK and i1.relres_true <= 2e-8
     assert i1.outer_iters == i0.outer_iters and torch.equal(x1, x0)
+
+
+@pytest.mark.parametrize("dims", [(24, 20, 16), (33, 9, 13), (76, 12, 17), (128, 24, 20)])
+def test_fp32_pcg_matrix_free(dims, monkeypatch):
+    """Classical PCG in the FP32-basis recipe on the matrix-free operator (A p and p^T A p in the
+    FP32 Q1 kernels): it reaches the FP64 true residual with a count close to the oracle's PCG on
+    the assembled matrix, and on the small grids its solution agrees with the oracle's to the
+    kappa-scaled FP64 bound.  Where the TMA-fed kernel applies (nx a multiple of 4, nx >= 72,
+    ny >= 10) the plain-load kernel gives the same solve up to the order of the p^T A p sums."""
+    csr, kappa, b = problem(dims, corr=4.0)
+    kw = dict(algo="pcg", rtol=1e-8, precision="fp32_rr", lambda_max=2.0)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SSTEP_Q1_TMA", flag)
+        with sstep.Solver(q1(dims, kappa), **kw) as S:
+            x = torch.zeros(csr.n, dtype=torch.float64, device=DEV)
+            info = S.solve(dev(b), x)
+        out.append((info, x.cpu().numpy()))
+    (i1, x1), (i0, x0) = out
+    ref = O.pcg(csr, b, rtol=1e-8)
+    for info in (i1, i0):
+        assert info.status == sstep.OK and info.relres_true <= 2e-8
+        assert abs(info.outer_iters - ref.iters) <= max(3, 0.05 * ref.iters), (info.outer_iters,
+                                                                             ref.iters)
+    assert abs(i1.outer_iters - i0.outer_iters) <= 2
+    if csr.n <= 8000:
+        lam = np.linalg.eigvalsh(csr.dense())
+        exact = O.pcg(csr, b, rtol=1e-13).x
+        for x in (x1, x0):
+            assert relerr(x, exact) <= 2e-8 * lam[-1] / lam[0]
