@@ -121,9 +121,9 @@ enum {
 /* Reduced solves.  FGS: nu forward Gauss-Seidel sweeps from 0 (Section 3.1, Eq. fgs-iteration).
  * FGS_OPERATOR: the same nu sweeps applied as one s x s matrix, x = P_nu b with
  * P_nu = (I + M + ... + M^{nu-1}) (D + L)^{-1}, M = I - (D + L)^{-1} W, formed by repeated
- * doubling in O(log nu) small products (s <= 5); equal to FGS in exact arithmetic, different
+ * doubling in O(log nu) small products (s <= 8); equal to FGS in exact arithmetic, different
  * in rounding; formed once per W_k and applied to both systems that share it (alpha_k,
- * beta_k).  The FP32-basis path uses it whenever FGS is asked for and s <= 5.
+ * beta_k).  The FP32-basis path uses it whenever FGS is asked for.
  * CHOLESKY: exact solves (Section 3.3). */
 enum { SSTEP_GRAM_FGS = 0, SSTEP_GRAM_CHOLESKY = 1, SSTEP_GRAM_FGS_OPERATOR = 2 };
 
@@ -296,7 +296,7 @@ SSTEP_API sstep_status sstep_block_gram_noalloc(int64_t n, int nl, const double*
  * W itself: W = D + L_W + L_W^T).  W: s x s column-major, B and X: s x nrhs column-major, all
  * device pointers; 1 <= s <= 16, 1 <= nrhs <= 16.  Breakdown (W_ii <= 0 or non-finite) is
  * written to *status_dev (device int, may be NULL) as SSTEP_ERR_BREAKDOWN, else SSTEP_OK.
- * solver = SSTEP_GRAM_CHOLESKY solves exactly instead; SSTEP_GRAM_FGS_OPERATOR (s <= 5,
+ * solver = SSTEP_GRAM_CHOLESKY solves exactly instead; SSTEP_GRAM_FGS_OPERATOR (s <= 8,
  * else SSTEP_ERR_UNSUPPORTED) forms P_nu and returns X = P_nu B, the products in increasing
  * order of the summed index.  stream: cudaStream_t as void*. */
 SSTEP_API sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu, int solver,

@@ -501,9 +501,9 @@ sstep_status reset_ctrl(sstep_ctx* h) {
   c->s = h->s;
   c->nu = h->o.sweeps;
   c->solver = h->o.gram_solver;
-  // the FP32-basis path applies the FGS sweeps in operator form where it can (s <= 5): one
+  // the FP32-basis path applies the FGS sweeps in operator form (s <= 8, all it supports): one
   // P_nu(W_k) serves alpha_k and beta_k, and the chain of the reduced solve is O(log nu)
-  if (h->o.precision == SSTEP_PRECISION_FP32_RR && c->solver == SSTEP_GRAM_FGS && h->s <= 5)
+  if (h->o.precision == SSTEP_PRECISION_FP32_RR && c->solver == SSTEP_GRAM_FGS && h->s <= 8)
     c->solver = SSTEP_GRAM_FGS_OPERATOR;
   c->full_gram = full_blocks(h);
   c->power_tol = h->o.power_tol;
@@ -615,8 +615,8 @@ sstep_status validate_opts(const sstep_opts* o) {
   if (o->max_outer < 0) return fail(SSTEP_ERR_INVALID, "max_outer must be >= 0");
   if (o->algo < 0 || o->algo > 2) return fail(SSTEP_ERR_INVALID, "unknown algo");
   if (o->gram_solver < 0 || o->gram_solver > 2) return fail(SSTEP_ERR_INVALID, "unknown gram_solver");
-  if (o->gram_solver == SSTEP_GRAM_FGS_OPERATOR && o->s > 5)
-    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 5");
+  if (o->gram_solver == SSTEP_GRAM_FGS_OPERATOR && o->s > 8)
+    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 8");
   if (o->power_iters < 1 && !(o->lambda_max > 0.0))
     return fail(SSTEP_ERR_INVALID, "power_iters must be >= 1 when lambda_max is not given");
   if (o->precision != SSTEP_PRECISION_FP64 && o->precision != SSTEP_PRECISION_FP32_RR)
@@ -1325,8 +1325,8 @@ sstep_status sstep_fgs(int s, const double* W, int nrhs, const double* B, int nu
       (solver != SSTEP_GRAM_FGS && solver != SSTEP_GRAM_CHOLESKY &&
        solver != SSTEP_GRAM_FGS_OPERATOR))
     return fail(SSTEP_ERR_INVALID, "bad fgs arguments");
-  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > 5)
-    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 5");
+  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > 8)
+    return fail(SSTEP_ERR_UNSUPPORTED, "the FGS operator form takes s <= 8");
   CK(launch_fgs_standalone(s, W, nrhs, B, nu, solver, X, status_dev, (cudaStream_t)stream));
   return SSTEP_OK;
 }

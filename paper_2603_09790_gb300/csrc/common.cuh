@@ -60,7 +60,7 @@ struct Ctrl {
   double alpha[kMaxS];
   double beta[kMaxS * kMaxS];    // column-major s x s
   double W[kMaxS * kMaxS];       // W_k used for alpha_k (and for beta_k)
-  double P[32];                  // FGS operator P_nu(W_k) (solver SSTEP_GRAM_FGS_OPERATOR, s <= 5)
+  double P[64];                  // FGS operator P_nu(W_k) (solver SSTEP_GRAM_FGS_OPERATOR, s <= 8)
   int p_valid;                   // 1 once P holds the operator of the current W
   double sums[kMaxEntries];      // reduced Gram sums of the last reduction
   unsigned int ticket[kNumTickets];

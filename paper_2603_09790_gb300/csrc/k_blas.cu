@@ -201,16 +201,95 @@ __device__ void fgs_operator_s(const double* W, const double* rinv, int nu, doub
   if (in) P[lane] = p;
 }
 
-// Returns false when s is too large for the one-warp layout.
-__device__ bool fgs_operator(int s, const double* W, const double* rinv, int nu, double* P) {
-  switch (s) {
-    case 1: fgs_operator_s<1>(W, rinv, nu, P); return true;
-    case 2: fgs_operator_s<2>(W, rinv, nu, P); return true;
-    case 3: fgs_operator_s<3>(W, rinv, nu, P); return true;
-    case 4: fgs_operator_s<4>(W, rinv, nu, P); return true;
-    case 5: fgs_operator_s<5>(W, rinv, nu, P); return true;
-    default: return false;
+// C = A B for s x s matrices in shared memory (column-major), one entry per thread of the CTA's
+// first s^2 threads starting at thread `first`, products summed in increasing k from 0 (the
+// order of lane_mm).
+__device__ __forceinline__ void smem_mm(int s, const double* A, const double* B, double* C,
+                                        int first) {
+  const int e = (int)threadIdx.x - first;
+  if (e < 0 || e >= s * s) return;
+  const int i = e % s, j = e / s;
+  double acc = 0.0;
+  for (int k = 0; k < s; ++k) acc = fma(A[i + k * s], B[k + j * s], acc);
+  C[e] = acc;
+}
+
+constexpr int kOpMaxS = 8;  // largest s of the operator form
+
+// fgs_operator_s for 6 <= s <= 8: the same products in the same order, one matrix entry per
+// thread through shared memory.  Executed by the whole CTA (blockDim >= 2 s^2).
+__device__ void fgs_operator_cta(int s, const double* W, const double* rinv, int nu, double* P) {
+  constexpr int Q = kOpMaxS * kOpMaxS;
+  __shared__ double T[Q], M1[Q], Sm[Q], Pw[Q], X1[Q], X2[Q];
+  const int e = threadIdx.x, ss = s * s;
+  const bool in = e < ss;
+  const int i = in ? e % s : 0, j = in ? e / s : 0;
+  const double eye = (in && i == j) ? 1.0 : 0.0;
+  // T = (D + L)^{-1}: row r of every column final after step r
+  double acc = eye;
+  for (int r = 0; r < s; ++r) {
+    if (in && i == r) T[e] = acc * rinv[i];
+    __syncthreads();
+    if (in && i > r) acc = fma(-W[i + r * s], T[r + j * s], acc);
   }
+  __syncthreads();
+  if (nu <= 0) {
+    if (in) P[e] = 0.0;
+    __syncthreads();
+    return;
+  }
+  smem_mm(s, T, W, X1, 0);
+  __syncthreads();
+  if (in) {
+    M1[e] = eye - X1[e];
+    Sm[e] = eye;
+  }
+  __syncthreads();
+  if (in) Pw[e] = M1[e];
+  __syncthreads();
+  for (int bit = 30 - __clz(nu); bit >= 0; --bit) {
+    smem_mm(s, Pw, Sm, X1, 0);   // M^m S_m
+    smem_mm(s, Pw, Pw, X2, ss);  // (M^m)^2, on the next s^2 threads
+    __syncthreads();
+    if (in) {
+      Sm[e] += X1[e];
+      Pw[e] = X2[e];
+    }
+    __syncthreads();
+    if ((nu >> bit) & 1) {
+      smem_mm(s, M1, Sm, X1, 0);   // M S_m
+      smem_mm(s, Pw, M1, X2, ss);  // M^m M
+      __syncthreads();
+      if (in) {
+        Sm[e] = eye + X1[e];
+        Pw[e] = X2[e];
+      }
+      __syncthreads();
+    }
+  }
+  smem_mm(s, Sm, T, P, 0);
+  __syncthreads();
+}
+
+// P = P_nu(W) for s <= kOpMaxS; executed by the whole CTA (blockDim >= 2 kOpMaxS^2); ends with
+// __syncthreads().  Returns false for larger s.
+__device__ bool fgs_operator(int s, const double* W, const double* rinv, int nu, double* P) {
+  if (s > kOpMaxS) return false;
+  if (s > 5) {
+    fgs_operator_cta(s, W, rinv, nu, P);
+    return true;
+  }
+  if (threadIdx.x < 32) {
+    switch (s) {
+      case 1: fgs_operator_s<1>(W, rinv, nu, P); break;
+      case 2: fgs_operator_s<2>(W, rinv, nu, P); break;
+      case 3: fgs_operator_s<3>(W, rinv, nu, P); break;
+      case 4: fgs_operator_s<4>(W, rinv, nu, P); break;
+      default: fgs_operator_s<5>(W, rinv, nu, P); break;
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // X = P B (P: s x s, B and X: s x nrhs, column-major), one entry per thread, the products
@@ -279,14 +358,14 @@ __device__ void chol_column(int s, const double* L, const double* b, double* x, 
 // (fgs_warp: lane i owns row i, successive right-hand sides on successive warps, which the SM
 // schedules on different sub-partitions).
 //
-// solver SSTEP_GRAM_FGS_OPERATOR (s <= 5; larger s take the sweeps): warp 0 forms P_nu(W) into
+// solver SSTEP_GRAM_FGS_OPERATOR (s <= 8; larger s take the sweeps): P_nu(W) is formed into
 // scratch[0 .. s*s) (fgs_operator) and X = P_nu B; the caller may keep P for a later system
 // with the same W.
 __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs, int nu,
                               int solver, double* X, double* scratch /* s*s + s */) {
   __shared__ int ok;
   const int tid = threadIdx.x;
-  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > 5) solver = SSTEP_GRAM_FGS;
+  if (solver == SSTEP_GRAM_FGS_OPERATOR && s > kOpMaxS) solver = SSTEP_GRAM_FGS;
   if (solver == SSTEP_GRAM_CHOLESKY) {
     if (tid == 0) {
       ok = 1;
@@ -314,8 +393,7 @@ __device__ bool reduced_solve(int s, const double* W, const double* B, int nrhs,
   __syncthreads();
   if (!ok) return false;
   if (solver == SSTEP_GRAM_FGS_OPERATOR) {
-    if (tid < 32) fgs_operator(s, W, scratch + s * s, nu, scratch);
-    __syncthreads();
+    fgs_operator(s, W, scratch + s * s, nu, scratch);
     apply_operator(s, scratch, B, nrhs, X);
   } else if (solver != SSTEP_GRAM_CHOLESKY) {
     fgs_warp_dispatch(s, W, scratch + s * s, B, nrhs, nu, X);
@@ -382,14 +460,14 @@ __device__ void record_beta(Ctrl* c, int s, const double* B, const double* X) {
 // Operator form: keeps P_nu(W) (left in scr[0 .. s*s) by reduced_solve) for the next system
 // with the same W.
 __device__ __forceinline__ void keep_operator(Ctrl* c, int s, const double* scr) {
-  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || s > 5) return;
+  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || s > kOpMaxS) return;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) c->P[e] = scr[e];
   if (threadIdx.x == 0) c->p_valid = 1;
 }
 
 // Operator form: whether a kept P_nu(W) can serve the next system with the same W.
 __device__ __forceinline__ bool can_reuse_operator(const Ctrl* c, int s) {
-  return c->solver == SSTEP_GRAM_FGS_OPERATOR && s <= 5 && c->p_valid;
+  return c->solver == SSTEP_GRAM_FGS_OPERATOR && s <= kOpMaxS && c->p_valid;
 }
 
 // X = P B with the kept P for the s right-hand sides of the conjugation system (no new checks:
@@ -409,7 +487,7 @@ __device__ __forceinline__ void reuse_operator(const Ctrl* c, int s, const doubl
 // Loads c->P into shared memory (all CTAs of a conjugation-system kernel, at its start: the
 // last CTA then finds it there).  Executed by the whole CTA; the caller synchronises.
 __device__ __forceinline__ void preload_operator(const Ctrl* c, double* pre) {
-  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || c->s > 5 || !c->p_valid) return;
+  if (c->solver != SSTEP_GRAM_FGS_OPERATOR || c->s > kOpMaxS || !c->p_valid) return;
   for (int e = threadIdx.x; e < c->s * c->s; e += blockDim.x) pre[e] = c->P[e];
 }
 
@@ -1211,17 +1289,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
 #pragma unroll
     for (int j = 0; j < NC; ++j) yv[j] = __ldg(reinterpret_cast<const float4*>(yp[j]) + v);
     if (ylo) yl = __ldg(reinterpret_cast<const float4*>(ylo) + v);
-#define SSTEP_DF_LANE(c)                                                          \
-    _Pragma("unroll") for (int i = 0; i < NR; ++i) {                              \
-      _Pragma("unroll") for (int j = 0; j < NC; ++j)                              \
-        df_acc_prod(hi[i * NC + j], lo[i * NC + j], xv[i].c, yv[j].c);            \
-      lo[i * NC + NC - 1] = fmaf(xv[i].c, yl.c, lo[i * NC + NC - 1]);             \
+    // the four points of a trip share one update of each low part (df_acc_dot4)
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) df_acc_dot4(hi[i * NC + j], lo[i * NC + j], xv[i], yv[j]);
+      float& l = lo[i * NC + NC - 1];
+      l = fmaf(xv[i].x, yl.x, fmaf(xv[i].y, yl.y, fmaf(xv[i].z, yl.z, fmaf(xv[i].w, yl.w, l))));
     }
-    SSTEP_DF_LANE(x)
-    SSTEP_DF_LANE(y)
-    SSTEP_DF_LANE(z)
-    SSTEP_DF_LANE(w)
-#undef SSTEP_DF_LANE
   }
   for (int64_t p = 4 * n4 + gid; p < g.n; p += stride) {  // the last n mod 4 points
     float xv[NR], yv[NC];
@@ -1238,10 +1313,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (K <= 32) {
+    // the warp stage on the FP32 pipe (reduce-scatter, as in df_grid_sums), one FP64
+    // conversion per lane that ends with a value
+    float vh, vl;
+    df_warp_scatter<K>(hi, lo, vh, vl);
+    constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    constexpr int R = 32 / KP;
+    if (lane % R == 0 && lane / R < K) buf[wid * K + lane / R] = (double)vh + (double)vl;
+  } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double v = warp_sum((double)hi[k] + (double)lo[k]);
-    if (lane == 0) buf[wid * K + k] = v;
+    for (int k = 0; k < K; ++k) {
+      const double v = warp_sum((double)hi[k] + (double)lo[k]);
+      if (lane == 0) buf[wid * K + k] = v;
+    }
   }
   __syncthreads();
   const unsigned int cta = blockIdx.x + gridDim.x * blockIdx.y;
@@ -1995,7 +2080,7 @@ cudaError_t launch_update(const UpdArgs& u, cudaStream_t st) {
 
 cudaError_t launch_fgs_standalone(int s, const double* W, int nrhs, const double* B, int nu,
                                   int solver, double* X, int* status_dev, cudaStream_t st) {
-  k_fgs_standalone<<<1, 32, 0, st>>>(s, W, nrhs, B, nu, solver, X, status_dev);
+  k_fgs_standalone<<<1, 128, 0, st>>>(s, W, nrhs, B, nu, solver, X, status_dev);
   return cudaGetLastError();
 }
 

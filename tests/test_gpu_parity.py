@@ -153,7 +153,8 @@ def test_fgs(s, nrhs, nu, solver):
 
 
 @pytest.mark.parametrize("s,nrhs,nu", [(1, 1, 1), (2, 3, 2), (3, 2, 3), (4, 4, 3), (4, 1, 30),
-                                       (4, 2, 1), (5, 5, 7), (5, 2, 0), (4, 4, 64)])
+                                       (4, 2, 1), (5, 5, 7), (5, 2, 0), (4, 4, 64), (6, 3, 5),
+                                       (7, 7, 30), (8, 8, 30), (8, 2, 1), (6, 1, 0), (8, 16, 3)])
 def test_fgs_operator(s, nrhs, nu):
     """The operator form of the nu sweeps (P_nu by doubling, then X = P_nu B) against the oracle's
     sweeps: equal up to rounding, bounded by the magnitudes the products involve."""
@@ -178,10 +179,10 @@ def test_fgs_operator(s, nrhs, nu):
 
 
 def test_fgs_operator_rejects_large_s():
-    W = np.eye(6)
-    X = torch.zeros((1, 6), dtype=torch.float64, device=DEV)
+    W = np.eye(9)
+    X = torch.zeros((1, 9), dtype=torch.float64, device=DEV)
     with pytest.raises(sstep.SstepError) as e:
-        sstep.fgs(dev(W), dev(np.ones((1, 6))), 2, X, solver="fgs_operator")
+        sstep.fgs(dev(W), dev(np.ones((1, 9))), 2, X, solver="fgs_operator")
     assert e.value.status == sstep.ERR_UNSUPPORTED
 
 
@@ -289,7 +290,9 @@ def gpu_solve(A, b, x0=None, **kw):
     # the operator form of the sweeps (equal to the oracle's sweeps up to rounding)
     ((64, 64), 5, "csr", 4, 2, "literal", "fgs_operator", 40),
     ((30, 26, 22), 7, "stencil", 4, 30, "literal", "fgs_operator", 25),
-    ((30, 26, 22), 7, "stencil", 5, 3, "onesync", "fgs_operator", 12)])
+    ((30, 26, 22), 7, "stencil", 5, 3, "onesync", "fgs_operator", 12),
+    ((30, 26, 22), 7, "stencil", 8, 3, "onesync", "fgs_operator", 12),
+    ((30, 26, 22), 7, "stencil", 6, 30, "literal", "fgs_operator", 12)])
 def test_solve_fixed_count(dims, points, form, s, nu, algo, gram, K):
     A, csr = operators(dims, points, form)
     xt, b = I.poisson_problem(dims, points)
