@@ -293,28 +293,44 @@ __device__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* t
   return true;
 }
 
-// Warp stage of df_grid_sums for K <= 32 values per lane, a reduce-scatter: with KP the next
-// power of two >= K (missing values 0) and L = log2 KP, level t < L pairs lanes at distance
-// 16 >> t; the lane whose bit (4 - t) is set keeps the upper half of its current values and
-// sends the lower half, its partner the reverse, and each adds what it receives.  After the L
-// levels a lane holds the sum of value index lane >> (5 - L) over the 2^L lanes that share its
-// other bits; plain butterfly levels over the remaining 5 - L lane bits finish the warp sum.
-// KP - 1 + 5 - L double-float additions per lane instead of 5 K.
+// Warp stage of df_grid_sums for K <= 64 values per lane, a reduce-scatter: with KP the next
+// power of two >= K (missing values 0) and L = min(5, log2 KP), level t < L pairs lanes at
+// distance 16 >> t; the lane whose bit (4 - t) is set keeps the upper half of its current values
+// and sends the lower half, its partner the reverse, and each adds what it receives.  After the
+// L levels a lane holds C = KP >> L values, value c being index ((lane >> (5 - L)) << log2 C) + c
+// summed over the 2^L lanes that share the lane's other bits; plain butterfly levels over the
+// remaining 5 - L lane bits finish the warp sums.  KP - C + 5 - L double-float additions per lane
+// instead of 5 K.
+template <int K>
+struct DfScatter {
+  static constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16
+                          : K <= 32 ? 32 : 64;
+  static constexpr int LOGKP = KP == 1 ? 0 : KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : KP == 16 ? 4
+                             : KP == 32 ? 5 : 6;
+  static constexpr int L = LOGKP < 5 ? LOGKP : 5;
+  static constexpr int C = KP >> L;         // values per lane at the end
+  static constexpr int LOGC = LOGKP - L;
+  static constexpr int R = 1 << (5 - L);    // lanes per group that end with the same values
+  // index of value c held by `lane`
+  __device__ static int index(int lane, int c) { return ((lane >> (5 - L)) << LOGC) + c; }
+};
+
 template <int K>
 __device__ __forceinline__ void df_warp_scatter(const float (&hi)[K], const float (&lo)[K],
-                                                float& vh, float& vl) {
-  constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-  constexpr int L = KP == 1 ? 0 : KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : KP == 16 ? 4 : 5;
+                                                float (&vh)[DfScatter<K>::C],
+                                                float (&vl)[DfScatter<K>::C]) {
+  using D = DfScatter<K>;
+  static_assert(K >= 1 && K <= 64, "K <= 64 values per thread");
   const int lane = threadIdx.x & 31;
-  float h[KP], l[KP];
+  float h[D::KP], l[D::KP];
 #pragma unroll
-  for (int k = 0; k < KP; ++k) {
+  for (int k = 0; k < D::KP; ++k) {
     h[k] = k < K ? hi[k] : 0.0f;
     l[k] = k < K ? lo[k] : 0.0f;
   }
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const int half = KP >> (t + 1), o = 16 >> t;
+  for (int t = 0; t < D::L; ++t) {
+    const int half = D::KP >> (t + 1), o = 16 >> t;
     const bool upper = (lane & o) != 0;
 #pragma unroll
     for (int k = 0; k < half; ++k) {
@@ -327,17 +343,35 @@ __device__ __forceinline__ void df_warp_scatter(const float (&hi)[K], const floa
       df_add(h[k], l[k], rh, rl);
     }
   }
-  float a = h[0], b = l[0];
 #pragma unroll
-  for (int o = 16 >> L; o > 0; o >>= 1) {
-    const float rh = __shfl_xor_sync(0xffffffffu, a, o), rl = __shfl_xor_sync(0xffffffffu, b, o);
-    df_add(a, b, rh, rl);
+  for (int c = 0; c < D::C; ++c) {
+    float a = h[c], b = l[c];
+#pragma unroll
+    for (int o = 16 >> D::L; o > 0; o >>= 1) {
+      const float rh = __shfl_xor_sync(0xffffffffu, a, o), rl = __shfl_xor_sync(0xffffffffu, b, o);
+      df_add(a, b, rh, rl);
+    }
+    vh[c] = a;
+    vl[c] = b;
   }
-  vh = a;
-  vl = b;
 }
 
-// Last step of df_grid_sums: out[e] = sum over b < nblk of partials[b * K + e] (K <= 32).
+// Writes a warp's K sums (after df_warp_scatter) to out[0 .. K) as FP64, one conversion per lane
+// that ends with a value.
+template <int K>
+__device__ __forceinline__ void df_scatter_store(const float (&vh)[DfScatter<K>::C],
+                                                 const float (&vl)[DfScatter<K>::C], double* out) {
+  using D = DfScatter<K>;
+  const int lane = threadIdx.x & 31;
+  if (lane % D::R != 0) return;
+#pragma unroll
+  for (int c = 0; c < D::C; ++c) {
+    const int v = D::index(lane, c);
+    if (v < K) out[v] = (double)vh[c] + (double)vl[c];
+  }
+}
+
+// Last step of df_grid_sums: out[e] = sum over b < nblk of partials[b * K + e] (K <= 64).
 // G = the largest power of two with G K <= blockDim groups; thread g K + e loads the partials
 // b = g, g + G, ..., up to 24 at a time (one round trip to L2 for up to 24 G CTAs) and adds them
 // by a pairwise tree; the G group sums of an entry are then added by a tree over g in shared
@@ -378,27 +412,22 @@ __device__ __forceinline__ void sum_partials_df(const double* partials, unsigned
 }
 
 // Per-thread double-float (hi, lo) pairs -> FP64 per-CTA partials -> fixed-order sum in the
-// last CTA (no CTA waits for another).  Grids may be 1D, 2D or 3D; K <= 32, blockDim a multiple
+// last CTA (no CTA waits for another).  Grids may be 1D, 2D or 3D; K <= 64, blockDim a multiple
 // of 32 up to kThreads.  buf: shared memory of at least (blockDim.x / 32) * K doubles.  Returns
 // true in the last CTA, with the K sums in buf[0..K) (valid in all of its threads).
 template <int K>
 __device__ bool df_grid_sums(const float (&hi)[K], const float (&lo)[K], double* buf,
                              double* partials, unsigned int* ticket) {
-  static_assert(K >= 1 && K <= 32, "K <= 32 values per thread");
+  static_assert(K >= 1 && K <= 64, "K <= 64 values per thread");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
   // the warp stage on the FP32 pipe; each lane then holds the warp sum of one value, so that a
   // warp converts its K values to FP64 in one instruction sequence (an FP64 instruction costs a
   // sub-partition tens of cycles however few of its lanes are active)
-  float vh, vl;
+  float vh[DfScatter<K>::C], vl[DfScatter<K>::C];
   df_warp_scatter<K>(hi, lo, vh, vl);
-  {
-    constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-    constexpr int R = 32 / KP;  // lanes per value
-    const int v = lane / R;
-    if (lane % R == 0 && v < K) buf[wid * K + v] = (double)vh + (double)vl;
-  }
+  df_scatter_store<K>(vh, vl, buf + wid * K);
   __syncthreads();
   // the warps' sums of a value in four interleaved chains
   for (int k = threadIdx.x; k < K; k += blockDim.x) {

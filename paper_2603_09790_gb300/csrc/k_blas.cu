@@ -12,6 +12,7 @@
 //    (Eq. blockdirupdate), x <- x + Q alpha, r <- r - AQ alpha, ||r||^2 and Algorithm 1's stop test.
 //  * PCG vector kernels (x/r/z update with r^T z and ||r||^2; direction update).
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -1257,6 +1258,131 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
   }
 }
 
+// Direction-block update fused with W = Q^T AQ (upper triangle, r30) and b1 = Q^T r for
+// 5 <= s <= 8: the work of k_upd_gramf with two points per thread and trip (8-byte loads and
+// stores) and one CTA per SM, since the s (s + 1) / 2 + s double-float sums take up to 88
+// registers; the two points of a trip share one update of each low part.  The last CTA forms
+// alpha (gram_tail).
+template <int S, bool FIRST>
+__global__ void __launch_bounds__(kThreads, 1) k_upd_gramwf(MixedArgs a) {
+  if (a.ctrl->done) return;
+  constexpr int NW = S * (S + 1) / 2;
+  constexpr int K = NW + S;
+  __shared__ float sb[S * S];
+  __shared__ double buf[kTiledSmem];
+  if (!FIRST)
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+  __syncthreads();
+  float hi[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+  const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n2 = a.n >> 1;
+  for (int64_t v = gid; v < n2; v += stride) {
+    float2 qn[S], an[S];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        qn[j] = __ldg(reinterpret_cast<const float2*>(a.Z + j * ld) + v);
+        an[j] = __ldg(reinterpret_cast<const float2*>(a.AZ + j * ld) + v);
+      }
+    } else {
+      float2 qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = reinterpret_cast<const float2*>(a.Q + l * ld)[v];
+        ao[l] = reinterpret_cast<const float2*>(a.AQ + l * ld)[v];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float2 vq = __ldg(reinterpret_cast<const float2*>(a.Z + j * ld) + v);
+        float2 va = __ldg(reinterpret_cast<const float2*>(a.AZ + j * ld) + v);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const float bl = sb[l + j * S];
+          vq.x = fmaf(qo[l].x, bl, vq.x);
+          vq.y = fmaf(qo[l].y, bl, vq.y);
+          va.x = fmaf(ao[l].x, bl, va.x);
+          va.y = fmaf(ao[l].y, bl, va.y);
+        }
+        qn[j] = vq;
+        an[j] = va;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      reinterpret_cast<float2*>(a.Q + j * ld)[v] = qn[j];
+      reinterpret_cast<float2*>(a.AQ + j * ld)[v] = an[j];
+    }
+    const float2 rh = __ldg(reinterpret_cast<const float2*>(a.rhi) + v);
+    const float2 rl = __ldg(reinterpret_cast<const float2*>(a.rlo) + v);
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+      for (int i = 0; i <= j; ++i) {
+        float& h = hi[tri(i, j)];
+        const float l0 = df_step(h, qn[i].x, an[j].x), l1 = df_step(h, qn[i].y, an[j].y);
+        lo[tri(i, j)] = __fadd_rn(lo[tri(i, j)], __fadd_rn(l0, l1));
+      }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      float& h = hi[NW + i];
+      const float l0 = df_step(h, qn[i].x, rh.x), l1 = df_step(h, qn[i].y, rh.y);
+      lo[NW + i] = fmaf(qn[i].x, rl.x, fmaf(qn[i].y, rl.y, __fadd_rn(lo[NW + i], __fadd_rn(l0, l1))));
+    }
+  }
+  for (int64_t p = 2 * n2 + gid; p < a.n; p += stride) {  // the last point when n is odd
+    float qn[S], an[S];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        qn[j] = __ldg(a.Z + j * ld + p);
+        an[j] = __ldg(a.AZ + j * ld + p);
+      }
+    } else {
+      float qo[S], ao[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        qo[l] = a.Q[l * ld + p];
+        ao[l] = a.AQ[l * ld + p];
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        float vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          vq = fmaf(qo[l], sb[l + j * S], vq);
+          va = fmaf(ao[l], sb[l + j * S], va);
+        }
+        qn[j] = vq;
+        an[j] = va;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      a.Q[j * ld + p] = qn[j];
+      a.AQ[j * ld + p] = an[j];
+    }
+    const float rh = __ldg(a.rhi + p), rl = __ldg(a.rlo + p);
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+      for (int i = 0; i <= j; ++i) df_acc_prod(hi[tri(i, j)], lo[tri(i, j)], qn[i], an[j]);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      df_acc_prod(hi[NW + i], lo[NW + i], qn[i], rh);
+      lo[NW + i] = fmaf(qn[i], rl, lo[NW + i]);
+    }
+  }
+  if (!df_grid_sums<K>(hi, lo, buf, a.partials, &a.ctrl->ticket[TK_GRAM])) return;
+  double* sums = buf + K;  // s^2 + s entries in the full layout
+  expand_sym_w<S>(buf, sums);
+  for (int e = threadIdx.x; e < S * S + S; e += blockDim.x) a.ctrl->sums[e] = sums[e];
+  gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + S * S + S);
+}
+
 // Register-tiled Gram products of FP32 vectors with double-float accumulation (the FP32
 // counterpart of k_gram_tiled).  A column may carry a second FP32 vector (ylo) holding the
 // low part of an FP64 vector split as hi + lo.
@@ -1313,14 +1439,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if constexpr (K <= 32) {
-    // the warp stage on the FP32 pipe (reduce-scatter, as in df_grid_sums), one FP64
-    // conversion per lane that ends with a value
-    float vh, vl;
+  if constexpr (K <= 64) {
+    // the warp stage on the FP32 pipe (reduce-scatter, as in df_grid_sums)
+    float vh[DfScatter<K>::C], vl[DfScatter<K>::C];
     df_warp_scatter<K>(hi, lo, vh, vl);
-    constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-    constexpr int R = 32 / KP;
-    if (lane % R == 0 && lane / R < K) buf[wid * K + lane / R] = (double)vh + (double)vl;
+    df_scatter_store<K>(vh, vl, buf + wid * K);
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -1951,7 +2074,26 @@ cudaError_t launch_gram_b2_f32(const MixedArgs& a, int s, cudaStream_t st) {
 }
 
 cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStream_t st) {
-  if (s > 4) {  // Q, AQ update and W, b1 as two passes (the fused form would spill)
+  const char* tp = std::getenv("SSTEP_FP32_UPD_TWO_PASS");  // read per launch (a test switch)
+  const bool two_pass = tp && tp[0] == '1';
+  if (s > 4 && !two_pass) {  // one pass, two points per thread (k_upd_gramwf)
+    switch (s) {
+#define CASE(S)                                                                               \
+  case S:                                                                                     \
+    if (first) {                                                                              \
+      static int occ = 0;                                                                     \
+      k_upd_gramwf<S, true><<<occ_grid(k_upd_gramwf<S, true>, a.n, occ), kThreads, 0, st>>>(a); \
+    } else {                                                                                  \
+      static int occ = 0;                                                                     \
+      k_upd_gramwf<S, false><<<occ_grid(k_upd_gramwf<S, false>, a.n, occ), kThreads, 0, st>>>(a); \
+    }                                                                                         \
+    return cudaGetLastError();
+      CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+      default: return cudaErrorNotSupported;
+    }
+  }
+  if (s > 4) {  // Q, AQ update and W, b1 as two passes (SSTEP_FP32_UPD_TWO_PASS=1)
     const int grid = update_ctas(a.n);
     switch (s) {
 #define CASE(S)                                                                   \

@@ -99,6 +99,30 @@ def test_mixed_fixed_count_close_to_fp64(s):
     assert relerr(xm, xd) <= 1e-4
 
 
+@pytest.mark.parametrize("s", [5, 7, 8])
+def test_mixed_wide_update_one_pass_equals_two_pass(s, monkeypatch):
+    """For 5 <= s <= 8 the Q/AQ update and W, b1 run as one pass (two points per thread); the
+    two-pass form (SSTEP_FP32_UPD_TWO_PASS=1) does the same arithmetic with the Gram sums in
+    another order.  On a grid with an odd number of points (the one-point tail) both stay
+    within the FP32 recipe's distance of the FP64 solve at a fixed outer count and agree with
+    each other to the level of that summation-order difference."""
+    dims = (31, 25, 21)
+    A = sstep.Stencil(*dims, points=7)
+    xt, b = I.poisson_problem(dims, 7)
+    K = 10
+    kw = dict(s=s, sweeps=30, rtol=0.0, max_outer=K, lambda_max=1.95)
+    xs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("SSTEP_FP32_UPD_TWO_PASS", flag)
+        x, info, _ = solve(A, b, precision="fp32_rr", **kw)
+        assert info.outer_iters == K
+        xs.append(x)
+    xd, idd, _ = solve(A, b, **kw)
+    for x in xs:
+        assert relerr(x, xd) <= 1e-4
+    assert relerr(xs[0], xs[1]) <= 1e-5
+
+
 def test_mixed_rejects_unsupported():
     A = sstep.Stencil(10, 10, 10, 7)
     for kw in (dict(s=9), dict(algo="onesync"), dict(gram="cholesky")):
