@@ -558,96 +558,106 @@ constexpr int TX2 = 32, TY2 = 8;
 constexpr int kRow2 = 2 * TX2 + 4;  // doubles per staged row: 2 pad | 64 values | 2 pad
 
 template <bool POISSON, int EPI>
-__global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs e, int zc) {
+__global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs e, int gx,
+                                                           int64_t items) {
   if (skip<EPI>(e)) return;
   __shared__ __align__(16) double sm[2][TY2 + 2][kRow2];
   const int tx = threadIdx.x % TX2, ty = threadIdx.x / TX2;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const int x0 = (blockIdx.x * TX2 + tx) * 2, y = blockIdx.y * TY2 + ty;
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
   const int64_t pxy = (int64_t)nx * ny;
-  const bool in = x0 < nx && y < ny;  // nx even: both points inside
-  const int64_t col = (int64_t)y * nx + x0;
-  const int hy = ty == 0 ? -1 : (ty == TY2 - 1 ? 1 : 0);
-  const bool hyok = hy != 0 && x0 < nx && y + hy >= 0 && y + hy < ny;
-  const int64_t hycol = col + (int64_t)hy * nx;
-  const int hx = tx == 0 ? -1 : (tx == TX2 - 1 ? 2 : 0);
-  const bool hxok = hx != 0 && y < ny && x0 + hx >= 0 && x0 + hx < nx;
-  const int64_t hxcol = col + hx;
   const double2 zero2 = make_double2(0.0, 0.0);
-  auto ld2 = [&](int64_t c, int zz, bool ok) -> double2 {
-    if (!ok || zz < 0 || zz >= nz) return zero2;
-    return __ldg(reinterpret_cast<const double2*>(e.u + c + (int64_t)zz * pxy));
-  };
-  auto ld1 = [&](int64_t c, int zz, bool ok) -> double {
-    if (!ok || zz < 0 || zz >= nz) return 0.0;
-    return __ldg(e.u + c + (int64_t)zz * pxy);
-  };
-  double2 ub = ld2(col, z0 - 1, in), uc = ld2(col, z0, in), ua = ld2(col, z0 + 1, in);
-  double2 hyv = ld2(hycol, z0, hyok);
-  double hxv = ld1(hxcol, z0, hxok);
+  // this CTA's share of the (tile, z plane) items in tile-major order: one launch wave of
+  // CTAs with equal shares (to a plane), marched as one or more z segments of whole tiles
+  const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
   int set = 0;
-  for (int z = z0; z < z1; ++z) {
-    double (*P)[kRow2] = sm[set];
-    *reinterpret_cast<double2*>(&P[ty + 1][2 + 2 * tx]) = uc;
-    if (hy) *reinterpret_cast<double2*>(&P[ty + 1 + hy][2 + 2 * tx]) = hyv;
-    if (hx < 0) P[ty + 1][1] = hxv;
-    if (hx > 0) P[ty + 1][2 + 2 * TX2] = hxv;
-    const double2 nz2 = ld2(col, z + 2, in);
-    const double2 nhy = ld2(hycol, z + 1, hyok);
-    const double nhx = ld1(hxcol, z + 1, hxok);
-    __syncthreads();
-    if (in) {
-      const double2 ym = *reinterpret_cast<const double2*>(&P[ty][2 + 2 * tx]);
-      const double2 yp = *reinterpret_cast<const double2*>(&P[ty + 2][2 + 2 * tx]);
-      const double xl = P[ty + 1][1 + 2 * tx], xr = P[ty + 1][4 + 2 * tx];
-      const double xm[2] = {xl, uc.x}, xp[2] = {uc.y, xr};
-      const double c[2] = {uc.x, uc.y}, dn[2] = {ub.x, ub.y}, up[2] = {ua.x, ua.y};
-      const double yM[2] = {ym.x, ym.y}, yP[2] = {yp.x, yp.y};
-      double av[2], cv[2];
+  for (int64_t it = it0; it < it1;) {
+    const int64_t tile = it / nz;
+    const int z0 = (int)(it % nz);
+    const int z1 = (int)std::min<int64_t>(nz, z0 + (it1 - it));
+    it += z1 - z0;
+    const int bx = (int)(tile % gx), by = (int)(tile / gx);
+    const int x0 = (bx * TX2 + tx) * 2, y = by * TY2 + ty;
+    const bool in = x0 < nx && y < ny;  // nx even: both points inside
+    const int64_t col = (int64_t)y * nx + x0;
+    const int hy = ty == 0 ? -1 : (ty == TY2 - 1 ? 1 : 0);
+    const bool hyok = hy != 0 && x0 < nx && y + hy >= 0 && y + hy < ny;
+    const int64_t hycol = col + (int64_t)hy * nx;
+    const int hx = tx == 0 ? -1 : (tx == TX2 - 1 ? 2 : 0);
+    const bool hxok = hx != 0 && y < ny && x0 + hx >= 0 && x0 + hx < nx;
+    const int64_t hxcol = col + hx;
+    auto ld2 = [&](int64_t c, int zz, bool ok) -> double2 {
+      if (!ok || zz < 0 || zz >= nz) return zero2;
+      return __ldg(reinterpret_cast<const double2*>(e.u + c + (int64_t)zz * pxy));
+    };
+    auto ld1 = [&](int64_t c, int zz, bool ok) -> double {
+      if (!ok || zz < 0 || zz >= nz) return 0.0;
+      return __ldg(e.u + c + (int64_t)zz * pxy);
+    };
+    double2 ub = ld2(col, z0 - 1, in), uc = ld2(col, z0, in), ua = ld2(col, z0 + 1, in);
+    double2 hyv = ld2(hycol, z0, hyok);
+    double hxv = ld1(hxcol, z0, hxok);
+    for (int z = z0; z < z1; ++z) {
+      double (*P)[kRow2] = sm[set];
+      *reinterpret_cast<double2*>(&P[ty + 1][2 + 2 * tx]) = uc;
+      if (hy) *reinterpret_cast<double2*>(&P[ty + 1 + hy][2 + 2 * tx]) = hyv;
+      if (hx < 0) P[ty + 1][1] = hxv;
+      if (hx > 0) P[ty + 1][2 + 2 * TX2] = hxv;
+      const double2 nz2 = ld2(col, z + 2, in);
+      const double2 nhy = ld2(hycol, z + 1, hyok);
+      const double nhx = ld1(hxcol, z + 1, hxok);
+      __syncthreads();
+      if (in) {
+        const double2 ym = *reinterpret_cast<const double2*>(&P[ty][2 + 2 * tx]);
+        const double2 yp = *reinterpret_cast<const double2*>(&P[ty + 2][2 + 2 * tx]);
+        const double xl = P[ty + 1][1 + 2 * tx], xr = P[ty + 1][4 + 2 * tx];
+        const double xm[2] = {xl, uc.x}, xp[2] = {uc.y, xr};
+        const double c[2] = {uc.x, uc.y}, dn[2] = {ub.x, ub.y}, up[2] = {ua.x, ua.y};
+        const double yM[2] = {ym.x, ym.y}, yP[2] = {yp.x, yp.y};
+        double av[2], cv[2];
 #pragma unroll
-      for (int l = 0; l < 2; ++l) {
-        double a;
-        if constexpr (POISSON) {
-          double s = (xm[l] + xp[l]) + (yM[l] + yP[l]);
-          s += dn[l] + up[l];
-          a = fma(op.wc, c[l], -s);
-        } else {  // weights in the order -z, -y, -x, centre, +x, +y, +z
-          a = op.w[0] * dn[l];
-          a = fma(op.w[1], yM[l], a);
-          a = fma(op.w[2], xm[l], a);
-          a = fma(op.w[3], c[l], a);
-          a = fma(op.w[4], xp[l], a);
-          a = fma(op.w[5], yP[l], a);
-          a = fma(op.w[6], up[l], a);
+        for (int l = 0; l < 2; ++l) {
+          double a;
+          if constexpr (POISSON) {
+            double s = (xm[l] + xp[l]) + (yM[l] + yP[l]);
+            s += dn[l] + up[l];
+            a = fma(op.wc, c[l], -s);
+          } else {  // weights in the order -z, -y, -x, centre, +x, +y, +z
+            a = op.w[0] * dn[l];
+            a = fma(op.w[1], yM[l], a);
+            a = fma(op.w[2], xm[l], a);
+            a = fma(op.w[3], c[l], a);
+            a = fma(op.w[4], xp[l], a);
+            a = fma(op.w[5], yP[l], a);
+            a = fma(op.w[6], up[l], a);
+          }
+          double cc = c[l];
+          if constexpr (EPI == EP_MPK_FIRST) {  // uniform M^{-1}: A (d r) = d (A r)
+            a *= e.M.dinv_u;
+            cc *= e.M.dinv_u;
+          }
+          av[l] = a;
+          cv[l] = cc;
         }
-        double cc = c[l];
-        if constexpr (EPI == EP_MPK_FIRST) {  // uniform M^{-1}: A (d r) = d (A r)
-          a *= e.M.dinv_u;
-          cc *= e.M.dinv_u;
+        const int64_t i = (int64_t)z * pxy + col;
+        if constexpr (EPI == EP_MPK_FIRST) *reinterpret_cast<double2*>(e.z1 + i) = make_double2(cv[0], cv[1]);
+        *reinterpret_cast<double2*>(e.y + i) = make_double2(av[0], av[1]);
+        if (e.znext) {
+          double2 zp = zero2;
+          if (e.zprev) zp = __ldg(reinterpret_cast<const double2*>(e.zprev + i));
+          const double t0 = e.c3 == 1.0 ? -zp.x : -e.c3 * zp.x;
+          const double t1 = e.c3 == 1.0 ? -zp.y : -e.c3 * zp.y;
+          *reinterpret_cast<double2*>(e.znext + i) =
+              make_double2(fma(e.a1u, av[0], fma(-e.c2, cv[0], t0)),
+                           fma(e.a1u, av[1], fma(-e.c2, cv[1], t1)));
         }
-        av[l] = a;
-        cv[l] = cc;
       }
-      const int64_t i = (int64_t)z * pxy + col;
-      if constexpr (EPI == EP_MPK_FIRST) *reinterpret_cast<double2*>(e.z1 + i) = make_double2(cv[0], cv[1]);
-      *reinterpret_cast<double2*>(e.y + i) = make_double2(av[0], av[1]);
-      if (e.znext) {
-        double2 zp = zero2;
-        if (e.zprev) zp = __ldg(reinterpret_cast<const double2*>(e.zprev + i));
-        const double t0 = e.c3 == 1.0 ? -zp.x : -e.c3 * zp.x;
-        const double t1 = e.c3 == 1.0 ? -zp.y : -e.c3 * zp.y;
-        *reinterpret_cast<double2*>(e.znext + i) =
-            make_double2(fma(e.a1u, av[0], fma(-e.c2, cv[0], t0)),
-                         fma(e.a1u, av[1], fma(-e.c2, cv[1], t1)));
-      }
+      ub = uc;
+      uc = ua;
+      ua = nz2;
+      hyv = nhy;
+      hxv = nhx;
+      set ^= 1;
     }
-    ub = uc;
-    uc = ua;
-    ua = nz2;
-    hyv = nhy;
-    hxv = nhx;
-    set ^= 1;
   }
 }
 
@@ -658,13 +668,26 @@ cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t s
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };  // null passes
     const bool aligned = a16(e.u) && a16(e.y) && a16(e.znext) && a16(e.zprev) && a16(e.z1);
     if (op.points == 7 && op.nx % 2 == 0 && e.M.dinv == nullptr && aligned) {
+      // one wave: the SM count times the resident CTAs per SM, each with an equal share of
+      // the (tile, plane) items (at least 8 planes per CTA)
       const int gx = (op.nx + 2 * TX2 - 1) / (2 * TX2), gy = (op.ny + TY2 - 1) / TY2;
-      int64_t gz = std::max<int64_t>(1, (int64_t)num_sms() * 8 / std::max(1, gx * gy));
-      gz = std::min<int64_t>(gz, std::max(1, op.nz / 8));
-      const int zc = (int)((op.nz + gz - 1) / gz);
-      const dim3 grid(gx, gy, (op.nz + zc - 1) / zc);
-      if (op.poisson) k_stencil7_x2<true, EPI><<<grid, TX2 * TY2, 0, st>>>(op, e, zc);
-      else k_stencil7_x2<false, EPI><<<grid, TX2 * TY2, 0, st>>>(op, e, zc);
+      const int64_t items = (int64_t)gx * gy * op.nz;
+      auto wave = [&](auto kernel, int& per_sm) -> int {
+        if (!per_sm &&
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, TX2 * TY2, 0) !=
+                 cudaSuccess ||
+             per_sm < 1))
+          per_sm = 1;
+        return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, items / 8));
+      };
+      static int occ_p = 0, occ_g = 0;
+      if (op.poisson) {
+        const int ctas = wave(k_stencil7_x2<true, EPI>, occ_p);
+        k_stencil7_x2<true, EPI><<<ctas, TX2 * TY2, 0, st>>>(op, e, gx, items);
+      } else {
+        const int ctas = wave(k_stencil7_x2<false, EPI>, occ_g);
+        k_stencil7_x2<false, EPI><<<ctas, TX2 * TY2, 0, st>>>(op, e, gx, items);
+      }
       return cudaGetLastError();
     }
   }
