@@ -818,7 +818,7 @@ def main():
             fph = E.profile(bd, iters=5)
             F = 4.0 * n
             fb = {"mpk_step": (4 * (s_ - 1) + 2) * F / s_, "gram_b2": 2 * s_ * F,
-                  "update_w": (6 * s_ + 2) * F, "update_xr": (2 * s_ + 8) * F}
+                  "update_w": (6 * s_ + 6) * F, "update_xr": (s_ + 4) * F}
             fms = {"mpk_step": fph[0] / s_, "gram_b2": fph[1], "update_w": fph[2], "update_xr": fph[3]}
             hbm_, _ = hbm_peak()
             extra[key]["per_kernel"] = {

@@ -351,10 +351,17 @@ sstep_status run_mpk_f32(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
+// x += xhi + xlo (increments zeroed) after the pending step Q alpha of the FP32 s-step form.
+cudaError_t fold_x(sstep_ctx* h) {
+  const bool pcg = h->o.algo == SSTEP_ALGO_PCG;
+  return launch_fold_x(h->x, h->xhi, h->xlo, h->n, h->ctrl, pcg ? nullptr : h->Qf, h->ldf,
+                       pcg ? 0 : h->s, h->st);
+}
+
 // Residual replacement in FP64: x += xhi + xlo (increments zeroed), r = b - A x split into
 // rhi + rlo, ||r||^2 and the stop test on it.
 sstep_status run_rr(sstep_ctx* h) {
-  CK(launch_fold_x(h->x, h->xhi, h->xlo, h->n, h->ctrl, h->st));
+  CK(fold_x(h));
   EpiArgs e = epi_base(h, EP_RR);
   e.u = h->x;
   e.y = nullptr;
@@ -1051,8 +1058,8 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   }
   CK(cudaStreamSynchronize(h->st));
   if (st != SSTEP_OK) return st;
-  if (h->mixed) {  // fold the last increments into the FP64 solution
-    CK(launch_fold_x(h->x, h->xhi, h->xlo, n, h->ctrl, h->st));
+  if (h->mixed) {  // fold the last increments (and the pending step) into the FP64 solution
+    CK(fold_x(h));
     ++h->nlaunch;
   }
   CKS(read_ctrl(h));

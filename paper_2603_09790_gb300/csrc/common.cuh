@@ -62,6 +62,9 @@ struct Ctrl {
   double W[kMaxS * kMaxS];       // W_k used for alpha_k (and for beta_k)
   double P[64];                  // FGS operator P_nu(W_k) (solver SSTEP_GRAM_FGS_OPERATOR, s <= 8)
   int p_valid;                   // 1 once P holds the operator of the current W
+  // FP32-basis s-step form: 1 while x still lacks the last step's Q_k alpha_k; the direction
+  // update that next reads Q_k adds it, or the fold before a residual replacement does
+  int x_pending;
   double sums[kMaxEntries];      // reduced Gram sums of the last reduction
   unsigned int ticket[kNumTickets];
   // the reduced systems of every outer iteration k <= red_max (Section 3.3 experiments), kept
@@ -634,7 +637,11 @@ cudaError_t launch_sum_groups(const double* in, int groups, int per, int w, doub
 cudaError_t launch_pattern_grad(const CsrOp& A, const double* lam, const double* x, double* g,
                                 double scale, int accumulate, cudaStream_t st);
 // x64 += xhi + xlo; xhi = xlo = 0 (before a residual replacement and at the end)
-cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl, cudaStream_t st);
+// x64 += xhi + xlo (increments zeroed), after adding the pending step Q alpha (Q: the s FP32
+// columns at Q with leading dimension ld, alpha = ctrl->alpha) to the increments when
+// ctrl->x_pending; clears ctrl->x_pending.  Q == nullptr: no pending step (FP32 PCG).
+cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl,
+                          const float* Q, int64_t ld, int s, cudaStream_t st);
 
 struct GramArgs {
   int64_t n;

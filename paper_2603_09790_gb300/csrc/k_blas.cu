@@ -510,6 +510,8 @@ __device__ void gram_tail(int mode, Ctrl* c, const double* sums, double* sh,
   const int tid = threadIdx.x;
   bool ok = true;
   if (mode == GM_ONESYNC_FIRST || mode == GM_LITERAL_W) {
+    // the direction update before this reduction added the pending x step (FP32 forms)
+    if (tid == 0) c->x_pending = 0;
     // W = V^T AV (V = Z_0 or Q_k), b1 = V^T r;  alpha = FGS(W, b1)       (step system)
     for (int e = tid; e < s * s; e += blockDim.x) {
       const int i = e % s, j = e / s;
@@ -967,6 +969,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_b2f(MixedArgs a) {
   gram_tail(GM_LITERAL_B2, a.ctrl, buf, buf + K, pre);
 }
 
+// (xh, xl) += sum_j v_j (alh_j + all_j) in double-float, the operations of the x/r update's
+// former x part: the product with the FP32 high part of each step length exactly, its low
+// part by one FMA, then one renormalised addition.
+template <int NC>
+__device__ __forceinline__ void df_axpy_step(const float (&v)[NC], const float* alh,
+                                             const float* all, int nc, float& xh, float& xl) {
+  float dxh = 0.0f, dxl = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    if (j < nc) {
+      df_acc_prod(dxh, dxl, v[j], alh[j]);
+      dxl = fmaf(v[j], all[j], dxl);
+    }
+  }
+  df_add(xh, xl, dxh, dxl);
+}
+
+// The pending x step of the FP32 s-step form (ctrl->x_pending, alpha split into FP32 high and
+// low parts) in shared memory for a direction-update kernel; executed by the whole CTA, the
+// caller synchronises.
+template <int S>
+struct PendingX {
+  float alh[S], all[S];
+  int on;
+  __device__ void load(const Ctrl* c) {
+    if (threadIdx.x == 0) on = c->x_pending;
+    if (threadIdx.x < S) {
+      const double v = c->alpha[threadIdx.x];
+      const float h = __double2float_rn(v);
+      alh[threadIdx.x] = h;
+      all[threadIdx.x] = __double2float_rn(v - (double)h);
+    }
+  }
+};
+
 // Direction-block update in FP32 (FIRST: Q = Z, AQ = AZ) fused with W = Q^T AQ, b1 = Q^T r
 // accumulated in double-float (r = rhi + rlo), then alpha = FGS(W, b1) in the last CTA.
 template <int S, bool FIRST>
@@ -976,8 +1013,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_upd_gramf(MixedArgs a) {
   constexpr int K = NW + S;
   __shared__ float sb[S * S];
   __shared__ double buf[kTiledSmem];
-  if (!FIRST)
+  __shared__ PendingX<S> px;  // x += Q alpha of the previous step, while Q is read
+  if (!FIRST) {
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+    px.load(a.ctrl);
+  }
   __syncthreads();
   float hi[K], lo[K];
 #pragma unroll
@@ -1012,6 +1052,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_upd_gramf(MixedArgs a) {
       for (int l = 0; l < S; ++l) {
         qo4[l] = reinterpret_cast<const float4*>(a.Q + l * ld)[v];
         ao4[l] = reinterpret_cast<const float4*>(a.AQ + l * ld)[v];
+      }
+      if (px.on) {  // x += Q_old alpha_prev (the previous step's deferred x update)
+        float4 xh = reinterpret_cast<float4*>(a.xhi)[v], xl = reinterpret_cast<float4*>(a.xlo)[v];
+        float q[S];
+#define SSTEP_PX_LANE(c)                                   \
+        for (int l = 0; l < S; ++l) q[l] = qo4[l].c;       \
+        df_axpy_step<S>(q, px.alh, px.all, S, xh.c, xl.c);
+        SSTEP_PX_LANE(x)
+        SSTEP_PX_LANE(y)
+        SSTEP_PX_LANE(z)
+        SSTEP_PX_LANE(w)
+#undef SSTEP_PX_LANE
+        reinterpret_cast<float4*>(a.xhi)[v] = xh;
+        reinterpret_cast<float4*>(a.xlo)[v] = xl;
       }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1068,6 +1122,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_upd_gramf(MixedArgs a) {
         qo[l] = a.Q[l * ld + p];
         ao[l] = a.AQ[l * ld + p];
       }
+      if (px.on) {  // x += Q_old alpha_prev (deferred)
+        float h = a.xhi[p], l = a.xlo[p];
+        df_axpy_step<S>(qo, px.alh, px.all, S, h, l);
+        a.xhi[p] = h;
+        a.xlo[p] = l;
+      }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         float vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
@@ -1094,8 +1154,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_upd_gramf(MixedArgs a) {
   gram_tail(GM_LITERAL_W, a.ctrl, sums, sums + S * S + S);
 }
 
-// x += Q alpha, r -= AQ alpha and the stop test, with x, r kept as FP32 (hi, lo) increments between
-// residual replacements, ||r||^2 in double-float, stop test in the last CTA.
+// r -= AQ alpha and the stop test, with r kept as an FP32 (hi, lo) pair between residual
+// replacements, ||r||^2 in double-float, stop test in the last CTA.  The step's x += Q alpha is
+// left pending (ctrl->x_pending): the next direction update, which reads Q anyway, adds it to
+// the FP32 (hi, lo) increments of x, or the fold before a residual replacement does.
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   if (a.ctrl->done) return;
@@ -1111,18 +1173,15 @@ __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   float rrh[1] = {0.0f}, rrl[1] = {0.0f};
   const int64_t ld = a.ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // one point: x += Q alpha, r -= AQ alpha in double-float, ||r||^2 accumulated
-  auto point = [&](const float (&q)[S], const float (&aq)[S], float& xh, float& xl, float& rh,
-                   float& rl) {
-    float dxh = 0.0f, dxl = 0.0f, drh = 0.0f, drl = 0.0f;
+  // one point: r -= AQ alpha in double-float, ||r||^2 accumulated (x += Q alpha is deferred to
+  // the next pass that reads Q: the direction update, or the fold before a replacement)
+  auto point = [&](const float (&aq)[S], float& rh, float& rl) {
+    float drh = 0.0f, drl = 0.0f;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      df_acc_prod(dxh, dxl, q[j], ah[j]);
-      dxl = fmaf(q[j], al[j], dxl);
       df_acc_prod(drh, drl, aq[j], ah[j]);
       drl = fmaf(aq[j], al[j], drl);
     }
-    df_add(xh, xl, dxh, dxl);
     df_add(rh, rl, -drh, -drl);
     df_acc_prod(rrh[0], rrl[0], rh, rh);
     rrl[0] = fmaf(2.0f * rh, rl, rrl[0]);
@@ -1132,47 +1191,34 @@ __global__ void __launch_bounds__(kThreads) k_update_xrf(MixedArgs a) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n4 = a.n >> 2;
   for (int64_t v = gid; v < n4; v += stride) {
-    float4 q4[S], aq4[S];
+    float4 aq4[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-      q4[j] = __ldg(reinterpret_cast<const float4*>(a.Q + j * ld) + v);
-      aq4[j] = __ldg(reinterpret_cast<const float4*>(a.AQ + j * ld) + v);
-    }
-    float4 xh = reinterpret_cast<float4*>(a.xhi)[v], xl = reinterpret_cast<float4*>(a.xlo)[v];
+    for (int j = 0; j < S; ++j) aq4[j] = __ldg(reinterpret_cast<const float4*>(a.AQ + j * ld) + v);
     float4 rh = reinterpret_cast<float4*>(a.rhi)[v], rl = reinterpret_cast<float4*>(a.rlo)[v];
-    float q[S], aq[S];
+    float aq[S];
 #define SSTEP_XR_LANE(c)                    \
-    for (int j = 0; j < S; ++j) {           \
-      q[j] = q4[j].c;                       \
-      aq[j] = aq4[j].c;                     \
-    }                                       \
-    point(q, aq, xh.c, xl.c, rh.c, rl.c);
+    for (int j = 0; j < S; ++j) aq[j] = aq4[j].c; \
+    point(aq, rh.c, rl.c);
     SSTEP_XR_LANE(x)
     SSTEP_XR_LANE(y)
     SSTEP_XR_LANE(z)
     SSTEP_XR_LANE(w)
 #undef SSTEP_XR_LANE
-    reinterpret_cast<float4*>(a.xhi)[v] = xh;
-    reinterpret_cast<float4*>(a.xlo)[v] = xl;
     reinterpret_cast<float4*>(a.rhi)[v] = rh;
     reinterpret_cast<float4*>(a.rlo)[v] = rl;
   }
   for (int64_t p = 4 * n4 + gid; p < a.n; p += stride) {  // the last n mod 4 points
-    float q[S], aq[S];
+    float aq[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-      q[j] = __ldg(a.Q + j * ld + p);
-      aq[j] = __ldg(a.AQ + j * ld + p);
-    }
-    float xh = a.xhi[p], xl = a.xlo[p], rh = a.rhi[p], rl = a.rlo[p];
-    point(q, aq, xh, xl, rh, rl);
-    a.xhi[p] = xh;
-    a.xlo[p] = xl;
+    for (int j = 0; j < S; ++j) aq[j] = __ldg(a.AQ + j * ld + p);
+    float rh = a.rhi[p], rl = a.rlo[p];
+    point(aq, rh, rl);
     a.rhi[p] = rh;
     a.rlo[p] = rl;
   }
   if (!df_grid_sums<1>(rrh, rrl, buf, a.partials, &a.ctrl->ticket[TK_UPDATE])) return;
   if (threadIdx.x == 0) {
+    a.ctrl->x_pending = 1;  // x lacks Q_k alpha_k
     stop_test(a.ctrl, buf[0]);
     if (a.hist) a.hist[a.ctrl->iters] = sqrt(buf[0] / a.ctrl->nb2);
   }
@@ -1184,8 +1230,11 @@ template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
   if (a.ctrl->done) return;
   __shared__ float sb[S * S];
-  if (!FIRST)
+  __shared__ PendingX<S> px;  // x += Q alpha of the previous step, while Q is read
+  if (!FIRST) {
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+    px.load(a.ctrl);
+  }
   __syncthreads();
   const int64_t ld = a.ld;  // a multiple of 64: every column is 16-byte aligned
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1207,6 +1256,20 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
       for (int l = 0; l < S; ++l) {
         qo[l] = reinterpret_cast<const float4*>(a.Q + l * ld)[v];
         ao[l] = reinterpret_cast<const float4*>(a.AQ + l * ld)[v];
+      }
+      if (px.on) {  // x += Q_old alpha_prev (deferred)
+        float4 xh = reinterpret_cast<float4*>(a.xhi)[v], xl = reinterpret_cast<float4*>(a.xlo)[v];
+        float q[S];
+#define SSTEP_PX_LANE(c)                                   \
+        for (int l = 0; l < S; ++l) q[l] = qo[l].c;        \
+        df_axpy_step<S>(q, px.alh, px.all, S, xh.c, xl.c);
+        SSTEP_PX_LANE(x)
+        SSTEP_PX_LANE(y)
+        SSTEP_PX_LANE(z)
+        SSTEP_PX_LANE(w)
+#undef SSTEP_PX_LANE
+        reinterpret_cast<float4*>(a.xhi)[v] = xh;
+        reinterpret_cast<float4*>(a.xlo)[v] = xl;
       }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1243,6 +1306,12 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
         qo[l] = a.Q[l * ld + p];
         ao[l] = a.AQ[l * ld + p];
       }
+      if (px.on) {  // x += Q_old alpha_prev (deferred)
+        float h = a.xhi[p], l = a.xlo[p];
+        df_axpy_step<S>(qo, px.alh, px.all, S, h, l);
+        a.xhi[p] = h;
+        a.xlo[p] = l;
+      }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         float vq = __ldg(a.Z + j * ld + p), va = __ldg(a.AZ + j * ld + p);
@@ -1270,8 +1339,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramwf(MixedArgs a) {
   constexpr int K = NW + S;
   __shared__ float sb[S * S];
   __shared__ double buf[kTiledSmem];
-  if (!FIRST)
+  __shared__ PendingX<S> px;  // x += Q alpha of the previous step, while Q is read
+  if (!FIRST) {
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = (float)a.ctrl->beta[e];
+    px.load(a.ctrl);
+  }
   __syncthreads();
   float hi[K], lo[K];
 #pragma unroll
@@ -1294,6 +1366,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramwf(MixedArgs a) {
       for (int l = 0; l < S; ++l) {
         qo[l] = reinterpret_cast<const float2*>(a.Q + l * ld)[v];
         ao[l] = reinterpret_cast<const float2*>(a.AQ + l * ld)[v];
+      }
+      if (px.on) {  // x += Q_old alpha_prev (deferred)
+        float2 xh = reinterpret_cast<float2*>(a.xhi)[v], xl = reinterpret_cast<float2*>(a.xlo)[v];
+        float q[S];
+#pragma unroll
+        for (int l = 0; l < S; ++l) q[l] = qo[l].x;
+        df_axpy_step<S>(q, px.alh, px.all, S, xh.x, xl.x);
+#pragma unroll
+        for (int l = 0; l < S; ++l) q[l] = qo[l].y;
+        df_axpy_step<S>(q, px.alh, px.all, S, xh.y, xl.y);
+        reinterpret_cast<float2*>(a.xhi)[v] = xh;
+        reinterpret_cast<float2*>(a.xlo)[v] = xl;
       }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1347,6 +1431,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gramwf(MixedArgs a) {
       for (int l = 0; l < S; ++l) {
         qo[l] = a.Q[l * ld + p];
         ao[l] = a.AQ[l * ld + p];
+      }
+      if (px.on) {  // x += Q_old alpha_prev (deferred)
+        float h = a.xhi[p], l = a.xlo[p];
+        df_axpy_step<S>(qo, px.alh, px.all, S, h, l);
+        a.xhi[p] = h;
+        a.xlo[p] = l;
       }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1482,12 +1572,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_gram_df(GramTilesF g) {
   gram_tail(g.mode, g.ctrl, sums, sums + g.ne);
 }
 
-__global__ void __launch_bounds__(kThreads) k_fold_x(double* x, float* xh, float* xl, int64_t n) {
+// x64 += xh + xl (increments zeroed), the pending step first (launch_fold_x); the last CTA
+// clears the pending flag, which every CTA read at entry.
+__global__ void __launch_bounds__(kThreads) k_fold_x(double* x, float* xh, float* xl, int64_t n,
+                                                    Ctrl* ctrl, const float* Q, int64_t ld,
+                                                    int s) {
+  __shared__ float alh[kOpMaxS], all[kOpMaxS];
+  __shared__ int pend;
+  if (threadIdx.x == 0) pend = ctrl && Q ? ctrl->x_pending : 0;
+  if (threadIdx.x < s && ctrl && Q) {
+    const double v = ctrl->alpha[threadIdx.x];
+    const float h = __double2float_rn(v);
+    alh[threadIdx.x] = h;
+    all[threadIdx.x] = __double2float_rn(v - (double)h);
+  }
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += (double)xh[i] + (double)xl[i];
+    float h = xh[i], l = xl[i];
+    if (pend) {
+      float v[kOpMaxS];
+#pragma unroll
+      for (int j = 0; j < kOpMaxS; ++j) v[j] = j < s ? __ldg(Q + j * ld + i) : 0.0f;
+      df_axpy_step<kOpMaxS>(v, alh, all, s, h, l);
+    }
+    x[i] += (double)h + (double)l;
     xh[i] = 0.0f;
     xl[i] = 0.0f;
+  }
+  if (!ctrl) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctrl->ticket[TK_UPDATE], 1u) == gridDim.x - 1) {
+      ctrl->x_pending = 0;
+      ctrl->ticket[TK_UPDATE] = 0u;
+    }
   }
 }
 
@@ -2173,9 +2293,9 @@ cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
 }
 
 cudaError_t launch_fold_x(double* x64, float* xhi, float* xlo, int64_t n, Ctrl* ctrl,
-                          cudaStream_t st) {
-  (void)ctrl;
-  k_fold_x<<<stream_ctas(n, 4), kThreads, 0, st>>>(x64, xhi, xlo, n);
+                          const float* Q, int64_t ld, int s, cudaStream_t st) {
+  if (Q && (s < 1 || s > kOpMaxS)) return cudaErrorInvalidValue;
+  k_fold_x<<<stream_ctas(n, 4), kThreads, 0, st>>>(x64, xhi, xlo, n, ctrl, Q, ld, s);
   return cudaGetLastError();
 }
 
