@@ -141,9 +141,10 @@ def kernel_work(s, n, points=7, sym_blocks=False):
     """Algorithmic bytes and FP64 flops of each kernel launch (FP64 values, 8 bytes).
 
     A multiply-add counts 2 flops.  Literal form (default): b2 = -Q^T AZ (s^2 products),
-    Q/AQ update fused with W = Q^T AQ (symmetric: its upper triangle, s (s + 1) / 2 products)
-    and b1 = Q^T r (2 s^2 + s (s + 1) / 2 + s multiply-adds), x/r update (2 s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products, or 2 s^2 + 3 s with
-    the symmetric shortcut) and one update pass (2 s^2 + 2 s + 1)."""
+    Q/AQ update fused with W = Q^T AQ (symmetric: its upper triangle, s (s + 1) / 2 products),
+    b1 = Q^T r and the previous step's deferred x += Q alpha (2 s^2 + s (s + 1) / 2 + 2 s
+    multiply-adds), r update (s + 1).  One-reduction form: one Gram pass (4 s^2 + 2 s products,
+    or 2 s^2 + 3 s with the symmetric shortcut) and one update pass (2 s^2 + 2 s + 1)."""
     V = 8.0 * n
     sp_flops = {5: 5, 7: 7, 27: 27}[points]  # Poisson: (points-1) adds + 1 multiply per row
     rec = 4  # z_{q+1} = c1 d (Az) - c2 z_q - z_{q-1}: 2 multiplies + 2 adds
@@ -152,8 +153,11 @@ def kernel_work(s, n, points=7, sym_blocks=False):
     return {
         "mpk_step": {"bytes": mpk_bytes / s, "flops": (sp_flops + rec) * n},
         "gram_b2": {"bytes": 2 * s * V, "flops": 2.0 * s * s * n},
-        "update_w": {"bytes": (6 * s + 1) * V, "flops": 2.0 * (2 * s * s + s * (s + 1) // 2 + s) * n},
-        "update_xr": {"bytes": (2 * s + 4) * V, "flops": (2.0 * (2 * s + 1) + 2) * n},
+        # the update also adds the previous step's x += Q alpha (read and write x, s FMAs); the
+        # r update reads AQ and r and writes r
+        "update_w": {"bytes": (6 * s + 3) * V,
+                     "flops": 2.0 * (2 * s * s + s * (s + 1) // 2 + s + s) * n},
+        "update_xr": {"bytes": (s + 2) * V, "flops": (2.0 * (s + 1) + 2) * n},
         "gram": {"bytes": (4 * s + 1) * V, "flops": 2.0 * ne * n},
         "update": {"bytes": (6 * s + 4) * V, "flops": 2.0 * (2 * s * s + 2 * s + 1) * n},
         "pcg_spmv_dot": {"bytes": 2 * V, "flops": (sp_flops + 2) * n},

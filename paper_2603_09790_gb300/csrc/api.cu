@@ -256,7 +256,7 @@ sstep_status run_update(sstep_ctx* h, int mode) {
   u.x = h->x;
   u.r = h->r;
   u.alpha = h->ctrl->alpha;
-  u.beta = (mode == UM_FIRST || mode == UM_XR) ? nullptr : h->ctrl->beta;
+  u.beta = (mode == UM_FIRST || mode == UM_XR || mode == UM_R) ? nullptr : h->ctrl->beta;
   u.ctrl = h->ctrl;
   u.partials = h->partials;
   u.ticket = &h->ctrl->ticket[TK_UPDATE];
@@ -270,7 +270,7 @@ sstep_status run_update(sstep_ctx* h, int mode) {
 // block: Q <- Z, AQ <- AZ) followed by the step system of Section 2 (W = Q^T AQ, b1 = Q^T r,
 // alpha = FGS(W, b1)).  Fused in one pass for s <= 8.
 sstep_status run_upd_w(sstep_ctx* h, bool first) {
-  UpdGramArgs a{h->n, h->ld, h->Z, h->AZ, h->Q, h->AQ, h->r, h->ctrl, h->partials};
+  UpdGramArgs a{h->n, h->ld, h->Z, h->AZ, h->Q, h->AQ, h->r, h->ctrl, h->partials, h->x};
   cudaError_t e = launch_upd_gram(a, h->s, first, h->st);
   if (e == cudaSuccess) {
     ++h->nlaunch;
@@ -462,7 +462,7 @@ sstep_status outer_iteration(sstep_ctx* h, int algo) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // basis of r^(k+1) (Algorithm 2)
     CKS(run_gram(h, GM_LITERAL_B2));                     // conjugation: b2 = -Q^T AZ, beta
     CKS(run_upd_w(h, false));                            // Q, AQ update, then W, b1, alpha
-    CKS(run_update(h, UM_XR));                           // x/r update and stop test
+    CKS(run_update(h, UM_R));                            // r update, stop test (x: pending)
   } else {
     EpiArgs e = epi_base(h, EP_PCG_AP);
     e.u = h->p;
@@ -1009,7 +1009,7 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
     if (maxit > 0) {
       CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));  // basis of r^(0)
       CKS(run_upd_w(h, true));                            // Q_0 = Z_0; W, b1, alpha
-      CKS(run_update(h, UM_XR));                          // x/r update and stop test
+      CKS(run_update(h, UM_R));                           // r update and stop test
     }
   } else {
     PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, h->hist};
@@ -1060,6 +1060,9 @@ sstep_status solve_impl(sstep_ctx* h, const double* b, double* x, sstep_info* in
   if (st != SSTEP_OK) return st;
   if (h->mixed) {  // fold the last increments (and the pending step) into the FP64 solution
     CK(fold_x(h));
+    ++h->nlaunch;
+  } else if (h->o.algo == SSTEP_ALGO_LITERAL) {  // the step x += Q alpha still pending
+    CK(launch_flush_x(h->x, h->Q, n, h->ld, h->s, h->ctrl, h->st));
     ++h->nlaunch;
   }
   CKS(read_ctrl(h));
@@ -1433,7 +1436,7 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
   } else if (algo == SSTEP_ALGO_LITERAL) {
     CKS(run_mpk(h, h->r, h->Z, h->AZ, h->s, h->ctrl));
     CKS(run_upd_w(h, true));
-    CKS(run_update(h, UM_XR));
+    CKS(run_update(h, UM_R));
   } else {
     PcgArgs a{h->n, h->x, h->r, h->p, h->Ap, h->M, h->ctrl, h->partials, nullptr};
     CK(launch_pcg_init(a, h->st));
@@ -1478,7 +1481,7 @@ sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* m
       cudaEventRecord(ev[2], h->st);
       ok(run_upd_w(h, false));
       cudaEventRecord(ev[3], h->st);
-      ok(run_update(h, UM_XR));
+      ok(run_update(h, UM_R));
     } else {
       EpiArgs e = epi_base(h, EP_PCG_AP);
       e.u = h->p;

@@ -34,7 +34,9 @@ enum UpdMode {
   UM_FIRST = 0,  // Q = Z, AQ = AZ, then x += Q alpha, r -= AQ alpha
   UM_FUSED = 1,  // Q = Z + Q beta, AQ = AZ + AQ beta, then x += Q alpha, r -= AQ alpha
   UM_XR = 2,     // x += Q alpha, r -= AQ alpha only                  (literal form)
-  UM_QAQ = 3     // Q = Z + Q beta, AQ = AZ + AQ beta only            (literal form)
+  UM_QAQ = 3,    // Q = Z + Q beta, AQ = AZ + AQ beta only (literal form), after the pending
+                 // x += Q alpha of the previous step (Ctrl::x_pending)
+  UM_R = 4       // r -= AQ alpha, x's step left pending              (literal form solve)
 };
 
 // Device-resident control block of one solve.  Written only by the last CTA of a reduction
@@ -676,6 +678,7 @@ struct UpdGramArgs {
   const double* r;
   Ctrl* ctrl;
   double* partials;
+  double* x;  // the pending x += Q alpha of the previous step is added here (ctrl->x_pending)
 };
 cudaError_t launch_upd_gram(const UpdGramArgs& a, int s, bool first, cudaStream_t st);
 
@@ -710,6 +713,10 @@ struct UpdArgs {
   double* hist;         // optional ||r||/||b|| history
 };
 cudaError_t launch_update(const UpdArgs& u, cudaStream_t st);
+// x += Q alpha (Q: s FP64 columns with leading dimension ld, alpha = ctrl->alpha) when
+// ctrl->x_pending, which it clears: the step the literal-form solve left pending at its end.
+cudaError_t launch_flush_x(double* x, const double* Q, int64_t n, int64_t ld, int s, Ctrl* ctrl,
+                           cudaStream_t st);
 
 cudaError_t launch_fgs_standalone(int s, const double* W, int nrhs, const double* B, int nu,
                                   int solver, double* X, int* status_dev, cudaStream_t st);

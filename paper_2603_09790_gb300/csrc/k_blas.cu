@@ -818,8 +818,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
   constexpr int K = NW + S;
   __shared__ double sb[S * S];
   __shared__ double buf[kTiledSmem];
-  if (!FIRST)
+  __shared__ double pa[S];  // alpha of the previous step, when its x update is pending
+  __shared__ int pend;
+  if (!FIRST) {
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = a.ctrl->beta[e];
+    if (threadIdx.x < S) pa[threadIdx.x] = a.ctrl->alpha[threadIdx.x];
+    if (threadIdx.x == 0) pend = a.x ? a.ctrl->x_pending : 0;
+  }
   __syncthreads();
   double acc[K];
 #pragma unroll
@@ -840,6 +845,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_upd_gram(UpdGramArgs a) {
       for (int l = 0; l < S; ++l) {
         qo[l] = a.Q[l * ld + p];
         ao[l] = a.AQ[l * ld + p];
+      }
+      if (pend) {  // x += Q_old alpha_prev: the previous step's x update, deferred to here
+        double dx = 0.0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) dx = fma(qo[l], pa[l], dx);
+        a.x[p] += dx;
       }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1327,11 +1338,11 @@ __global__ void __launch_bounds__(kThreads) k_upd_qaq_f(MixedArgs a) {
   }
 }
 
-// Direction-block update fused with W = Q^T AQ (upper triangle, r30) and b1 = Q^T r for
-// 5 <= s <= 8: the work of k_upd_gramf with two points per thread and trip (8-byte loads and
-// stores) and one CTA per SM, since the s (s + 1) / 2 + s double-float sums take up to 88
-// registers; the two points of a trip share one update of each low part.  The last CTA forms
-// alpha (gram_tail).
+// Direction-block update fused with W = Q^T AQ (its upper triangle: W is symmetric) and
+// b1 = Q^T r for 5 <= s <= 8: the work of k_upd_gramf with two points per thread and trip
+// (8-byte loads and stores) and one CTA per SM, since the s (s + 1) / 2 + s double-float sums
+// take up to 88 registers; the two points of a trip share one update of each low part.  The
+// last CTA forms alpha (gram_tail).
 template <int S, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 1) k_upd_gramwf(MixedArgs a) {
   if (a.ctrl->done) return;
@@ -1617,8 +1628,10 @@ template <int S, int MODE>
 __global__ void __launch_bounds__(kThreads) k_update(UpdArgs u) {
   if (u.ctrl && u.ctrl->done) return;
   __shared__ double sb[S * S], sa[S];
+  __shared__ int pend;  // UM_QAQ: the previous step's x update is pending
   for (int e = threadIdx.x; e < S * S; e += blockDim.x) sb[e] = u.beta ? u.beta[e] : 0.0;
   for (int e = threadIdx.x; e < S; e += blockDim.x) sa[e] = u.alpha ? u.alpha[e] : 0.0;
+  if (threadIdx.x == 0) pend = (MODE == UM_QAQ && u.ctrl && u.x) ? u.ctrl->x_pending : 0;
   __syncthreads();
   double rr = 0.0;
   const int64_t ld = u.ld;
@@ -1640,6 +1653,12 @@ __global__ void __launch_bounds__(kThreads) k_update(UpdArgs u) {
         qo[l] = u.Q[l * ld + i];
         ao[l] = u.AQ[l * ld + i];
       }
+      if (MODE == UM_QAQ && pend) {  // x += Q_old alpha_prev (deferred; sa holds alpha_prev)
+        double dx = 0.0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) dx = fma(qo[l], sa[l], dx);
+        u.x[i] += dx;
+      }
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         double vq = __ldg(u.Z + j * ld + i), va = __ldg(u.AZ + j * ld + i);
@@ -1653,21 +1672,24 @@ __global__ void __launch_bounds__(kThreads) k_update(UpdArgs u) {
         u.Q[j * ld + i] = vq;
         u.AQ[j * ld + i] = va;
       }
-    } else {  // UM_XR
+    } else if constexpr (MODE == UM_XR) {
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         q[j] = u.Q[j * ld + i];
         aq[j] = u.AQ[j * ld + i];
       }
+    } else {  // UM_R: Q is not read; x's step stays pending
+#pragma unroll
+      for (int j = 0; j < S; ++j) aq[j] = u.AQ[j * ld + i];
     }
     if constexpr (MODE != UM_QAQ) {
       double dx = 0.0, dr = 0.0;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        dx = fma(q[j], sa[j], dx);
+        if constexpr (MODE != UM_R) dx = fma(q[j], sa[j], dx);
         dr = fma(aq[j], sa[j], dr);
       }
-      u.x[i] += dx;
+      if constexpr (MODE != UM_R) u.x[i] += dx;
       const double ri = u.r[i] - dr;
       u.r[i] = ri;
       rr = fma(ri, ri, rr);
@@ -1678,6 +1700,7 @@ __global__ void __launch_bounds__(kThreads) k_update(UpdArgs u) {
     if (grid_sum_last<1>(v, u.partials, u.ticket, tot)) {
       if (threadIdx.x == 0) {
         if (u.ctrl) {
+          if (MODE == UM_R) u.ctrl->x_pending = 1;  // x lacks Q_k alpha_k
           stop_test(u.ctrl, tot[0]);
           if (u.hist) u.hist[u.ctrl->iters] = sqrt(tot[0] / u.ctrl->nb2);
         }
@@ -1694,6 +1717,7 @@ cudaError_t launch_update_s(const UpdArgs& u, int grid, cudaStream_t st) {
     case UM_FUSED: k_update<S, UM_FUSED><<<grid, kThreads, 0, st>>>(u); break;
     case UM_XR: k_update<S, UM_XR><<<grid, kThreads, 0, st>>>(u); break;
     case UM_QAQ: k_update<S, UM_QAQ><<<grid, kThreads, 0, st>>>(u); break;
+    case UM_R: k_update<S, UM_R><<<grid, kThreads, 0, st>>>(u); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -2289,6 +2313,42 @@ __global__ void k_d2f(const double* a, float* b, int64_t n) {
 
 cudaError_t launch_d2f(const double* a, float* b, int64_t n, cudaStream_t st) {
   k_d2f<<<stream_ctas(n, 4), kThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+namespace {
+// x += Q alpha when the step is pending (the products in increasing j from 0, the order of the
+// x update it replaces); the last CTA clears the flag every CTA read at entry.
+__global__ void __launch_bounds__(kThreads) k_flush_x(double* x, const double* Q, int64_t n,
+                                                     int64_t ld, int s, Ctrl* ctrl) {
+  __shared__ double sa[kMaxS];
+  __shared__ int pend;
+  if (threadIdx.x == 0) pend = ctrl->x_pending;
+  if (threadIdx.x < s) sa[threadIdx.x] = ctrl->alpha[threadIdx.x];
+  __syncthreads();
+  if (pend) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double dx = 0.0;
+      for (int j = 0; j < s; ++j) dx = fma(Q[j * ld + i], sa[j], dx);
+      x[i] += dx;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctrl->ticket[TK_UPDATE], 1u) == gridDim.x - 1) {
+      ctrl->x_pending = 0;
+      ctrl->ticket[TK_UPDATE] = 0u;
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_flush_x(double* x, const double* Q, int64_t n, int64_t ld, int s, Ctrl* ctrl,
+                           cudaStream_t st) {
+  if (s < 1 || s > kMaxS || !ctrl) return cudaErrorInvalidValue;
+  k_flush_x<<<stream_ctas(n, 4), kThreads, 0, st>>>(x, Q, n, ld, s, ctrl);
   return cudaGetLastError();
 }
 
