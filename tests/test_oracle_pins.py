@@ -78,3 +78,43 @@ def test_onesync_and_literal_share_the_first_steps_at_nu2():
     lit = O.pcgs(A, b, algo="literal", **kw)
     one = O.pcgs(A, b, algo="onesync", **kw)
     assert np.linalg.norm(lit.x - one.x) <= 1e-10 * np.linalg.norm(lit.x)
+
+
+def _doubling_operator(W, nu):
+    """P_nu = (I + M + ... + M^{nu-1}) T with T = (D + L)^{-1}, M = I - T W, formed from the
+    binary digits of nu by doubling (S_2m = S_m + M^m S_m, S_{m+1} = I + M S_m): the operator
+    form of the FGS sweeps, written here in numpy from the sweep's definition."""
+    s = W.shape[0]
+    T = np.linalg.inv(np.tril(W))
+    M = np.eye(s) - T @ W
+    if nu == 0:
+        return np.zeros((s, s))
+    S, Pw = np.eye(s), M.copy()
+    for bit in bin(nu)[3:]:
+        S, Pw = S + Pw @ S, Pw @ Pw
+        if bit == "1":
+            S, Pw = np.eye(s) + M @ S, Pw @ M
+    return S @ T
+
+
+@pytest.mark.parametrize("s,nu", [(1, 1), (2, 2), (3, 3), (4, 5), (4, 30), (5, 7), (8, 30), (8, 1),
+                                  (6, 0), (7, 64)])
+def test_fgs_sweeps_are_a_linear_operator(s, nu):
+    """The reading behind the operator form of the reduced solves: nu FGS sweeps from 0 are a
+    linear map of the right-hand side (the oracle's sweeps on a combination of right-hand sides
+    equal the combination of its sweeps), and that map is P_nu formed by doubling.  A wrong
+    splitting (D + U for D + L), a sweep miscounted in the binary digits or the factor T left
+    out fails it."""
+    rng = np.random.default_rng(50 + 10 * s + nu)
+    Qm, _ = np.linalg.qr(rng.standard_normal((s, s)))
+    W = Qm @ np.diag(np.geomspace(1.0, 40.0, s)) @ Qm.T
+    d = rng.uniform(0.5, 2.0, s)
+    W = (W * np.outer(d, d) + (W * np.outer(d, d)).T) / 2
+    cols = np.column_stack([O.fgs(W, np.eye(s)[:, j], nu) for j in range(s)])
+    b1, b2 = rng.standard_normal(s), rng.standard_normal(s)
+    lin = O.fgs(W, 2.5 * b1 - 0.75 * b2, nu)
+    assert np.allclose(lin, 2.5 * O.fgs(W, b1, nu) - 0.75 * O.fgs(W, b2, nu), rtol=1e-11, atol=1e-12)
+    P = _doubling_operator(W, nu)
+    scale = max(1.0, np.abs(cols).max())
+    assert np.max(np.abs(P - cols)) <= 1e-11 * scale
+    assert np.allclose(P @ b1, O.fgs(W, b1, nu), rtol=1e-10, atol=1e-12 * scale)
