@@ -373,8 +373,8 @@ sstep_status run_rr(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
-// One outer iteration of the mixed literal form (basis, conjugation, direction update, then
-// step system, x/r update and stop test).
+// One outer iteration of the mixed literal form (basis, conjugation, direction update with the
+// previous step's x update, then step system, r update and stop test).
 sstep_status mixed_outer(sstep_ctx* h) {
   const MixedArgs a = mixed_args(h);
   CKS(run_mpk_f32(h));
@@ -385,7 +385,7 @@ sstep_status mixed_outer(sstep_ctx* h) {
   return SSTEP_OK;
 }
 
-// First outer iteration of the mixed form: first block Q_0 = Z_0, step system, x/r update, stop test.
+// First outer iteration of the mixed form: first block Q_0 = Z_0, step system, r update, stop test.
 sstep_status mixed_first(sstep_ctx* h) {
   const MixedArgs a = mixed_args(h);
   CKS(run_mpk_f32(h));
