@@ -388,8 +388,8 @@ SSTEP_API sstep_status sstep_get_history(sstep_handle h, double* relres, int max
  * 5 doubles) receives the averages per outer iteration of 4 phases and their sum:
  * literal form: [MPK (all s steps), b2 = -Q^T AZ with beta, the Q/AQ update fused with W, b1,
  * alpha and the previous step's x += Q alpha, r update with the stop test]; one-reduction form:
- * [MPK, Gram reduction with the reduced
- * solves, block update, 0]; PCG: [A p with p^T A p, x/r/z update, direction update, 0].
+ * [MPK, Gram reduction with the reduced solves, block update, 0]; PCG: [A p with p^T A p,
+ * x/r/z update, direction update, 0].
  * The handle's own x, r and basis blocks are overwritten. */
 SSTEP_API sstep_status sstep_profile(sstep_handle h, const double* b, int iters, double* ms);
 
