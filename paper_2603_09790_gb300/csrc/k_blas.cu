@@ -2272,10 +2272,15 @@ cudaError_t launch_upd_gram_f32(const MixedArgs& a, int s, bool first, cudaStrea
 }
 
 cudaError_t launch_update_xr_f32(const MixedArgs& a, int s, cudaStream_t st) {
-  const int grid = stream_ctas(a.n, 8);  // 2048 threads per SM: latency-bound otherwise
+  // one full wave of resident CTAs (as many as the registers allow, up to 2048 threads per SM:
+  // latency-bound otherwise); the grid-stride loop spreads the points evenly over them
   switch (s) {
-#define CASE(S) \
-  case S: k_update_xrf<S><<<grid, kThreads, 0, st>>>(a); return cudaGetLastError();
+#define CASE(S)                                                                      \
+  case S: {                                                                          \
+    static int occ = 0;                                                              \
+    k_update_xrf<S><<<occ_grid(k_update_xrf<S>, a.n / 4, occ), kThreads, 0, st>>>(a); \
+    return cudaGetLastError();                                                       \
+  }
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
     default: return cudaErrorNotSupported;
@@ -2409,7 +2414,8 @@ cudaError_t launch_fgs_standalone(int s, const double* W, int nrhs, const double
 int pcg_ctas(int64_t n) { return stream_ctas(n, 8); }
 
 cudaError_t launch_pcg_update(const PcgArgs& a, cudaStream_t st) {
-  k_pcg_update<<<pcg_ctas(a.n), kThreads, 0, st>>>(a);
+  static int occ = 0;  // one full wave of resident CTAs
+  k_pcg_update<<<occ_grid(k_pcg_update, a.n, occ), kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_pcg_pdir(const PcgArgs& a, cudaStream_t st) {

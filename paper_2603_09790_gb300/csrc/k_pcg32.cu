@@ -166,7 +166,11 @@ __global__ void __launch_bounds__(kThreads) k_pcgf_pdir(PcgF32Args a, int init) 
   }
 }
 
-int pcgf_ctas(int64_t n) {
+// One full wave of resident CTAs of `kernel` (as many as its registers allow, up to 2048 threads
+// per SM: the vector kernels are latency-bound otherwise), no more CTAs than four points per
+// thread; the grid-stride loops spread the points evenly over them.
+template <typename KernelT>
+int pcgf_ctas(KernelT kernel, int& per_sm, int64_t n) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -174,8 +178,11 @@ int pcgf_ctas(int64_t n) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  // 2048 threads per SM (latency-bound otherwise), no more CTAs than four points per thread
-  const int64_t want = (int64_t)sms * 8;
+  if (!per_sm &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+       per_sm < 1))
+    per_sm = 1;
+  const int64_t want = (int64_t)sms * std::min(per_sm, 8);
   const int64_t need = (n / 4 + kThreads - 1) / kThreads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, need));
 }
@@ -183,17 +190,20 @@ int pcgf_ctas(int64_t n) {
 }  // namespace
 
 cudaError_t launch_pcgf_update(const PcgF32Args& a, cudaStream_t st) {
-  k_pcgf_update<<<pcgf_ctas(a.n), kThreads, 0, st>>>(a);
+  static int occ = 0;
+  k_pcgf_update<<<pcgf_ctas(k_pcgf_update, occ, a.n), kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcgf_rz(const PcgF32Args& a, int init, cudaStream_t st) {
-  k_pcgf_rz<<<pcgf_ctas(a.n), kThreads, 0, st>>>(a, init);
+  static int occ = 0;
+  k_pcgf_rz<<<pcgf_ctas(k_pcgf_rz, occ, a.n), kThreads, 0, st>>>(a, init);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcgf_pdir(const PcgF32Args& a, int init, cudaStream_t st) {
-  k_pcgf_pdir<<<pcgf_ctas(a.n), kThreads, 0, st>>>(a, init);
+  static int occ = 0;
+  k_pcgf_pdir<<<pcgf_ctas(k_pcgf_pdir, occ, a.n), kThreads, 0, st>>>(a, init);
   return cudaGetLastError();
 }
 
