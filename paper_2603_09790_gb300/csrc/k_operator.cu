@@ -566,6 +566,7 @@ __global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs
   const int nx = op.nx, ny = op.ny, nz = op.nz;
   const int64_t pxy = (int64_t)nx * ny;
   const double2 zero2 = make_double2(0.0, 0.0);
+  double red[2] = {0.0, 0.0};  // the reducing epilogues' sums
   // this CTA's share of the (tile, z plane) items in tile-major order: one launch wave of
   // CTAs with equal shares (to a plane), marched as one or more z segments of whole tiles
   const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
@@ -639,16 +640,21 @@ __global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs
           cv[l] = cc;
         }
         const int64_t i = (int64_t)z * pxy + col;
-        if constexpr (EPI == EP_MPK_FIRST) *reinterpret_cast<double2*>(e.z1 + i) = make_double2(cv[0], cv[1]);
-        *reinterpret_cast<double2*>(e.y + i) = make_double2(av[0], av[1]);
-        if (e.znext) {
-          double2 zp = zero2;
-          if (e.zprev) zp = __ldg(reinterpret_cast<const double2*>(e.zprev + i));
-          const double t0 = e.c3 == 1.0 ? -zp.x : -e.c3 * zp.x;
-          const double t1 = e.c3 == 1.0 ? -zp.y : -e.c3 * zp.y;
-          *reinterpret_cast<double2*>(e.znext + i) =
-              make_double2(fma(e.a1u, av[0], fma(-e.c2, cv[0], t0)),
-                           fma(e.a1u, av[1], fma(-e.c2, cv[1], t1)));
+        if constexpr (EPI == EP_MPK || EPI == EP_MPK_FIRST) {
+          if constexpr (EPI == EP_MPK_FIRST) *reinterpret_cast<double2*>(e.z1 + i) = make_double2(cv[0], cv[1]);
+          *reinterpret_cast<double2*>(e.y + i) = make_double2(av[0], av[1]);
+          if (e.znext) {
+            double2 zp = zero2;
+            if (e.zprev) zp = __ldg(reinterpret_cast<const double2*>(e.zprev + i));
+            const double t0 = e.c3 == 1.0 ? -zp.x : -e.c3 * zp.x;
+            const double t1 = e.c3 == 1.0 ? -zp.y : -e.c3 * zp.y;
+            *reinterpret_cast<double2*>(e.znext + i) =
+                make_double2(fma(e.a1u, av[0], fma(-e.c2, cv[0], t0)),
+                             fma(e.a1u, av[1], fma(-e.c2, cv[1], t1)));
+          }
+        } else {  // the other epilogues, point by point (PCG product, residuals)
+          epilogue<EPI>(e, i, av[0], cv[0], red);
+          epilogue<EPI>(e, i + 1, av[1], cv[1], red);
         }
       }
       ub = uc;
@@ -659,15 +665,18 @@ __global__ void __launch_bounds__(TX2 * TY2) k_stencil7_x2(StencilOp op, EpiArgs
       set ^= 1;
     }
   }
+  reduce_and_finish<EPI>(e, red);
 }
 
 template <int EPI, bool SCALE>
 cudaError_t launch_stencil(const StencilOp& op, const EpiArgs& e, cudaStream_t st) {
-  // the middle steps only: with its three outputs the first step ran faster in the scalar kernel
-  if constexpr (EPI == EP_MPK && !SCALE) {
+  // the middle MPK steps (with its three outputs the first step runs faster in the scalar
+  // kernel), the PCG product and the residuals
+  if constexpr ((EPI == EP_MPK || EPI == EP_PCG_AP || EPI == EP_RR || EPI == EP_RESID ||
+                 EPI == EP_TRUERES) && !SCALE) {
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };  // null passes
     const bool aligned = a16(e.u) && a16(e.y) && a16(e.znext) && a16(e.zprev) && a16(e.z1);
-    if (op.points == 7 && op.nx % 2 == 0 && e.M.dinv == nullptr && aligned) {
+    if (op.points == 7 && op.nx % 2 == 0 && (EPI != EP_MPK || e.M.dinv == nullptr) && aligned) {
       // one wave: the SM count times the resident CTAs per SM, each with an equal share of
       // the (tile, plane) items (at least 8 planes per CTA)
       const int gx = (op.nx + 2 * TX2 - 1) / (2 * TX2), gy = (op.ny + TY2 - 1) / TY2;
