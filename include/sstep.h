@@ -61,7 +61,11 @@ enum { SSTEP_MATRIX_CSR = 0, SSTEP_MATRIX_STENCIL = 1, SSTEP_MATRIX_Q1 = 2 };
  *      (row index i + nx*(j + ny*k); Dirichlet neighbours dropped).  points = 5 (2D, nz = 1),
  *      7 or 27 (3D).  weights: NULL for the Poisson weights (diagonal 4 / 6 / 26, neighbours -1),
  *      or `points` host doubles in the order of increasing linear offset (for 7 points:
- *      -z, -y, -x, centre, +x, +y, +z; for 27: dz-major, then dy, then dx).
+ *      -z, -y, -x, centre, +x, +y, +z; for 27: dz-major, then dy, then dx).  In the
+ *      FP32-basis form a 7-point grid with nx a multiple of 4 (nx >= 72, ny >= 18) has its MPK
+ *      steps and its PCG product fed by tensor-memory-accelerator copies;
+ *      SSTEP_STENCIL_TMA=0 in the environment at set-up selects plain loads (the same MPK
+ *      results bit for bit; p^T A p summed over another grid).
  * Q1: matrix-free trilinear (Q1) finite-element diffusion operator (a variable-coefficient
  *      SPD matrix; the method takes any SPD A, Section 1): the nx*ny*nz interior vertices
  *      (row index i + nx*(j + ny*k)) of a grid of (nx+1)*(ny+1)*(nz+1) unit cells, Dirichlet boundary vertices eliminated.  weights: the

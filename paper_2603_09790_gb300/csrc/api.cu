@@ -75,6 +75,7 @@ struct sstep_ctx {
   int64_t ncell = 0;
   double q1_gersh = 0.0;    // Q1 operator: Gershgorin lower bound found at set-up
   Q1TmaMaps* q1tma = nullptr;  // Q1 operator, FP32 path: tensor maps of the basis columns
+  St7TmaMaps* st7tma = nullptr;  // 7-point stencil, FP32 path: tensor maps of r_hi and Z, or p
   double *Z = nullptr, *AZ = nullptr, *Q = nullptr, *AQ = nullptr;
   double *x = nullptr, *r = nullptr, *b = nullptr, *p = nullptr, *Ap = nullptr;
   double* partials = nullptr;
@@ -644,6 +645,7 @@ void destroy(sstep_ctx* h) {
   if (h->batch) batch_free(h->batch);
   if (h->amg) amg_free(h->amg);
   if (h->q1tma) q1_tma_free(h->q1tma);
+  if (h->st7tma) st7_tma_free(h->st7tma);
   if (h->t) cudaFree(h->t);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& g : h->gexec)
@@ -948,6 +950,21 @@ sstep_status setup_impl(const sstep_matrix* A, int nsys, const sstep_precond* M,
       }
     } else if (A->points == 27) {
       return fail(SSTEP_ERR_UNSUPPORTED, "the FP32-basis path takes 27-point operators as CSR");
+    }
+    if (A->kind == SSTEP_MATRIX_STENCIL && A->points == 7) {
+      // the vectors the TMA-fed 7-point steps read: r_hi and the basis columns, or PCG's p
+      std::vector<const float*> cols;
+      if (pcg) {
+        cols.push_back(h->pf);
+      } else {
+        cols.push_back(h->rhi);
+        for (int c = 0; c < s; ++c) cols.push_back(h->Zf + c * lf);
+      }
+      // null (or SSTEP_STENCIL_TMA=0 in the environment): the register-fed kernel serves them
+      const char* tma_env = std::getenv("SSTEP_STENCIL_TMA");
+      if (!(tma_env && tma_env[0] == '0'))
+        h->st7tma = st7_tma_build(h->op.st, cols.data(), (int)cols.size());
+      h->op.st.tma = h->st7tma;
     }
   }
   CK(cudaStreamSynchronize(h->st));

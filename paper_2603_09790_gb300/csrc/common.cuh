@@ -81,11 +81,13 @@ __host__ __device__ constexpr int red_stride_for(int s) { return 3 * s * s + 2 *
 
 // ---------------------------------------------------------------- operator descriptors
 
+struct St7TmaMaps;  // TMA descriptors of the FP32 7-point steps (k_operator.cu)
 struct StencilOp {
   int nx, ny, nz, points;
   int poisson;       // 1: off-diagonal weights all -1 (fast path)
   double w[27];      // weights in order of increasing linear offset
   double wc;         // centre weight
+  const St7TmaMaps* tma;  // FP32 path: tensor maps of the vectors its steps read, or null
 };
 
 struct CsrOp {
@@ -545,6 +547,12 @@ struct MpkF32Args {
   double* partials;
 };
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st);
+// Tensor maps for the TMA-fed FP32 7-point steps: one per vector (cols[c], n floats each) that
+// an MPK or PCG product step reads.  Null when the grid does not allow them (not 7 points, nx
+// not a multiple of 4, nx < 72 or ny < 18) or the driver cannot encode them; the steps then run
+// on plain loads.
+St7TmaMaps* st7_tma_build(const StencilOp& op, const float* const* cols, int ncols);
+void st7_tma_free(St7TmaMaps* m);
 
 // FP32 PCG product step: the last CTA turns the grid's double-float sum p^T (A p) into
 // alpha = r^T z / p^T A p (breakdown when p^T A p is not positive and finite).  Reached by every

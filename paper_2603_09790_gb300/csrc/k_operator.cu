@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "epilogue.cuh"
+#include "tma.cuh"
 
 namespace sstep {
 
@@ -494,6 +495,150 @@ __global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4(StencilOp op, MpkF32Ar
   if constexpr (PAP) pap_finish(e, ph, pl);
 }
 
+// The same FP32 steps (MPK with a uniform M^{-1}, and the PCG product) with the u planes brought
+// in by the tensor-memory accelerator.  A CTA owns the same 64 x 16 tile and z chunk as
+// k_stencil7f4; one thread keeps up to kS7 planes of u in flight, each a 72 x 18 box (x from 4
+// left of the tile, so that the x coordinate stays a multiple of 16 bytes; y from 1 below)
+// that lands on its stage's mbarrier.  The copy zero-fills whatever lies outside the grid: the
+// eliminated Dirichlet boundary.  Plane z reads stages z-1, z, z+1 straight from shared memory,
+// so the depth of the pipeline costs shared memory, not registers (the register-fed kernel held
+// two planes ahead and waited about one memory latency per plane).  The arithmetic is
+// k_stencil7f4's, operation for operation.  Every wait is bounded: a copy that never lands
+// stops the solve with SSTEP_ERR_TIMEOUT instead of hanging.
+constexpr int S7W = 4 * TX4 + 8, S7H = TY4 + 2;  // box: 72 x 18 floats
+constexpr int kS7 = 8;                           // pipeline stages (z planes)
+constexpr int kS7Stage = 1312;                   // floats per stage: 1296 used, 5248 bytes (41 x 128)
+constexpr uint32_t kS7Bytes = S7W * S7H * 4;
+constexpr int kS7MaxCols = kMaxS + 1;
+
+struct __align__(128) St7Smem {
+  float u[kS7][kS7Stage];
+  unsigned long long full[kS7];
+};
+
+template <bool POISSON, bool FIRST, bool PAP = false>
+__global__ void __launch_bounds__(TX4 * TY4) k_stencil7f4_tma(const __grid_constant__ CUtensorMap mu,
+                                                             StencilOp op, MpkF32Args e, int zc) {
+  if (e.ctrl && e.ctrl->done) return;
+  __shared__ St7Smem sh;
+  float ph[1] = {0.0f}, pl[1] = {0.0f};  // PAP: p^T (A p)
+  const int tid = threadIdx.x, tx = tid % TX4, ty = tid / TX4;
+  const int nx = op.nx, ny = op.ny, nz = op.nz;
+  const int bx = blockIdx.x * (4 * TX4), by = blockIdx.y * TY4;
+  const int x0 = bx + 4 * tx, y = by + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const int nzc = z1 - z0;
+  const int np = nzc + 2;  // stage p holds plane z0 - 1 + p
+  const int64_t pxy = (int64_t)nx * ny;
+  const bool in = x0 < nx && y < ny;  // nx % 4 == 0: the whole vector is inside
+  int issued = 0;                     // stages issued (thread 0's count)
+  auto issue = [&](int p) {
+    const uint32_t bar = tma::smem_addr(&sh.full[p % kS7]);
+    tma::mbar_expect_tx(bar, kS7Bytes);
+    tma::load_3d(tma::smem_addr(sh.u[p % kS7]), &mu, bx - 4, by - 1, z0 - 1 + p, bar);
+    issued = p + 1;
+  };
+  if (tid == 0) {
+    for (int i = 0; i < kS7; ++i) tma::mbar_init(tma::smem_addr(&sh.full[i]), 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int p = 0; p < min(kS7, np); ++p) issue(p);
+  int waited = 0;  // stages 0 .. waited-1 have landed
+  bool lost = false;
+  auto wait_stage = [&](int p) {
+    if (!lost && !tma::mbar_wait(tma::smem_addr(&sh.full[p % kS7]), (uint32_t)(p / kS7) & 1u))
+      lost = true;
+    if (!lost) waited = p + 1;
+  };
+  const float wc = e.wc, a1 = e.c1 * e.dinv_u, c2 = e.c2;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const bool zpv_on = in && e.znext && e.zprev;
+  int64_t idx = (int64_t)z0 * pxy + (int64_t)y * nx + x0;
+  float4 zp = zpv_on ? __ldg(reinterpret_cast<const float4*>(e.zprev + idx)) : zero4;
+  const int r = (ty + 1) * S7W + 4 + 4 * tx;  // this thread's first point in a staged plane
+  wait_stage(0);
+  wait_stage(1);
+  bool stop = false;
+  for (int i = 0; i < nzc; ++i) {
+    // z_{q-1} of the next plane, requested a plane ahead
+    const float4 nzp = (zpv_on && i + 1 < nzc)
+                           ? __ldg(reinterpret_cast<const float4*>(e.zprev + idx + pxy))
+                           : zero4;
+    wait_stage(i + 2);
+    // every thread is done with plane i - 1's stage: refill its slot kS7 stages ahead
+    stop = __syncthreads_or(lost);
+    if (stop) break;
+    if (tid == 0 && i >= 1 && i - 1 + kS7 < np) issue(i - 1 + kS7);
+    if (in) {
+      const float* Pm = sh.u[i % kS7];
+      const float* Pc = sh.u[(i + 1) % kS7];
+      const float* Pp = sh.u[(i + 2) % kS7];
+      const float4 uc = *reinterpret_cast<const float4*>(Pc + r);
+      const float4 ym = *reinterpret_cast<const float4*>(Pc + r - S7W);
+      const float4 yp = *reinterpret_cast<const float4*>(Pc + r + S7W);
+      const float4 ub = *reinterpret_cast<const float4*>(Pm + r);
+      const float4 ua = *reinterpret_cast<const float4*>(Pp + r);
+      const float xl = Pc[r - 1], xr = Pc[r + 4];
+      const float xm[4] = {xl, uc.x, uc.y, uc.z}, xp[4] = {uc.y, uc.z, uc.w, xr};
+      const float c[4] = {uc.x, uc.y, uc.z, uc.w}, dn[4] = {ub.x, ub.y, ub.z, ub.w};
+      const float up[4] = {ua.x, ua.y, ua.z, ua.w};
+      const float yM[4] = {ym.x, ym.y, ym.z, ym.w}, yP[4] = {yp.x, yp.y, yp.z, yp.w};
+      float av[4], cv[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        float a;
+        if constexpr (POISSON) {
+          float s = (xm[l] + xp[l]) + (yM[l] + yP[l]);
+          s += dn[l] + up[l];
+          a = fmaf(wc, c[l], -s);
+        } else {  // weights in the order -z, -y, -x, centre, +x, +y, +z
+          a = e.w[0] * dn[l];
+          a = fmaf(e.w[1], yM[l], a);
+          a = fmaf(e.w[2], xm[l], a);
+          a = fmaf(e.w[3], c[l], a);
+          a = fmaf(e.w[4], xp[l], a);
+          a = fmaf(e.w[5], yP[l], a);
+          a = fmaf(e.w[6], up[l], a);
+        }
+        float cc = c[l];
+        if constexpr (FIRST) {  // uniform M^{-1}: A (d r) = d (A r)
+          a *= e.dinv_u;
+          cc *= e.dinv_u;
+        }
+        av[l] = a;
+        cv[l] = cc;
+      }
+      if constexpr (PAP) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) df_acc_prod(ph[0], pl[0], cv[l], av[l]);
+      }
+      if constexpr (FIRST) *reinterpret_cast<float4*>(e.z1 + idx) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+      *reinterpret_cast<float4*>(e.y + idx) = make_float4(av[0], av[1], av[2], av[3]);
+      if (e.znext) {
+        const float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+        float zn[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) zn[l] = fmaf(a1, av[l], fmaf(-c2, cv[l], -zpv[l]));
+        *reinterpret_cast<float4*>(e.znext + idx) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+      }
+    }
+    zp = nzp;
+    idx += pxy;
+  }
+  if (stop && tid == 0) {
+    // let the copies still in flight land before the CTA's shared memory is released
+    for (int p = waited; p < issued; ++p)
+      tma::mbar_wait(tma::smem_addr(&sh.full[p % kS7]), (uint32_t)(p / kS7) & 1u);
+    if (e.ctrl) {
+      e.ctrl->status = SSTEP_ERR_TIMEOUT;
+      e.ctrl->done = 1;
+    }
+  }
+  if constexpr (PAP) pap_finish(e, ph, pl);  // every thread: stop is uniform over the CTA
+}
+
 template <bool FIRST, bool SCALE, bool PAP = false>
 __global__ void __launch_bounds__(kThreads) k_csrf(CsrOp A, MpkF32Args e) {
   if (e.ctrl && e.ctrl->done) return;
@@ -763,12 +908,77 @@ cudaError_t launch_operator(const OpDesc& A, const EpiArgs& e, cudaStream_t st) 
   }
 }
 
+struct St7TmaMaps {
+  int ncols;
+  const float* col[kS7MaxCols];
+  CUtensorMap mu[kS7MaxCols];
+};
+
+namespace {
+
+// The tensor map of the vector u, or null when u has none.
+const CUtensorMap* st7_map(const StencilOp& op, const float* u) {
+  if (!op.tma) return nullptr;
+  for (int c = 0; c < op.tma->ncols; ++c)
+    if (op.tma->col[c] == u) return &op.tma->mu[c];
+  return nullptr;
+}
+
+// One wave of resident CTAs, each marching a z chunk of at least 8 planes: the pipeline fill
+// is paid once per CTA.
+template <bool POISSON, bool FIRST, bool PAP>
+cudaError_t launch_st7_tma(const CUtensorMap* m, const StencilOp& op, const MpkF32Args& e,
+                           cudaStream_t st) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_stencil7f4_tma<POISSON, FIRST, PAP>, TX4 * TY4, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int gx = (op.nx + 4 * TX4 - 1) / (4 * TX4), gy = (op.ny + TY4 - 1) / TY4;
+  int64_t gz = std::max<int64_t>(1, (int64_t)num_sms() * per_sm / std::max(1, gx * gy));
+  gz = std::min<int64_t>(gz, std::max(1, op.nz / 8));
+  const int zc = (int)((op.nz + gz - 1) / gz);
+  const dim3 grid(gx, gy, (op.nz + zc - 1) / zc);
+  k_stencil7f4_tma<POISSON, FIRST, PAP><<<grid, TX4 * TY4, 0, st>>>(*m, op, e, zc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+St7TmaMaps* st7_tma_build(const StencilOp& op, const float* const* cols, int ncols) {
+  // rows must be 16-byte multiples (nx % 4 == 0); boxes no larger than the grid
+  if (op.points != 7 || op.nx % 4 != 0 || op.nx < S7W || op.ny < S7H || ncols < 1 ||
+      ncols > kS7MaxCols)
+    return nullptr;
+  auto* m = new St7TmaMaps{};
+  m->ncols = ncols;
+  bool ok = true;
+  for (int c = 0; ok && c < ncols; ++c) {
+    m->col[c] = cols[c];
+    ok = tma::encode_3d(&m->mu[c], cols[c], (uint64_t)op.nx, (uint64_t)op.ny, (uint64_t)op.nz,
+                        (uint64_t)op.nx, S7W, S7H);
+  }
+  if (!ok) {
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void st7_tma_free(St7TmaMaps* m) { delete m; }
+
 cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st) {
   if (e.pap) {  // FP32 PCG product step: y = A p with p^T A p (no recurrence)
     if (e.first || e.znext || !e.ctrl || !e.partials) return cudaErrorInvalidValue;
     if (A.kind == SSTEP_MATRIX_STENCIL) {
       const StencilOp& op = A.st;
       if (op.points == 27) return cudaErrorNotSupported;
+      if (const CUtensorMap* m = op.points == 7 ? st7_map(op, e.u) : nullptr) {
+        if (op.poisson) return launch_st7_tma<true, false, true>(m, op, e, st);
+        return launch_st7_tma<false, false, true>(m, op, e, st);
+      }
       if (op.points == 7 && op.nx % 4 == 0) {
         const int gx = (op.nx + 4 * TX4 - 1) / (4 * TX4), gy = (op.ny + TY4 - 1) / TY4;
         int64_t gz = std::max<int64_t>(1, (int64_t)num_sms() * 4 / std::max(1, gx * gy));
@@ -802,6 +1012,15 @@ cudaError_t launch_mpk_f32(const OpDesc& A, const MpkF32Args& e, cudaStream_t st
   if (A.kind == SSTEP_MATRIX_STENCIL) {
     const StencilOp& op = A.st;
     if (op.points == 27) return cudaErrorNotSupported;  // the mixed path takes 27 points as CSR
+    const CUtensorMap* m = op.points == 7 && e.dinv == nullptr ? st7_map(op, e.u) : nullptr;
+    if (m) {
+      if (e.first) {
+        if (op.poisson) return launch_st7_tma<true, true, false>(m, op, e, st);
+        return launch_st7_tma<false, true, false>(m, op, e, st);
+      }
+      if (op.poisson) return launch_st7_tma<true, false, false>(m, op, e, st);
+      return launch_st7_tma<false, false, false>(m, op, e, st);
+    }
     if (op.points == 7 && op.nx % 4 == 0 && !scale && e.dinv == nullptr) {
       // vector kernel: about four 256-thread CTAs per SM, z chunks of at least 8 planes
       const int gx = (op.nx + 4 * TX4 - 1) / (4 * TX4), gy = (op.ny + TY4 - 1) / TY4;

@@ -30,6 +30,7 @@
 
 #include "common.cuh"
 #include "epilogue.cuh"
+#include "tma.cuh"
 
 namespace sstep {
 
@@ -304,50 +305,12 @@ constexpr int kNS = 6;             // pipeline stages (z planes)
 constexpr int kUStage = 736;       // floats per u stage: 720 used, 2944 bytes (23 x 128)
 constexpr int kKStage = 640;       // floats per cell stage: 612 used, 2560 bytes (20 x 128)
 constexpr uint32_t kStageBytes = (TUW * TUH + TKW * TKH) * 4;
-constexpr uint32_t kWaitRounds = 1u << 22;  // try_wait rounds before a copy counts as lost
 
 struct __align__(128) TmaSmem {
   float u[kNS][kUStage];
   float k[kNS][kKStage];
   unsigned long long full[kNS];
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitRounds; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
 
 // Register window of one staged plane for a thread's two vertices (x and x + 1): u at rows
 // y-1..y+1 and columns x-1..x+2 (v[dy + 1][c]); the conductivities of cells x..x+2 at rows
@@ -441,15 +404,15 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
   int issued = 0;          // stages issued (thread 0's count)
   auto issue = [&](int p) {
     const int slot = p % kNS;
-    const uint32_t bar = smem_addr(&sh.full[slot]);
-    mbar_expect_tx(bar, kStageBytes);
-    tma_load_3d(smem_addr(sh.u[slot]), &mu, x0 - 4, y0 - 1, z0 - 1 + p, bar);
-    tma_load_3d(smem_addr(sh.k[slot]), &mk, x0, y0, z0 - 1 + p, bar);
+    const uint32_t bar = tma::smem_addr(&sh.full[slot]);
+    tma::mbar_expect_tx(bar, kStageBytes);
+    tma::load_3d(tma::smem_addr(sh.u[slot]), &mu, x0 - 4, y0 - 1, z0 - 1 + p, bar);
+    tma::load_3d(tma::smem_addr(sh.k[slot]), &mk, x0, y0, z0 - 1 + p, bar);
     issued = p + 1;
   };
   if (tid == 0) {
-    for (int i = 0; i < kNS; ++i) mbar_init(smem_addr(&sh.full[i]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < kNS; ++i) tma::mbar_init(tma::smem_addr(&sh.full[i]), 1);
+    tma::mbar_init_fence();
   }
   __syncthreads();
   if (tid == 0)
@@ -459,7 +422,7 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
   int waited = 0;                    // stages 0 .. waited-1 have landed
   bool lost = false;
   auto wait_stage = [&](int slot, uint32_t parity) {
-    if (!lost && !mbar_wait(smem_addr(&sh.full[slot]), parity)) lost = true;
+    if (!lost && !tma::mbar_wait(tma::smem_addr(&sh.full[slot]), parity)) lost = true;
     if (!lost) ++waited;
   };
   UWin2 uw[3];  // stage p in uw[p % 3]
@@ -527,7 +490,7 @@ __global__ void __launch_bounds__(QT, 3) k_q1f_tma(const __grid_constant__ CUten
   if (stop && tid == 0) {
     // let the copies still in flight land before the CTA's shared memory is released
     for (int p = waited; p < issued; ++p)
-      mbar_wait(smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u);
+      tma::mbar_wait(tma::smem_addr(&sh.full[p % kNS]), (uint32_t)(p / kNS) & 1u);
     if (e.ctrl) {
       e.ctrl->status = SSTEP_ERR_TIMEOUT;
       e.ctrl->done = 1;
@@ -725,39 +688,6 @@ cudaError_t launch_q1_mpk_f32(const Q1Op& A, const MpkF32Args& e, cudaStream_t s
   return cudaGetLastError();
 }
 
-namespace {
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
-bool encode_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
-               uint64_t pitch_elems, uint32_t b0, uint32_t b1) {
-  auto enc = tensor_map_encoder();
-  if (!enc || ((uintptr_t)base & 15) != 0) return false;
-  const cuuint64_t dims[3] = {d0, d1, d2};
-  const cuuint64_t strides[2] = {pitch_elems * 4, pitch_elems * d1 * 4};
-  const cuuint32_t box[3] = {b0, b1, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-}  // namespace
 
 Q1TmaMaps* q1_tma_build(const Q1Op& A, const float* const* cols, int ncols) {
   // rows of u must be 16-byte multiples (nx % 4 == 0); boxes no larger than the grid
@@ -766,11 +696,11 @@ Q1TmaMaps* q1_tma_build(const Q1Op& A, const float* const* cols, int ncols) {
     return nullptr;
   auto* m = new Q1TmaMaps{};
   m->ncols = ncols;
-  bool ok = encode_3d(&m->mk, A.kappaf, (uint64_t)A.nx + 1, (uint64_t)A.ny + 1,
+  bool ok = tma::encode_3d(&m->mk, A.kappaf, (uint64_t)A.nx + 1, (uint64_t)A.ny + 1,
                       (uint64_t)A.nz + 1, (uint64_t)A.kpitch, TKW, TKH);
   for (int c = 0; ok && c < ncols; ++c) {
     m->col[c] = cols[c];
-    ok = encode_3d(&m->mu[c], cols[c], (uint64_t)A.nx, (uint64_t)A.ny, (uint64_t)A.nz,
+    ok = tma::encode_3d(&m->mu[c], cols[c], (uint64_t)A.nx, (uint64_t)A.ny, (uint64_t)A.nz,
                    (uint64_t)A.nx, TUW, TUH);
   }
   if (!ok) {

@@ -176,3 +176,69 @@ def test_pcg_fp32_zero_rhs():
     A = sstep.Stencil(12, 10, 8, 7)
     x, info, _ = solve(A, np.zeros(960), algo="pcg", precision="fp32_rr", lambda_max=2.0)
     assert info.status == sstep.OK and info.outer_iters == 0 and not x.any()
+
+
+# ---------------------------------------------------------------- TMA-fed 7-point steps
+# With nx a multiple of 4, nx >= 72 and ny >= 18 the FP32 MPK steps and the FP32 PCG product
+# take the kernel whose u planes arrive by tensor-memory-accelerator copies (64 x 16 tiles of a
+# z chunk, 72 x 18 boxes).  SSTEP_STENCIL_TMA=0 keeps the register-fed kernel, which does the
+# same arithmetic in the same order.
+
+ANISO7 = [-0.5, -1.0, -2.0, 7.5, -2.0, -1.0, -0.5]  # -z, -y, -x, centre, +x, +y, +z
+
+
+@pytest.mark.parametrize("dims,weights,s", [
+    ((72, 18, 9), None, 4), ((76, 19, 17), None, 4), ((136, 40, 30), None, 8),
+    ((76, 35, 21), ANISO7, 3), ((68, 18, 9), None, 4)])
+def test_fp32_stencil_tma_steps_equal_register_fed(dims, weights, s, monkeypatch):
+    """One full tile; ragged x and y tails; several tiles and z chunks at s = 8; weights that
+    are not Poisson's; and a grid narrower than the box (plain loads either way).  The MPK
+    steps carry no reduction, so the two kernels give the same basis and the same iterates bit
+    for bit; the solve reaches the FP64 true residual."""
+    A = sstep.Stencil(*dims, points=7, weights=weights)
+    xt, b = I.poisson_problem(dims, 7)
+    kw = dict(s=s, sweeps=30, rtol=1e-8, precision="fp32_rr", lambda_max=2.0)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SSTEP_STENCIL_TMA", flag)
+        x, info, _ = solve(A, b, **kw)
+        out.append((info, x))
+    (i1, x1), (i0, x0) = out
+    assert i1.status == sstep.OK and i1.relres_true <= 2e-8
+    assert i1.outer_iters == i0.outer_iters and np.array_equal(x1, x0)
+
+
+def test_fp32_stencil_tma_against_oracle():
+    """The TMA-fed steps on a grid with ragged tiles against the FP64 oracle (Algorithm 1, same
+    Chebyshev interval): the solution within rtol * kappa(A) of the oracle's."""
+    dims = (80, 21, 19)
+    csr = O.CSR(*I.poisson_csr(dims, 7))
+    xt, b = I.poisson_problem(dims, 7)
+    x, info, bi = solve(sstep.Stencil(*dims, points=7), b, s=4, sweeps=3, rtol=1e-8,
+                        precision="fp32_rr", power_v0=dev(I.power_start(csr.n)))
+    assert info.status == sstep.OK and info.relres_true <= 2e-8
+    ref = O.pcgs(csr, b, s=4, nu=3, rtol=1e-8, algo="literal", lambda_max=bi["lambda_max"])
+    assert ref.status == O.OK
+    assert relerr(x, ref.x) <= 2e-8 * poisson_kappa(dims, 7) + 1e-10
+
+
+@pytest.mark.parametrize("dims", [(76, 19, 17), (128, 36, 24)])
+def test_fp32_pcg_stencil_tma(dims, monkeypatch):
+    """The FP32 PCG product (A p with p^T A p) on the TMA-fed kernel: both kernels reach the
+    FP64 true residual with counts close to the oracle's PCG; the grids differ (one wave of
+    resident CTAs each), so p^T A p is summed in another order and the counts may differ by a
+    step or two."""
+    csr = O.CSR(*I.poisson_csr(dims, 7))
+    xt, b = I.poisson_problem(dims, 7)
+    ref = O.pcg(csr, b, rtol=1e-8)
+    assert ref.status == O.OK
+    its = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SSTEP_STENCIL_TMA", flag)
+        x, info, _ = solve(sstep.Stencil(*dims, points=7), b, algo="pcg", rtol=1e-8,
+                           precision="fp32_rr", lambda_max=2.0)
+        assert info.status == sstep.OK and info.relres_true <= 2e-8
+        assert abs(info.outer_iters - ref.iters) <= max(3, 0.05 * ref.iters)
+        assert relerr(x, ref.x) <= 2e-8 * poisson_kappa(dims, 7) + 1e-10
+        its.append(info.outer_iters)
+    assert abs(its[0] - its[1]) <= 2
